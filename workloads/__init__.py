@@ -1,0 +1,18 @@
+"""Seeded synthetic inputs for the graph search: vectors, queries, proximity
+graphs and ghost samples.
+
+This package produces INPUTS only. It holds none of the search arithmetic
+(distances inside the search, direction bits, codecs, merges): the CPU oracle
+under ``oracle/`` and the CUDA library each implement those on their own, and
+both consume what this package generates. The proximity graph is an input of
+the method (the paper assumes it pre-constructed, Section 2.1), so its builder
+lives here too.
+"""
+
+from .mixtures import Mixture, CONFIGS, WorkloadSpec, make_mixture, make_queries
+from .graph import knn_exact, knn_partitioned, prune_by_detours, build_graph, ghost_sample
+
+__all__ = [
+    "Mixture", "CONFIGS", "WorkloadSpec", "make_mixture", "make_queries",
+    "knn_exact", "knn_partitioned", "prune_by_detours", "build_graph", "ghost_sample",
+]

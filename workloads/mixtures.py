@@ -1,0 +1,169 @@
+"""Seeded Gaussian-mixture base vectors and queries.
+
+Every generator takes an explicit seed and uses numpy's PCG64, so the CPU
+oracle and the CUDA path read bit-identical inputs. Nothing here computes any
+step of the search.
+
+Seeds follow one convention per workload number ``c``: base vectors
+``1000 + c``, queries ``2000 + c``, ghost sample ``3000 + c``, search RNG
+``4000 + c``, MLP initialisation ``5000 + c``.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional, Tuple
+
+import numpy as np
+
+
+@dataclass
+class Mixture:
+    """A Gaussian mixture: per-cluster centers, per-cluster per-dimension
+    standard deviations and cluster weights, plus the post-processing the
+    workload applies to every sample (L2 normalisation or integer clamping)."""
+
+    centers: np.ndarray           # C x d float64
+    sigmas: np.ndarray            # C x d float64
+    weights: np.ndarray           # C float64, sums to 1
+    normalize: bool = False
+    integer_range: Optional[Tuple[int, int]] = None
+
+    @property
+    def dim(self) -> int:
+        return self.centers.shape[1]
+
+    def _post(self, x: np.ndarray) -> np.ndarray:
+        if self.normalize:
+            nrm = np.sqrt(np.einsum("ij,ij->i", x, x))
+            nrm[nrm == 0] = 1.0
+            x = x / nrm[:, None]
+        if self.integer_range is not None:
+            lo, hi = self.integer_range
+            x = np.rint(np.clip(x, lo, hi))
+        return x.astype(np.float32)
+
+    def sample(self, n: int, seed: int, chunk: int = 1 << 20) -> Tuple[np.ndarray, np.ndarray]:
+        """Draw ``n`` points. Returns (X float32 n x d, cluster labels int32)."""
+        rng = np.random.Generator(np.random.PCG64(seed))
+        labels = rng.choice(len(self.weights), size=n, p=self.weights).astype(np.int32)
+        out = np.empty((n, self.dim), dtype=np.float32)
+        for s in range(0, n, chunk):
+            e = min(n, s + chunk)
+            lab = labels[s:e]
+            z = rng.standard_normal((e - s, self.dim))
+            out[s:e] = self._post(self.centers[lab] + self.sigmas[lab] * z)
+        return out, labels
+
+    def sample_between(self, n: int, seed: int) -> np.ndarray:
+        """Off-distribution points: the midpoint of two distinct random cluster
+        centers plus the mean cluster's noise. Lands between clusters."""
+        rng = np.random.Generator(np.random.PCG64(seed))
+        c = len(self.weights)
+        a = rng.integers(0, c, size=n)
+        b = (a + 1 + rng.integers(0, c - 1, size=n)) % c
+        mid = 0.5 * (self.centers[a] + self.centers[b])
+        sig = 0.5 * (self.sigmas[a] + self.sigmas[b])
+        return self._post(mid + sig * rng.standard_normal((n, self.dim)))
+
+
+def make_mixture(d: int, n_clusters: int, seed: int, *, center_range=(0.0, 100.0),
+                 sigma=8.0, sigma_range=None, zipf_s: Optional[float] = None,
+                 normalize=False, integer_range=None) -> Mixture:
+    """Build a mixture: centers ~ U[center_range]^d; sigma fixed (isotropic) or
+    per-cluster per-dimension ~ U[sigma_range]; weights equal or Zipf(s) over
+    a seeded permutation of the clusters."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x5EED))
+    lo, hi = center_range
+    centers = rng.uniform(lo, hi, size=(n_clusters, d))
+    if sigma_range is not None:
+        sigmas = rng.uniform(sigma_range[0], sigma_range[1], size=(n_clusters, d))
+    else:
+        sigmas = np.full((n_clusters, d), float(sigma))
+    if zipf_s is not None:
+        w = 1.0 / np.arange(1, n_clusters + 1, dtype=np.float64) ** zipf_s
+        w = w[rng.permutation(n_clusters)]
+    else:
+        w = np.ones(n_clusters)
+    return Mixture(centers, sigmas, w / w.sum(), normalize, integer_range)
+
+
+@dataclass
+class WorkloadSpec:
+    """One synthetic workload: data shape, graph shape and search defaults."""
+
+    number: int
+    name: str
+    n: int
+    d: int
+    n_clusters: int
+    nq: int
+    degree: int
+    knn_k: int                     # kNN list length before pruning
+    graph: str                     # "exact" or "partitioned"
+    ghost_n: int
+    ghost_degree: int
+    center_range: Tuple[float, float] = (0.0, 100.0)
+    sigma: float = 8.0
+    sigma_range: Optional[Tuple[float, float]] = None
+    zipf_s: Optional[float] = None
+    normalize: bool = False
+    integer_range: Optional[Tuple[int, int]] = None
+    search: dict = field(default_factory=dict)
+
+    @property
+    def seeds(self) -> dict:
+        c = self.number
+        return {"base": 1000 + c, "query": 2000 + c, "ghost": 3000 + c,
+                "search": 4000 + c, "mlp": 5000 + c}
+
+    def mixture(self) -> Mixture:
+        return make_mixture(self.d, self.n_clusters, self.seeds["base"],
+                            center_range=self.center_range, sigma=self.sigma,
+                            sigma_range=self.sigma_range, zipf_s=self.zipf_s,
+                            normalize=self.normalize, integer_range=self.integer_range)
+
+    def scaled(self, n: int, nq: Optional[int] = None, n_clusters: Optional[int] = None,
+               ghost_n: Optional[int] = None) -> "WorkloadSpec":
+        """The same recipe at a smaller size (for fast tests)."""
+        import dataclasses
+        return dataclasses.replace(
+            self, n=n, nq=nq if nq is not None else self.nq,
+            n_clusters=n_clusters if n_clusters is not None else max(1, min(self.n_clusters, n // 100)),
+            ghost_n=ghost_n if ghost_n is not None else max(16, n // 100))
+
+
+# The five workloads. Where the recipe leaves a detail open, the value here is
+# this project's reading (cluster centers and spreads of workloads 3-5, the
+# degree of workload 4, the kNN list length before pruning).
+CONFIGS = {
+    1: WorkloadSpec(1, "tiny-10k-128d", 10_000, 128, 50, 100, 32, 64, "exact", 100, 16,
+                    sigma=8.0, search=dict(k=10, itopk=64, search_width=1, max_iters=64)),
+    2: WorkloadSpec(2, "scale-1M-96d", 1_000_000, 96, 1000, 10_000, 64, 96, "partitioned",
+                    10_000, 16, sigma_range=(0.5, 4.0), normalize=True,
+                    search=dict(k=10, itopk=64, search_width=1, max_iters=160)),
+    3: WorkloadSpec(3, "precision-10M-128d-int", 10_000_000, 128, 10_000, 10_000, 32, 64,
+                    "partitioned", 100_000, 16, center_range=(0.0, 255.0), sigma=16.0,
+                    integer_range=(0, 255),
+                    search=dict(k=10, itopk=128, search_width=1, max_iters=160)),
+    4: WorkloadSpec(4, "learned-5M-256d-zipf", 5_000_000, 256, 5000, 10_000, 32, 64,
+                    "partitioned", 50_000, 16, sigma=8.0, zipf_s=1.1,
+                    search=dict(k=10, itopk=64, search_width=1, max_iters=160)),
+    5: WorkloadSpec(5, "serving-20M-96d", 20_000_000, 96, 20_000, 10_000, 32, 64,
+                    "partitioned", 200_000, 16, sigma_range=(0.5, 4.0), normalize=True,
+                    search=dict(k=10, itopk=64, search_width=1, max_iters=160)),
+}
+
+
+def make_queries(spec: WorkloadSpec, nq: Optional[int] = None, seed: Optional[int] = None,
+                 off_fraction: float = 0.0) -> np.ndarray:
+    """Queries from the workload's mixture; a fraction may be drawn between
+    clusters (off-distribution)."""
+    nq = spec.nq if nq is None else nq
+    seed = spec.seeds["query"] if seed is None else seed
+    mix = spec.mixture()
+    n_off = int(round(off_fraction * nq))
+    q, _ = mix.sample(nq - n_off, seed)
+    if n_off:
+        q = np.concatenate([q, mix.sample_between(n_off, seed + 7)], axis=0)
+    return np.ascontiguousarray(q, dtype=np.float32)
