@@ -1,0 +1,170 @@
+/*
+ * ann.h — C ABI of the GB300 graph-search library (libann.so).
+ *
+ * Batched best-first (beam) search over a fixed-degree proximity graph, with
+ * ghost staging and direction-guided selection, after PathWeaver
+ * (arXiv 2507.17094). All search work runs in the library's own CUDA kernels
+ * for sm_103a; there is no CPU fallback.
+ *
+ * Conventions for every call:
+ *   - Ids are uint32; ANN_INVALID_ID marks "no result". Distances are SQUARED
+ *     L2 (Eq. 2 without the root; the ranking is the same).
+ *   - Results are ordered by (distance, id) ascending.
+ *   - "device" pointers are CUDA device memory of the index's device; "host"
+ *     pointers are ordinary (preferably pinned) host memory. The caller owns
+ *     every buffer it passes; the library owns the index and its scratch.
+ *   - Calls return ann_status. Argument errors are found on the host before
+ *     any launch and return ANN_EINVAL with nothing launched; the message is
+ *     in ann_last_error() (thread-local). Work on a stream is asynchronous;
+ *     device-side failures (a bounded wait that ran out) are recorded in the
+ *     index's device error word and reported by ann_sync().
+ *   - An index is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef ANN_H
+#define ANN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ANN_INVALID_ID 0xFFFFFFFFu
+#define ANN_MAX_ITOPK 512u
+#define ANN_MAX_DIM 1024u
+#define ANN_MAX_DEGREE 128u
+#define ANN_MAX_WIDTH 8u
+
+typedef enum {
+    ANN_OK = 0,
+    ANN_EINVAL = 1,    /* bad argument; nothing was launched */
+    ANN_ENOMEM = 2,    /* device or host allocation failed */
+    ANN_ECUDA = 3,     /* a CUDA runtime call failed */
+    ANN_EIO = 4,       /* index file unreadable or malformed */
+    ANN_ETIMEOUT = 5,  /* a bounded device wait ran out (reported by ann_sync) */
+    ANN_EBUSY = 6,     /* serving: not admissible right now */
+    ANN_EDEVICE = 7    /* no usable CUDA device */
+} ann_status;
+
+typedef enum { ANN_F32 = 0, ANN_F16 = 1, ANN_E4M3 = 2 } ann_storage;
+
+typedef enum {
+    ANN_ENTRY_RANDOM = 0,      /* Section 2.2 Step 2: m random nodes */
+    ANN_ENTRY_GHOST = 1,       /* Section 3.2.2: ghost staging from random ghost nodes */
+    ANN_ENTRY_GIVEN_GHOST = 2  /* ghost staging from caller-given ghost nodes (learned entry);
+                                  a query whose first given id is ANN_INVALID_ID falls back to 1 */
+} ann_entry;
+
+/* Search parameters. Paper notation: itopk = l (queue size), search_width =
+ * r (parents per iteration), max_iters = the iteration cap (Section 2.2). */
+typedef struct {
+    uint32_t k;                 /* results per query, 1 <= k <= itopk */
+    uint32_t itopk;             /* queue size l, 1..ANN_MAX_ITOPK */
+    uint32_t search_width;      /* parents per iteration r, 1..ANN_MAX_WIDTH */
+    uint32_t max_iters;         /* iteration cap T (0 = seeds only) */
+    uint32_t num_seeds;         /* random seeds m (entry 0); 0 = search_width * degree */
+    float dgs_discard;          /* DGS discard ratio rho in [0,1); 0 disables DGS (Section 3.3.2) */
+    float dgs_cooldown;         /* cool-down fraction c of max_iters without selection (default 0.3) */
+    uint32_t dgs_reexpand;      /* 1: parents expanded under DGS expand fully again in cool-down */
+    uint32_t entry;             /* ann_entry */
+    uint32_t ghost_itopk;       /* ghost queue size; 0 = min(itopk, 64) */
+    uint32_t ghost_max_iters;   /* ghost iterations from random ghost seeds (default 16) */
+    uint32_t ghost_max_iters_given; /* ghost iterations from given ghost seeds (default 4) */
+    uint32_t ghost_seeds_out;   /* ghost results that seed the base queue; 0 = ghost_itopk */
+    uint32_t rerank;            /* 1: rescore the final queue on the FP32 originals (low precision) */
+    uint64_t seed;              /* search RNG seed (splitmix64 counter stream) */
+    uint64_t qid_base;          /* global index of query 0 of this call (RNG stream per query) */
+} ann_search_params;
+
+/* Per-query event counters (exact counts of the work done). */
+typedef struct {
+    uint32_t iters, parents, dgs_parents, vec_rows;
+    uint32_t ghost_iters, ghost_parents, ghost_vec_rows, rerank_rows;
+    uint32_t hash_resets, status;
+} ann_query_stats;
+
+typedef struct ann_index ann_index;
+
+/* Fill *p with the defaults above (k 10, itopk 64, width 1, 64 iterations,
+ * DGS off, cool-down 0.3, random entry, ghost 16/4 iterations). */
+void ann_default_params(ann_search_params *p);
+
+/* Build an index on `device` from host arrays (Section 2.1 takes the graph as
+ * given; Section 3.2.2 the ghost sample and its graph; Section 3.3.2 (a) the
+ * direction table, which is built here on the GPU).
+ *   vectors      host, n x dim FP32, row-major (the source values)
+ *   graph        host, n x degree uint32 (ANN_INVALID_ID = missing edge)
+ *   ghost_ids    host, n_ghost distinct node ids in ascending order (may be NULL if n_ghost = 0)
+ *   ghost_graph  host, n_ghost x ghost_degree uint32 over ghost indices 0..n_ghost-1
+ *   storage      ANN_F32 / ANN_F16 / ANN_E4M3 (codes with a per-vector FP32 scale)
+ *   keep_fp32    1: also keep the FP32 originals on the device for rerank
+ *   build_dir    1: build the direction table (needed for DGS)
+ * Errors: ANN_EINVAL (sizes, ids out of range), ANN_ENOMEM, ANN_ECUDA, ANN_EDEVICE. */
+ann_status ann_index_create(int device, ann_storage storage, uint64_t n, uint32_t dim, uint32_t degree,
+                            const float *vectors, const uint32_t *graph, uint32_t n_ghost,
+                            const uint32_t *ghost_ids, uint32_t ghost_degree, const uint32_t *ghost_graph,
+                            uint32_t keep_fp32, uint32_t build_dir, ann_index **out);
+
+/* Load an index file (magic "ANNIDX01", then u64 n, u32 dim, degree, n_ghost,
+ * ghost_degree, then the arrays of ann_index_create in that order, all
+ * little-endian) and build it as ann_index_create does. Errors: ANN_EIO plus
+ * those of ann_index_create. */
+ann_status ann_index_load(const char *path, int device, ann_storage storage, uint32_t keep_fp32,
+                          uint32_t build_dir, ann_index **out);
+
+ann_status ann_index_free(ann_index *index);
+
+ann_status ann_index_info(const ann_index *index, uint64_t *n, uint32_t *dim, uint32_t *degree,
+                          uint32_t *storage, uint32_t *n_ghost, uint32_t *ghost_degree);
+
+/* Copy one of the index's device arrays to host memory (for inspection):
+ *   0 codes (n x dim, element type of the storage, row stride padded away)
+ *   1 scales (n floats; FP16/E4M3 only)
+ *   2 direction table (n x degree x ceil(dim/32) uint32)
+ *   3 ghost codes (n_ghost x dim)   4 ghost scales (n_ghost floats)
+ * `bytes` must equal the array's size. */
+ann_status ann_index_export(const ann_index *index, int which, void *host_dst, uint64_t bytes);
+
+/* Batched search (Section 2.2 Steps 1-4, Section 3.2.2, Section 3.3.2).
+ *   queries      device, nq x dim FP32 row-major
+ *   given_seeds  device, nq x n_given ghost indices (entry ANN_ENTRY_GIVEN_GHOST), else NULL
+ *   ids, dists   device, nq x k (caller-owned)
+ *   stats        device, nq ann_query_stats, or NULL
+ *   stream       cudaStream_t (NULL = legacy default stream)
+ * Asynchronous on `stream`; returns after the launch. */
+ann_status ann_search(ann_index *index, const float *queries, uint32_t nq, const ann_search_params *params,
+                      const uint32_t *given_seeds, uint32_t n_given, uint32_t *ids, float *dists,
+                      ann_query_stats *stats, void *stream);
+
+/* The same search with HOST buffers: copies the queries in, searches, copies
+ * the results out, and synchronises `stream` before returning. Uses a device
+ * workspace owned by the index (grown on demand). */
+ann_status ann_search_host(ann_index *index, const float *queries, uint32_t nq,
+                           const ann_search_params *params, const uint32_t *given_seeds, uint32_t n_given,
+                           uint32_t *ids, float *dists, void *stream);
+
+/* Synchronise `stream` and report (then clear) the index's device error
+ * word: ANN_OK, or ANN_ETIMEOUT if a bounded device wait ran out. */
+ann_status ann_sync(ann_index *index, void *stream);
+
+/* Preprocessing primitives on caller-owned device memory (Section 3.3.2 (a)
+ * and the low-precision codec), used by ann_index_create.
+ * ann_encode: x (n x dim FP32) -> codes (n x dim FP16 or E4M3, dense rows) +
+ *   scales (n floats). FP16 scale 2^(floor(log2 max|x|) - 14); E4M3 scale
+ *   max|x| / 448 with round-to-nearest-even saturating codes.
+ * ann_dir_table: stored vectors (codes + scales, or FP32 when storage is
+ *   ANN_F32 and scales NULL), graph (n x degree) -> dir (n x degree x
+ *   ceil(dim/32) uint32); bit b of word w is 1 iff x_v[32w+b] > x_u[32w+b]. */
+ann_status ann_encode(const float *x, uint64_t n, uint32_t dim, ann_storage storage, void *codes,
+                      float *scales, void *stream);
+ann_status ann_dir_table(const void *vectors, const float *scales, ann_storage storage, uint64_t n,
+                         uint32_t dim, const uint32_t *graph, uint32_t degree, uint32_t *dir, void *stream);
+
+/* Thread-local message for the last failing call on this thread. */
+const char *ann_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANN_H */

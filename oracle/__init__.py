@@ -215,7 +215,10 @@ def recall_at_k(ann_ids: np.ndarray, gt_ids: np.ndarray, gt_dists: np.ndarray, X
 def derived_counts(degree: int, max_iters: int, dgs_discard: float, dgs_cooldown: float):
     """Readings of Section 3.3.2: DGS keeps n = deg - round(rho * deg) of a
     parent's neighbours (at least 1); the cool-down is the last
-    round(c * T) iterations. Rounding is half-up, in double."""
+    round(c * T) iterations. Rounding is half-up, in double. Both ratios are
+    taken at FP32 precision, the width the search parameters have."""
+    dgs_discard = float(np.float32(dgs_discard))
+    dgs_cooldown = float(np.float32(dgs_cooldown))
     n_keep = degree - int(math.floor(dgs_discard * degree + 0.5)) if dgs_discard > 0 else degree
     n_keep = max(1, min(degree, n_keep))
     it_cool = max_iters - int(math.floor(dgs_cooldown * max_iters + 0.5))

@@ -1,0 +1,15 @@
+"""GB300-native batched graph beam search (PathWeaver, arXiv 2507.17094).
+
+The search runs in hand-written CUDA kernels for sm_103a behind the C ABI in
+``include/ann.h`` (``libann.so``); this package is its build step and a thin
+ctypes binding. PyTorch supplies device memory and streams.
+"""
+
+from .binding import (E4M3, ENTRY_GHOST, ENTRY_GIVEN_GHOST, ENTRY_RANDOM, EXPORTS, F16, F32, INVALID,
+                      STATS_DTYPE, AnnError, Index, SearchParams, dir_table, encode, lib, make_params,
+                      stats_to_numpy)
+from .build import build
+
+__all__ = ["E4M3", "ENTRY_GHOST", "ENTRY_GIVEN_GHOST", "ENTRY_RANDOM", "EXPORTS", "F16", "F32", "INVALID",
+           "STATS_DTYPE", "AnnError", "Index", "SearchParams", "build", "dir_table", "encode", "lib",
+           "make_params", "stats_to_numpy"]

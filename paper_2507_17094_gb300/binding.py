@@ -1,0 +1,230 @@
+"""Python binding of libann.so (ctypes). Argument marshalling only: every step
+of the search runs in the library's CUDA kernels; PyTorch provides device
+memory and streams.
+
+The binding never falls back to anything: if libann.so is missing or no GPU
+is present, the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from .build import LIB
+
+INVALID = 0xFFFFFFFF
+F32, F16, E4M3 = 0, 1, 2
+ENTRY_RANDOM, ENTRY_GHOST, ENTRY_GIVEN_GHOST = 0, 1, 2
+STATUS = {0: "ANN_OK", 1: "ANN_EINVAL", 2: "ANN_ENOMEM", 3: "ANN_ECUDA", 4: "ANN_EIO", 5: "ANN_ETIMEOUT",
+          6: "ANN_EBUSY", 7: "ANN_EDEVICE"}
+
+# Every symbol include/ann.h declares (checked by the tests).
+EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_index_free", "ann_index_info",
+           "ann_index_export", "ann_search", "ann_search_host", "ann_sync", "ann_encode", "ann_dir_table",
+           "ann_last_error")
+
+
+class AnnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SearchParams(C.Structure):
+    _fields_ = [("k", C.c_uint32), ("itopk", C.c_uint32), ("search_width", C.c_uint32),
+                ("max_iters", C.c_uint32), ("num_seeds", C.c_uint32), ("dgs_discard", C.c_float),
+                ("dgs_cooldown", C.c_float), ("dgs_reexpand", C.c_uint32), ("entry", C.c_uint32),
+                ("ghost_itopk", C.c_uint32), ("ghost_max_iters", C.c_uint32),
+                ("ghost_max_iters_given", C.c_uint32), ("ghost_seeds_out", C.c_uint32),
+                ("rerank", C.c_uint32), ("seed", C.c_uint64), ("qid_base", C.c_uint64)]
+
+
+STATS_FIELDS = ("iters", "parents", "dgs_parents", "vec_rows", "ghost_iters", "ghost_parents",
+                "ghost_vec_rows", "rerank_rows", "hash_resets", "status")
+STATS_DTYPE = np.dtype([(f, np.uint32) for f in STATS_FIELDS])
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libann.so (built by ``paper_2507_17094_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"{LIB} is missing: run paper_2507_17094_gb300.build.build() first")
+            L = C.CDLL(LIB)
+            vp, u32, u64, st = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+            L.ann_default_params.argtypes = [C.POINTER(SearchParams)]
+            L.ann_default_params.restype = None
+            L.ann_index_create.argtypes = [C.c_int, C.c_int, u64, u32, u32, vp, vp, u32, vp, u32, vp, u32, u32,
+                                           C.POINTER(vp)]
+            L.ann_index_load.argtypes = [C.c_char_p, C.c_int, C.c_int, u32, u32, C.POINTER(vp)]
+            L.ann_index_free.argtypes = [vp]
+            L.ann_index_info.argtypes = [vp] + [vp] * 6
+            L.ann_index_export.argtypes = [vp, C.c_int, vp, u64]
+            L.ann_search.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp, vp]
+            L.ann_search_host.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp]
+            L.ann_sync.argtypes = [vp, vp]
+            L.ann_encode.argtypes = [vp, u64, u32, C.c_int, vp, vp, vp]
+            L.ann_dir_table.argtypes = [vp, vp, C.c_int, u64, u32, vp, u32, vp, vp]
+            L.ann_last_error.restype = C.c_char_p
+            for f in ("ann_index_create", "ann_index_load", "ann_index_free", "ann_index_info", "ann_index_export",
+                      "ann_search", "ann_search_host", "ann_sync", "ann_encode", "ann_dir_table"):
+                getattr(L, f).restype = st
+            _lib = L
+        return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise AnnError(status, lib().ann_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def make_params(**kw) -> SearchParams:
+    """ann_search_params from keyword arguments over the library defaults."""
+    p = SearchParams()
+    lib().ann_default_params(C.byref(p))
+    names = {f for f, _ in SearchParams._fields_}
+    for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown search parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+class Index:
+    """A device-resident index (library-owned memory)."""
+
+    def __init__(self, vectors: np.ndarray, graph: np.ndarray, storage: int = F32,
+                 ghost_ids: Optional[np.ndarray] = None, ghost_graph: Optional[np.ndarray] = None,
+                 keep_fp32: bool = True, build_dir: bool = True, device: int = 0, _handle=None):
+        self._h = C.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            X = np.ascontiguousarray(vectors, dtype=np.float32)
+            G = np.ascontiguousarray(graph, dtype=np.uint32)
+            S = None if ghost_ids is None else np.ascontiguousarray(ghost_ids, dtype=np.uint32)
+            GG = None if ghost_graph is None else np.ascontiguousarray(ghost_graph, dtype=np.uint32)
+            _check(lib().ann_index_create(device, storage, X.shape[0], X.shape[1], G.shape[1], _np_ptr(X),
+                                          _np_ptr(G), 0 if S is None else S.shape[0], _np_ptr(S),
+                                          0 if GG is None else GG.shape[1], _np_ptr(GG), int(keep_fp32),
+                                          int(build_dir), C.byref(self._h)))
+        n, d, deg, sto, ng, gd = (C.c_uint64(), C.c_uint32(), C.c_uint32(), C.c_uint32(), C.c_uint32(),
+                                  C.c_uint32())
+        _check(lib().ann_index_info(self._h, C.byref(n), C.byref(d), C.byref(deg), C.byref(sto), C.byref(ng),
+                                    C.byref(gd)))
+        self.n, self.dim, self.degree, self.storage = n.value, d.value, deg.value, sto.value
+        self.n_ghost, self.ghost_degree = ng.value, gd.value
+        self.device = device
+
+    @classmethod
+    def load(cls, path: str, storage: int = F32, keep_fp32: bool = True, build_dir: bool = True, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().ann_index_load(path.encode(), device, storage, int(keep_fp32), int(build_dir), C.byref(h)))
+        return cls(None, None, _handle=h, device=device)
+
+    def close(self):
+        if self._h:
+            lib().ann_index_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export(self, which: int) -> np.ndarray:
+        w = (self.dim + 31) // 32
+        dt = {F32: np.float32, F16: np.uint16, E4M3: np.uint8}[self.storage]
+        shape, dtype = {0: ((self.n, self.dim), dt), 1: ((self.n,), np.float32),
+                        2: ((self.n, self.degree, w), np.uint32), 3: ((self.n_ghost, self.dim), dt),
+                        4: ((self.n_ghost,), np.float32)}[which]
+        out = np.empty(shape, dtype=dtype)
+        _check(lib().ann_index_export(self._h, which, _np_ptr(out), out.nbytes))
+        return out
+
+    def search(self, queries, given=None, stats: bool = False, stream=None, out=None, **params):
+        """Search device queries (a CUDA float32 tensor nq x dim). Returns
+        (ids int32-view of uint32, dists, stats-or-None) as CUDA tensors; the
+        call is asynchronous on ``stream``."""
+        import torch
+        p = make_params(**params)
+        nq = queries.shape[0]
+        assert queries.is_cuda and queries.dtype == torch.float32 and queries.is_contiguous()
+        if out is None:
+            ids = torch.empty((nq, p.k), dtype=torch.int32, device=queries.device)
+            dists = torch.empty((nq, p.k), dtype=torch.float32, device=queries.device)
+        else:
+            ids, dists = out
+        st = torch.empty((nq, len(STATS_FIELDS)), dtype=torch.int32, device=queries.device) if stats else None
+        g_ptr, n_given = None, 0
+        if given is not None:
+            assert given.is_cuda and given.dtype == torch.int32 and given.is_contiguous()
+            g_ptr, n_given = given.data_ptr(), given.shape[1]
+        _check(lib().ann_search(self._h, queries.data_ptr(), nq, C.byref(p), g_ptr, n_given, ids.data_ptr(),
+                                dists.data_ptr(), None if st is None else st.data_ptr(), _stream_ptr(stream)))
+        return ids, dists, st
+
+    def search_host(self, queries: np.ndarray, given: Optional[np.ndarray] = None, stream=None, **params):
+        """Search host queries; copies in and out inside the call (synchronous)."""
+        p = make_params(**params)
+        Q = np.ascontiguousarray(queries, dtype=np.float32)
+        nq = Q.shape[0]
+        ids = np.empty((nq, p.k), dtype=np.uint32)
+        dists = np.empty((nq, p.k), dtype=np.float32)
+        G = None if given is None else np.ascontiguousarray(given, dtype=np.uint32)
+        _check(lib().ann_search_host(self._h, _np_ptr(Q), nq, C.byref(p), _np_ptr(G),
+                                     0 if G is None else G.shape[1], _np_ptr(ids), _np_ptr(dists),
+                                     _stream_ptr(stream)))
+        return ids, dists
+
+    def sync(self, stream=None):
+        _check(lib().ann_sync(self._h, _stream_ptr(stream)))
+
+
+def stats_to_numpy(st) -> np.ndarray:
+    a = st.cpu().numpy().astype(np.uint32)
+    return np.ascontiguousarray(a).view(STATS_DTYPE).reshape(-1)
+
+
+def encode(x, storage: int, stream=None):
+    """Device FP32 rows -> (codes, scales) as CUDA tensors (dense rows)."""
+    import torch
+    n, d = x.shape
+    codes = torch.empty((n, d), dtype=torch.int16 if storage == F16 else torch.uint8, device=x.device)
+    scales = torch.empty((n,), dtype=torch.float32, device=x.device)
+    _check(lib().ann_encode(x.data_ptr(), n, d, storage, codes.data_ptr(), scales.data_ptr(),
+                            _stream_ptr(stream)))
+    return codes, scales
+
+
+def dir_table(vectors, scales, storage: int, graph, stream=None):
+    """Direction table of stored vectors (codes + scales, or FP32 rows)."""
+    import torch
+    n, d = vectors.shape
+    deg = graph.shape[1]
+    w = (d + 31) // 32
+    out = torch.empty((n, deg, w), dtype=torch.int32, device=vectors.device)
+    _check(lib().ann_dir_table(vectors.data_ptr(), None if scales is None else scales.data_ptr(), storage, n, d,
+                               graph.data_ptr(), deg, out.data_ptr(), _stream_ptr(stream)))
+    return out

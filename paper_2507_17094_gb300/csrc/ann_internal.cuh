@@ -1,0 +1,144 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "ann.h"
+
+#define ANN_DEV_OK 0
+#define ANN_DEV_TIMEOUT 1
+
+// Device-side bound on any wait (an mbarrier phase, a flag): about one second
+// at the GB300's clock. On expiry the waiter records ANN_DEV_TIMEOUT in the
+// error word and gives up instead of spinning forever.
+#define ANN_WAIT_LIMIT_CYCLES (2000000000ll)
+
+struct ann_index {
+    int device = 0;
+    int storage = ANN_F32;
+    uint64_t n = 0;
+    uint32_t dim = 0, degree = 0, deg_pad = 0, words = 0;
+    uint32_t elem_bytes = 4;     // bytes per stored element
+    uint32_t row_bytes = 0;      // device row stride of the stored codes (multiple of 16)
+    uint32_t row32_bytes = 0;    // device row stride of the FP32 originals (multiple of 16)
+    void *codes = nullptr;       // n x row_bytes
+    float *scales = nullptr;     // n (FP16 / E4M3)
+    float *x32 = nullptr;        // n x row32_bytes (FP32 originals, optional)
+    uint32_t *graph = nullptr;   // n x deg_pad
+    uint32_t *dir = nullptr;     // n x deg_pad x words (optional)
+    uint32_t n_ghost = 0, ghost_degree = 0, gdeg_pad = 0;
+    uint32_t *ghost_ids = nullptr;     // n_ghost ascending
+    void *ghost_codes = nullptr;       // n_ghost x row_bytes
+    float *ghost_scales = nullptr;     // n_ghost
+    uint32_t *ghost_graph = nullptr;   // n_ghost x gdeg_pad
+    uint32_t *d_counter = nullptr;     // work counter for the persistent search kernel
+    int *d_error = nullptr;            // device error word
+    void *ws = nullptr;                // ann_search_host workspace
+    size_t ws_bytes = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+};
+
+namespace ann {
+
+void set_error(const char *fmt, ...);
+ann_status cuda_fail(cudaError_t e, const char *what);
+
+#define ANN_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t _e = (call);                                    \
+        if (_e != cudaSuccess) return ::ann::cuda_fail(_e, #call);  \
+    } while (0)
+
+inline uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
+
+// Device row stride for `bytes` of payload: a multiple of 16 bytes (the
+// bulk-copy granule).
+inline uint32_t row_stride(uint32_t bytes) { return round_up(bytes, 16); }
+
+// Shared-memory row stride for staged rows: a multiple of 16 bytes whose
+// word count is 4 mod 8, so 8 lanes reading 16 bytes each from 8 different
+// rows hit 8 different 4-bank groups.
+inline uint32_t smem_row_stride(uint32_t bytes)
+{
+    uint32_t w = round_up(bytes, 16) / 4;
+    while (w % 8 != 4) w += 4;
+    return w * 4;
+}
+
+}  // namespace ann
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Make an mbarrier initialisation (and prior generic-proxy shared-memory
+// writes) visible to the async proxy that bulk copies complete through.
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` to complete, at most ANN_WAIT_LIMIT_CYCLES.
+// Returns false (and records a timeout in *err) if it did not.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > ANN_WAIT_LIMIT_CYCLES) {
+            atomicExch(err, ANN_DEV_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// One-dimensional bulk copy global -> this CTA's shared memory through the
+// TMA engine; completion is counted in bytes on `bar`. dst, src and bytes
+// must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}

@@ -1,0 +1,915 @@
+// Batched graph beam search on sm_103a (Section 2.2 Steps 1-4), with ghost
+// staging (Section 3.2.2) and direction-guided selection (Section 3.3.2).
+//
+// Design (GB300-first, not the paper's 32-thread-block CAGRA kernel):
+//   - persistent CTAs of 4 warps; each warp owns one query at a time and pulls
+//     the next query index from a device counter, so long and short searches
+//     balance across the 152 SMs;
+//   - per warp, shared memory holds the query, two copies of the priority
+//     queue (merge writes the other copy), the candidate list, the adjacency
+//     and direction rows of the current parents, 32 staged vector rows and an
+//     open-addressing visited table;
+//   - every random global read (adjacency rows, direction rows, vector rows,
+//     FP32 rerank rows) is a 1-D TMA bulk copy into shared memory completing
+//     on the warp's mbarrier, so a warp keeps up to 32 rows in flight with one
+//     instruction per row;
+//   - distances are computed lane-per-row from shared memory, elements in
+//     index order with one fused multiply-add each, so they are bit-identical
+//     to the FP32 reference definition; the query's sign bits relative to each
+//     evaluated node (for DGS) fall out of the same pass;
+//   - merges are rank-based: each entry's output slot is its rank among the
+//     candidates plus its rank in the queue, so any itopk up to 512 works.
+//
+// Visited set: the table is exact between resets. It is cleared (and refilled
+// with the queue's ids) only when it would pass half full. Forgetting a node
+// that is no longer in the queue cannot change the result: its key is larger
+// than the queue's current l-th key (which only decreases), so re-evaluating
+// it rejects it again. Results therefore equal those of an exact visited set;
+// only the work counters can grow (counted in hash_resets).
+#include <algorithm>
+#include <cmath>
+
+#include "ann_internal.cuh"
+
+using namespace ann;
+
+namespace {
+
+constexpr uint32_t kUnexpanded = 0, kPartial = 1, kExpanded = 2;
+constexpr uint64_t kGhostTag = 0x67686F7374ull;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kStageRows = 32;
+
+struct View {
+    const uint8_t *codes;
+    const float *scales;   // nullptr for FP32
+    uint32_t row_bytes;
+    const uint32_t *graph;
+    uint32_t deg, deg_pad;
+    const uint32_t *dir;   // nullptr: no DGS on this graph
+    uint32_t n;
+};
+
+struct Layout {  // byte offsets inside one warp's shared-memory region
+    uint32_t q, bd[2], bi[2], bs[2], bq[2], cd, ci, cq, cs, ck, adj, dir, par, stage, hash, bar, total;
+};
+
+struct Args {
+    View base, ghost;
+    const uint32_t *ghost_ids;
+    const uint8_t *x32;
+    uint32_t row32_bytes;
+    const float *queries;
+    uint32_t nq, d, w;
+    const uint32_t *given;
+    uint32_t n_given;
+    uint32_t *out_ids;
+    float *out_dists;
+    ann_query_stats *stats;
+    uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank, want_bits;
+    uint64_t seed, qid_base;
+    uint32_t *counter;
+    int *err;
+    Layout lay;
+    uint32_t cap_cand, hash_bits, stage_stride;
+};
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ bool key_less(float da, uint32_t ia, float db, uint32_t ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// One element of the distance: df = q - x, acc += df * df (one rounding),
+// and the DGS sign bit [q > x] == [df > 0].
+__device__ __forceinline__ void step(float qv, float xv, float &acc, uint32_t &word, uint32_t bit)
+{
+    const float df = __fsub_rn(qv, xv);
+    acc = __fmaf_rn(df, df, acc);
+    word |= (uint32_t)(df > 0.0f) << bit;
+}
+
+// Squared L2 between the staged row and the query (both in shared memory),
+// elements in index order; writes ceil(d/32) sign words when `bits`.
+template <int ST>
+__device__ __forceinline__ float row_dist(const uint8_t *row, const float *q, float scale, uint32_t d,
+                                          uint32_t *qb, bool bits)
+{
+    float acc = 0.0f;
+    const uint32_t nw = (d + 31) >> 5;
+    for (uint32_t t = 0; t < nw; ++t) {
+        uint32_t word = 0;
+        const uint32_t base = t * 32;
+        if (ST == ANN_F32) {
+#pragma unroll
+            for (uint32_t c = 0; c < 8; ++c) {
+                const uint32_t i = base + c * 4;
+                if (i < d) {
+                    const float4 x = *reinterpret_cast<const float4 *>(row + (size_t)i * 4);
+                    const float4 y = *reinterpret_cast<const float4 *>(q + i);
+                    step(y.x, x.x, acc, word, c * 4 + 0);
+                    if (i + 1 < d) step(y.y, x.y, acc, word, c * 4 + 1);
+                    if (i + 2 < d) step(y.z, x.z, acc, word, c * 4 + 2);
+                    if (i + 3 < d) step(y.w, x.w, acc, word, c * 4 + 3);
+                }
+            }
+        } else if (ST == ANN_F16) {
+#pragma unroll
+            for (uint32_t c = 0; c < 4; ++c) {
+                const uint32_t i = base + c * 8;
+                if (i < d) {
+                    const uint4 raw = *reinterpret_cast<const uint4 *>(row + (size_t)i * 2);
+                    const __half2 *h = reinterpret_cast<const __half2 *>(&raw);
+                    const float4 y0 = *reinterpret_cast<const float4 *>(q + i);
+                    const float4 y1 = *reinterpret_cast<const float4 *>(q + i + 4);
+                    const float ys[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+                    for (uint32_t e = 0; e < 4; ++e) {
+                        const float2 f = __half22float2(h[e]);
+                        if (i + 2 * e < d) step(ys[2 * e], __fmul_rn(scale, f.x), acc, word, c * 8 + 2 * e);
+                        if (i + 2 * e + 1 < d)
+                            step(ys[2 * e + 1], __fmul_rn(scale, f.y), acc, word, c * 8 + 2 * e + 1);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (uint32_t c = 0; c < 2; ++c) {
+                const uint32_t i = base + c * 16;
+                if (i < d) {
+                    const uint4 raw = *reinterpret_cast<const uint4 *>(row + i);
+                    const uint16_t *pr = reinterpret_cast<const uint16_t *>(&raw);
+#pragma unroll
+                    for (uint32_t e = 0; e < 8; ++e) {
+                        const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pr[e], __NV_E4M3);
+                        const float2 f = __half22float2(__half2(hr));
+                        const uint32_t ii = i + 2 * e;
+                        if (ii < d) step(q[ii], __fmul_rn(scale, f.x), acc, word, c * 16 + 2 * e);
+                        if (ii + 1 < d) step(q[ii + 1], __fmul_rn(scale, f.y), acc, word, c * 16 + 2 * e + 1);
+                    }
+                }
+            }
+        }
+        if (bits) qb[t] = word;
+    }
+    return acc;
+}
+
+template <int ST>
+struct WarpSearch {
+    const Args &a;
+    uint32_t lane;
+    float *q;
+    float *bd[2];
+    uint32_t *bi[2];
+    uint8_t *bs[2];
+    uint32_t *bq[2];
+    float *cd;
+    uint32_t *ci, *cq;
+    int *cs;
+    uint8_t *ck;
+    uint32_t *adj, *dirs, *par;
+    uint8_t *stage;
+    uint32_t *hash;
+    uint64_t *bar;
+    uint32_t cur = 0, cnt = 0, phase = 0, hash_count = 0;
+    bool failed = false;
+    uint32_t qi = 0;
+    uint64_t qid = 0;
+    ann_query_stats st;
+
+    __device__ WarpSearch(const Args &args, uint8_t *base) : a(args), lane(threadIdx.x & 31)
+    {
+        const Layout &L = a.lay;
+        q = reinterpret_cast<float *>(base + L.q);
+        for (int s = 0; s < 2; ++s) {
+            bd[s] = reinterpret_cast<float *>(base + L.bd[s]);
+            bi[s] = reinterpret_cast<uint32_t *>(base + L.bi[s]);
+            bs[s] = base + L.bs[s];
+            bq[s] = reinterpret_cast<uint32_t *>(base + L.bq[s]);
+        }
+        cd = reinterpret_cast<float *>(base + L.cd);
+        ci = reinterpret_cast<uint32_t *>(base + L.ci);
+        cq = reinterpret_cast<uint32_t *>(base + L.cq);
+        cs = reinterpret_cast<int *>(base + L.cs);
+        ck = base + L.ck;
+        adj = reinterpret_cast<uint32_t *>(base + L.adj);
+        dirs = reinterpret_cast<uint32_t *>(base + L.dir);
+        par = reinterpret_cast<uint32_t *>(base + L.par);
+        stage = base + L.stage;
+        hash = reinterpret_cast<uint32_t *>(base + L.hash);
+        bar = reinterpret_cast<uint64_t *>(base + L.bar);
+    }
+
+    // ---------------------------------------------------------- visited set
+    __device__ bool hash_insert(uint32_t v)
+    {
+        const uint32_t mask = (1u << a.hash_bits) - 1;
+        uint32_t h = (v * 2654435761u) >> (32 - a.hash_bits);
+        for (uint32_t probe = 0; probe <= mask; ++probe) {
+            const uint32_t old = atomicCAS(&hash[h], kEmpty, v);
+            if (old == kEmpty) return true;
+            if (old == v) return false;
+            h = (h + 1) & mask;
+        }
+        return true;  // unreachable: the table is never more than half full
+    }
+
+    __device__ void hash_clear()
+    {
+        const uint32_t H = 1u << a.hash_bits;
+        for (uint32_t i = lane; i < H; i += 32) hash[i] = kEmpty;
+        __syncwarp();
+        hash_count = 0;
+    }
+
+    // Forget everything but the queue (see the file comment for why the
+    // result cannot change).
+    __device__ void hash_reset()
+    {
+        hash_clear();
+        for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi[cur][i]);
+        __syncwarp();
+        hash_count = cnt;
+        st.hash_resets++;
+    }
+
+    __device__ void hash_make_room(uint32_t incoming)
+    {
+        if (hash_count + incoming > (1u << (a.hash_bits - 1))) hash_reset();
+    }
+
+    // ------------------------------------------------ bulk copies + waiting
+    // Every lane waits; the outcome is made warp-uniform so that the warp's
+    // later collectives never see a partial warp.
+    __device__ bool wait_copies()
+    {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase, a.err));
+        phase ^= 1;
+        if (!ok) {
+            failed = true;
+            // let the copies still in flight land before this warp leaves
+            mbar_wait_bounded(bar, phase ^ 1, a.err);
+            __syncwarp();
+        }
+        return ok;
+    }
+
+    // ----------------------------------------------------- evaluate rows
+    // Distances (and sign words) of candidates [0, nc) of view `v`.
+    template <int RST>
+    __device__ bool evaluate(const uint8_t *codes, const float *scales, uint32_t row_bytes, uint32_t nc,
+                             float *out_d, bool bits)
+    {
+        for (uint32_t b0 = 0; b0 < nc; b0 += kStageRows) {
+            const uint32_t rows = min(kStageRows, nc - b0);
+            uint32_t v = 0;
+            float scale = 1.0f;
+            if (lane == 0) {
+                fence_proxy_async();
+                mbar_arrive_expect_tx(bar, rows * row_bytes);
+            }
+            __syncwarp();
+            if (lane < rows) {
+                v = ci[b0 + lane];
+                bulk_g2s(stage + lane * a.stage_stride, codes + (uint64_t)v * row_bytes, row_bytes, bar);
+                if (RST != ANN_F32) scale = __ldg(scales + v);
+            }
+            if (!wait_copies()) return false;
+            if (lane < rows) {
+                const float dd = row_dist<RST>(stage + lane * a.stage_stride, q, scale, a.d,
+                                               cq + (b0 + lane) * a.w, bits);
+                out_d[b0 + lane] = dd;
+            }
+            __syncwarp();
+        }
+        return true;
+    }
+
+    // --------------------------------------------------------------- merge
+    // Rank-based merge of candidates [0, nc) into the queue, keeping the
+    // first lcap entries by (dist, id). New entries are UNEXPANDED.
+    __device__ void merge(uint32_t nc, uint32_t lcap)
+    {
+        const uint32_t s = cur, t = cur ^ 1, w = a.w;
+        const bool bits = a.want_bits;
+        for (uint32_t c = lane; c < nc; c += 32) {
+            const float kd = cd[c];
+            const uint32_t kid = ci[c];
+            uint32_t r = 0;
+            for (uint32_t c2 = 0; c2 < nc; ++c2) r += key_less(cd[c2], ci[c2], kd, kid);
+            uint32_t lo = 0, hi = cnt;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (key_less(bd[s][mid], bi[s][mid], kd, kid)) lo = mid + 1;
+                else hi = mid;
+            }
+            const uint32_t pos = r + lo;
+            if (pos < lcap) {
+                bd[t][pos] = kd;
+                bi[t][pos] = kid;
+                bs[t][pos] = kUnexpanded;
+                if (bits)
+                    for (uint32_t x = 0; x < w; ++x) bq[t][pos * w + x] = cq[c * w + x];
+            }
+        }
+        for (uint32_t b = lane; b < cnt; b += 32) {
+            const float kd = bd[s][b];
+            const uint32_t kid = bi[s][b];
+            uint32_t r = 0;
+            for (uint32_t c2 = 0; c2 < nc; ++c2) r += key_less(cd[c2], ci[c2], kd, kid);
+            const uint32_t pos = b + r;
+            if (pos < lcap) {
+                bd[t][pos] = kd;
+                bi[t][pos] = kid;
+                bs[t][pos] = bs[s][b];
+                if (bits)
+                    for (uint32_t x = 0; x < w; ++x) bq[t][pos * w + x] = bq[s][b * w + x];
+            }
+        }
+        cnt = min(lcap, cnt + nc);
+        cur = t;
+        __syncwarp();
+    }
+
+    // Collect a lane's id into the candidate list if it is new to the
+    // visited set; returns the warp's new count.
+    __device__ uint32_t collect(bool valid, uint32_t v, uint32_t nc)
+    {
+        const bool isnew = valid && hash_insert(v);
+        const uint32_t m = __ballot_sync(0xffffffffu, isnew);
+        if (isnew) ci[nc + __popc(m & lanemask_lt())] = v;
+        return nc + __popc(m);
+    }
+
+    // ------------------------------------------------------------- seeding
+    // Random seeds j = 0..m-1 (Step 2), deduplicated without redraw.
+    template <int RST>
+    __device__ bool seed_random(const View &v, uint32_t m, uint64_t tag, uint32_t lcap, uint32_t &rows)
+    {
+        for (uint32_t j0 = 0; j0 < m; j0 += a.cap_cand) {
+            const uint32_t chunk = min(a.cap_cand, m - j0);
+            hash_make_room(chunk);
+            uint32_t nc = 0;
+            for (uint32_t b = 0; b < chunk; b += 32) {
+                const bool valid = b + lane < chunk;
+                uint32_t id = 0;
+                if (valid) id = (uint32_t)(splitmix64(a.seed ^ tag ^ (qid << 32) ^ (uint64_t)(j0 + b + lane)) % v.n);
+                nc = collect(valid, id, nc);
+            }
+            __syncwarp();
+            hash_count += nc;
+            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, nc, cd, a.want_bits)) return false;
+            merge(nc, lcap);
+            rows += nc;
+        }
+        return true;
+    }
+
+    // Given ghost seeds (learned entry). Invalid or out-of-range ids are skipped.
+    template <int RST>
+    __device__ bool seed_given(const View &v, const uint32_t *ids, uint32_t m, uint32_t lcap, uint32_t &rows)
+    {
+        for (uint32_t j0 = 0; j0 < m; j0 += a.cap_cand) {
+            const uint32_t chunk = min(a.cap_cand, m - j0);
+            hash_make_room(chunk);
+            uint32_t nc = 0;
+            for (uint32_t b = 0; b < chunk; b += 32) {
+                uint32_t id = (b + lane < chunk) ? ids[j0 + b + lane] : kEmpty;
+                nc = collect(id < v.n, id, nc);
+            }
+            __syncwarp();
+            hash_count += nc;
+            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, nc, cd, a.want_bits)) return false;
+            merge(nc, lcap);
+            rows += nc;
+        }
+        return true;
+    }
+
+    // ---------------------------------------------------------- iterations
+    // Parents: the first `W` eligible queue entries in queue order.
+    __device__ uint32_t select_parents(uint32_t W, bool cool)
+    {
+        uint32_t np = 0;
+        for (uint32_t base = 0; base < cnt && np < W; base += 32) {
+            const uint32_t i = base + lane;
+            bool e = false;
+            if (i < cnt) {
+                const uint32_t s = bs[cur][i];
+                e = s == kUnexpanded || (cool && s == kPartial);
+            }
+            uint32_t m = __ballot_sync(0xffffffffu, e);
+            while (m && np < W) {
+                const uint32_t b = __ffs(m) - 1;
+                m &= m - 1;
+                if (lane == 0) par[np] = base + b;
+                ++np;
+            }
+        }
+        __syncwarp();
+        return np;
+    }
+
+    __device__ bool any_partial()
+    {
+        bool p = false;
+        for (uint32_t i = lane; i < cnt; i += 32) p |= bs[cur][i] == kPartial;
+        return __any_sync(0xffffffffu, p);
+    }
+
+    // Steps 3-4 repeated, with DGS and its cool-down (Section 3.3.2).
+    template <int RST>
+    __device__ bool iterate(const View &v, uint32_t lcap, uint32_t W, uint32_t T, uint32_t n_keep,
+                            uint32_t it_cool, uint32_t reexpand, uint32_t &c_iters, uint32_t &c_parents,
+                            uint32_t &c_dgs, uint32_t &c_rows)
+    {
+        const uint32_t deg = v.deg;
+        const bool dgs_on = v.dir != nullptr && n_keep < deg;
+        const uint32_t w = a.w;
+        bool cool = false;
+        for (uint32_t it = 0; it < T; ++it) {
+            if (dgs_on && it >= it_cool) cool = true;
+            uint32_t np = select_parents(W, cool);
+            if (np == 0 && dgs_on && reexpand && !cool && any_partial()) {
+                cool = true;
+                np = select_parents(W, cool);
+            }
+            if (np == 0) break;
+            ++c_iters;
+            const bool dgs_now = dgs_on && !cool;
+            // mark parents and fetch their adjacency (and direction) rows
+            const uint32_t adj_bytes = v.deg_pad * 4;
+            const uint32_t dir_bytes = v.deg_pad * w * 4;
+            uint32_t pid = 0;
+            if (lane < np) {
+                const uint32_t bidx = par[lane];
+                pid = bi[cur][bidx];
+                bs[cur][bidx] = (dgs_now && reexpand) ? kPartial : kExpanded;
+            }
+            if (lane == 0) {
+                fence_proxy_async();
+                mbar_arrive_expect_tx(bar, np * (adj_bytes + (dgs_now ? dir_bytes : 0)));
+            }
+            __syncwarp();
+            if (lane < np) {
+                bulk_g2s(adj + lane * v.deg_pad, v.graph + (uint64_t)pid * v.deg_pad, adj_bytes, bar);
+                if (dgs_now)
+                    bulk_g2s(dirs + lane * v.deg_pad * w, v.dir + (uint64_t)pid * v.deg_pad * w, dir_bytes, bar);
+            }
+            if (!wait_copies()) return false;
+            c_parents += np;
+            const uint32_t total = np * deg;
+            if (dgs_now) {
+                c_dgs += np;
+                // score = matching sign bits between the query's bits
+                // relative to the parent and the edge's stored bits
+                for (uint32_t e = lane; e < total; e += 32) {
+                    const uint32_t pi = e / deg, j = e - pi * deg;
+                    const uint32_t nb = adj[pi * v.deg_pad + j];
+                    int sc = -1;
+                    if (nb != ANN_INVALID_ID) {
+                        const uint32_t *qb = bq[cur] + par[pi] * w;
+                        const uint32_t *db = dirs + (pi * v.deg_pad + j) * w;
+                        int diff = 0;
+                        for (uint32_t x = 0; x < w; ++x) diff += __popc(qb[x] ^ db[x]);
+                        sc = (int)a.d - diff;
+                    }
+                    cs[e] = sc;
+                }
+                __syncwarp();
+                // keep the top n_keep per parent (ties: earlier adjacency slot)
+                for (uint32_t e = lane; e < total; e += 32) {
+                    const uint32_t pi = e / deg, j = e - pi * deg;
+                    const int sj = cs[e];
+                    uint32_t rank = 0;
+                    for (uint32_t i2 = 0; i2 < deg; ++i2) {
+                        const int si = cs[pi * deg + i2];
+                        rank += (si > sj) || (si == sj && i2 < j);
+                    }
+                    ck[e] = rank < n_keep;
+                }
+                __syncwarp();
+            }
+            hash_make_room(total);
+            uint32_t nc = 0;
+            for (uint32_t b = 0; b < total; b += 32) {
+                const uint32_t e = b + lane;
+                bool valid = e < total;
+                uint32_t nb = ANN_INVALID_ID;
+                if (valid) {
+                    const uint32_t pi = e / deg, j = e - pi * deg;
+                    nb = adj[pi * v.deg_pad + j];
+                    valid = nb != ANN_INVALID_ID && (!dgs_now || ck[e]);
+                }
+                nc = collect(valid, nb, nc);
+            }
+            __syncwarp();
+            hash_count += nc;
+            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, nc, cd, a.want_bits)) return false;
+            c_rows += nc;
+            merge(nc, lcap);
+        }
+        return true;
+    }
+
+    // ------------------------------------------------------------- a query
+    __device__ void run(uint32_t query)
+    {
+        qi = query;
+        qid = a.qid_base + query;
+        st = ann_query_stats{};
+        cnt = 0;
+        cur = 0;
+        const float *qg = a.queries + (uint64_t)qi * a.d;
+        const uint32_t dpad = (a.d + 31) & ~31u;
+        for (uint32_t i = lane; i < dpad; i += 32) q[i] = i < a.d ? qg[i] : 0.0f;
+        __syncwarp();
+        hash_clear();
+        bool ok = true;
+        const bool use_ghost = a.entry != ANN_ENTRY_RANDOM;
+        if (!use_ghost) {
+            ok = seed_random<ST>(a.base, a.m, 0, a.L, st.vec_rows);
+        } else {
+            const uint32_t *given = nullptr;
+            if (a.entry == ANN_ENTRY_GIVEN_GHOST && a.given) {
+                given = a.given + (uint64_t)qi * a.n_given;
+                if (given[0] == ANN_INVALID_ID) given = nullptr;  // fall back to random ghost seeds
+            }
+            uint32_t Tg = a.Tg;
+            if (given) {
+                Tg = a.Tg_given;
+                ok = seed_given<ST>(a.ghost, given, a.n_given, a.Lg, st.ghost_vec_rows);
+            } else {
+                ok = seed_random<ST>(a.ghost, a.ghost.deg, kGhostTag, a.Lg, st.ghost_vec_rows);
+            }
+            uint32_t no_dgs = 0;
+            if (ok)
+                ok = iterate<ST>(a.ghost, a.Lg, 1, Tg, a.ghost.deg, 0, 0, st.ghost_iters, st.ghost_parents,
+                                 no_dgs, st.ghost_vec_rows);
+            if (ok) {
+                // transition: the top g ghost results become the base queue;
+                // ghost ids are ascending, so the (dist, id) order carries over
+                const uint32_t g = min(min(a.g, cnt), a.L);
+                for (uint32_t i = lane; i < g; i += 32) {
+                    bi[cur][i] = __ldg(a.ghost_ids + bi[cur][i]);
+                    bs[cur][i] = kUnexpanded;
+                }
+                __syncwarp();
+                cnt = g;
+                hash_clear();
+                for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi[cur][i]);
+                __syncwarp();
+                hash_count = cnt;
+            }
+        }
+        if (ok)
+            ok = iterate<ST>(a.base, a.L, a.W, a.T, a.n_keep, a.it_cool, a.reexpand, st.iters, st.parents,
+                             st.dgs_parents, st.vec_rows);
+        uint32_t *oid = a.out_ids + (uint64_t)qi * a.k;
+        float *odist = a.out_dists + (uint64_t)qi * a.k;
+        if (ok && a.rerank) {
+            // FP32 distances of the whole queue on the originals, then sort
+            float *rd = bd[cur ^ 1];
+            for (uint32_t b0 = 0; b0 < cnt && ok; b0 += kStageRows) {
+                const uint32_t rows = min(kStageRows, cnt - b0);
+                for (uint32_t i = lane; i < rows; i += 32) ci[i] = bi[cur][b0 + i];
+                __syncwarp();
+                ok = evaluate<ANN_F32>(a.x32, nullptr, a.row32_bytes, rows, rd + b0, false);
+            }
+            st.rerank_rows += cnt;
+            if (ok) {
+                for (uint32_t e = lane; e < cnt; e += 32) {
+                    const float kd = rd[e];
+                    const uint32_t kid = bi[cur][e];
+                    uint32_t r = 0;
+                    for (uint32_t e2 = 0; e2 < cnt; ++e2) r += key_less(rd[e2], bi[cur][e2], kd, kid);
+                    if (r < a.k) {
+                        oid[r] = kid;
+                        odist[r] = kd;
+                    }
+                }
+                for (uint32_t j = cnt + lane; j < a.k; j += 32) {
+                    oid[j] = ANN_INVALID_ID;
+                    odist[j] = INFINITY;
+                }
+            }
+        } else if (ok) {
+            for (uint32_t j = lane; j < a.k; j += 32) {
+                oid[j] = j < cnt ? bi[cur][j] : ANN_INVALID_ID;
+                odist[j] = j < cnt ? bd[cur][j] : INFINITY;
+            }
+        }
+        if (!ok) {
+            for (uint32_t j = lane; j < a.k; j += 32) {
+                oid[j] = ANN_INVALID_ID;
+                odist[j] = INFINITY;
+            }
+            st.status = 1;
+        }
+        if (a.stats && lane == 0) a.stats[qi] = st;
+        __syncwarp();
+    }
+};
+
+template <int ST>
+__global__ void __launch_bounds__(128) search_kernel(const Args a)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *base = smem + (size_t)warp * a.lay.total;
+    WarpSearch<ST> ws(a, base);
+    if (lane == 0) mbar_init(ws.bar, 1);
+    fence_mbar_init();
+    __syncwarp();
+    while (true) {
+        uint32_t qi = 0;
+        if (lane == 0) qi = atomicAdd(a.counter, 1u);
+        qi = __shfl_sync(0xffffffffu, qi, 0);
+        if (qi >= a.nq) break;
+        ws.run(qi);
+        if (ws.failed) break;
+    }
+}
+
+uint32_t align16(uint32_t x) { return (x + 15) & ~15u; }
+
+Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, uint32_t par_cap,
+                   uint32_t adj_words, uint32_t dir_words, uint32_t stage_stride, uint32_t hash_bits)
+{
+    Layout L{};
+    uint32_t o = 0;
+    auto take = [&](uint32_t bytes) {
+        const uint32_t at = o;
+        o = align16(o + bytes);
+        return at;
+    };
+    L.q = take(((d + 31) & ~31u) * 4);
+    for (int s = 0; s < 2; ++s) {
+        L.bd[s] = take(cap_buf * 4);
+        L.bi[s] = take(cap_buf * 4);
+        L.bs[s] = take(cap_buf);
+        L.bq[s] = take(cap_buf * w * 4);
+    }
+    L.cd = take(cap_cand * 4);
+    L.ci = take(cap_cand * 4);
+    L.cq = take(cap_cand * w * 4);
+    L.cs = take(cap_cand * 4);
+    L.ck = take(cap_cand);
+    L.adj = take(adj_words * 4);
+    L.dir = take(dir_words * 4);
+    L.par = take(par_cap * 4);
+    L.stage = take(kStageRows * stage_stride);
+    L.hash = take((1u << hash_bits) * 4);
+    L.bar = take(16);
+    L.total = align16(o);
+    return L;
+}
+
+uint32_t next_pow2_bits(uint32_t x)
+{
+    uint32_t b = 0;
+    while ((1u << b) < x) ++b;
+    return b;
+}
+
+template <int ST>
+cudaError_t launch(const Args &a, int warps, int blocks, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    search_kernel<ST><<<blocks, warps * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int ST>
+int blocks_per_sm(int warps, size_t smem)
+{
+    int nb = 0;
+    cudaFuncSetAttribute(search_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<ST>, warps * 32, smem);
+    return nb;
+}
+
+}  // namespace
+
+namespace ann {
+
+// Validates parameters, derives the method's counts and launches the search.
+ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
+                         const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
+                         ann_query_stats *stats, cudaStream_t stream)
+{
+    if (!ix || !p) { set_error("ann_search: NULL index or params"); return ANN_EINVAL; }
+    const uint32_t L = p->itopk, W = p->search_width, deg = ix->degree;
+    if (p->k == 0 || p->k > L || L == 0 || L > ANN_MAX_ITOPK || W == 0 || W > ANN_MAX_WIDTH) {
+        set_error("ann_search: need 1 <= k <= itopk <= %u and 1 <= search_width <= %u", ANN_MAX_ITOPK,
+                  ANN_MAX_WIDTH);
+        return ANN_EINVAL;
+    }
+    if (!(p->dgs_discard >= 0.0f && p->dgs_discard < 1.0f) || !(p->dgs_cooldown >= 0.0f && p->dgs_cooldown <= 1.0f)) {
+        set_error("ann_search: dgs_discard must be in [0,1) and dgs_cooldown in [0,1]");
+        return ANN_EINVAL;
+    }
+    if (p->dgs_discard > 0.0f && !ix->dir) {
+        set_error("ann_search: DGS needs an index built with the direction table");
+        return ANN_EINVAL;
+    }
+    if (p->entry > ANN_ENTRY_GIVEN_GHOST || (p->entry != ANN_ENTRY_RANDOM && ix->n_ghost == 0)) {
+        set_error("ann_search: entry %u needs a ghost set", p->entry);
+        return ANN_EINVAL;
+    }
+    if (p->entry == ANN_ENTRY_GIVEN_GHOST && (!given || n_given == 0)) {
+        set_error("ann_search: given ghost seeds missing");
+        return ANN_EINVAL;
+    }
+    if (p->rerank && !ix->x32) {
+        set_error("ann_search: rerank needs the FP32 originals (keep_fp32)");
+        return ANN_EINVAL;
+    }
+    if (nq && (!queries || !ids || !dists)) {
+        set_error("ann_search: NULL queries or outputs");
+        return ANN_EINVAL;
+    }
+    const uint32_t Lg = p->ghost_itopk ? p->ghost_itopk : std::min(L, 64u);
+    if (Lg > ANN_MAX_ITOPK) {
+        set_error("ann_search: ghost_itopk > %u", ANN_MAX_ITOPK);
+        return ANN_EINVAL;
+    }
+    if (nq == 0) return ANN_OK;
+
+    Args a{};
+    a.base = View{(const uint8_t *)ix->codes, ix->scales, ix->row_bytes, ix->graph, deg, ix->deg_pad,
+                  ix->dir, (uint32_t)ix->n};
+    a.ghost = View{(const uint8_t *)ix->ghost_codes, ix->ghost_scales, ix->row_bytes, ix->ghost_graph,
+                   ix->ghost_degree, ix->gdeg_pad, nullptr, ix->n_ghost};
+    a.ghost_ids = ix->ghost_ids;
+    a.x32 = (const uint8_t *)ix->x32;
+    a.row32_bytes = ix->storage == ANN_F32 ? ix->row_bytes : ix->row32_bytes;
+    a.queries = queries;
+    a.nq = nq;
+    a.d = ix->dim;
+    a.w = ix->words;
+    a.given = given;
+    a.n_given = n_given;
+    a.out_ids = ids;
+    a.out_dists = dists;
+    a.stats = stats;
+    a.k = p->k;
+    a.L = L;
+    a.W = W;
+    a.T = p->max_iters;
+    a.m = p->num_seeds ? p->num_seeds : W * deg;
+    // Section 3.3.2 readings: keep n = deg - round(rho * deg) (at least 1);
+    // the cool-down is the last round(c * T) iterations (half-up, in double).
+    uint32_t n_keep = deg;
+    if (p->dgs_discard > 0.0f) {
+        const int64_t drop = (int64_t)std::floor((double)p->dgs_discard * deg + 0.5);
+        n_keep = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(deg, (int64_t)deg - drop));
+    }
+    a.n_keep = n_keep;
+    const int64_t n_cool = (int64_t)std::floor((double)p->dgs_cooldown * p->max_iters + 0.5);
+    a.it_cool = (uint32_t)std::max<int64_t>(0, (int64_t)p->max_iters - n_cool);
+    a.reexpand = p->dgs_reexpand ? 1 : 0;
+    a.entry = p->entry;
+    a.Lg = Lg;
+    a.Tg = p->ghost_max_iters;
+    a.Tg_given = p->ghost_max_iters_given;
+    a.g = p->ghost_seeds_out ? p->ghost_seeds_out : Lg;
+    a.rerank = p->rerank ? 1 : 0;
+    a.want_bits = (n_keep < deg) ? 1 : 0;
+    a.seed = p->seed;
+    a.qid_base = p->qid_base;
+    a.counter = ix->d_counter;
+    a.err = ix->d_error;
+
+    const uint32_t cap_buf = std::max(L, a.entry != ANN_ENTRY_RANDOM ? Lg : 1u);
+    uint32_t cap_cand = std::max(W * deg, 32u);
+    if (a.entry != ANN_ENTRY_RANDOM) cap_cand = std::max(cap_cand, ix->ghost_degree);
+    cap_cand = round_up(cap_cand, 32);
+    a.cap_cand = cap_cand;
+    const uint32_t adj_words = std::max(W * ix->deg_pad, ix->gdeg_pad);
+    const uint32_t dir_words = n_keep < deg ? W * ix->deg_pad * ix->words : 0;
+    const uint32_t stage_bytes = std::max(ix->row_bytes, a.rerank ? a.row32_bytes : 0u);
+    a.stage_stride = smem_row_stride(stage_bytes);
+    // visited table: at least twice (queue + one iteration's candidates), and
+    // room for a typical search's visits so resets stay rare
+    const uint32_t need = 2 * (cap_buf + cap_cand);
+    uint32_t hb = std::max(next_pow2_bits(need), next_pow2_bits(std::min(4096u, 32u * L)));
+    if (const char *env = getenv("ANN_HASH_BITS")) {
+        const int v = atoi(env);
+        if (v > 0 && (1u << v) >= need) hb = (uint32_t)v;
+    }
+    int warps = 4;
+    Layout lay{};
+    for (;;) {
+        lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, W, adj_words, dir_words, a.stage_stride, hb);
+        if ((size_t)lay.total * warps <= ix->smem_optin) break;
+        if (warps > 1) { warps /= 2; continue; }
+        if ((1u << (hb - 1)) >= need) { --hb; continue; }
+        set_error("ann_search: per-query state (%u bytes) exceeds shared memory", lay.total);
+        return ANN_EINVAL;
+    }
+    a.hash_bits = hb;
+    a.lay = lay;
+    const size_t smem = (size_t)lay.total * warps;
+    int nb = 0;
+    switch (ix->storage) {
+    case ANN_F32: nb = blocks_per_sm<ANN_F32>(warps, smem); break;
+    case ANN_F16: nb = blocks_per_sm<ANN_F16>(warps, smem); break;
+    default: nb = blocks_per_sm<ANN_E4M3>(warps, smem); break;
+    }
+    if (nb <= 0) {
+        set_error("ann_search: kernel does not fit on an SM (%zu bytes shared)", smem);
+        return ANN_EINVAL;
+    }
+    const uint64_t want = ((uint64_t)nq + warps - 1) / warps;
+    const int blocks = (int)std::min<uint64_t>(want, (uint64_t)nb * ix->num_sms);
+    ANN_CUDA(cudaMemsetAsync(ix->d_counter, 0, sizeof(uint32_t), stream));
+    cudaError_t e;
+    switch (ix->storage) {
+    case ANN_F32: e = launch<ANN_F32>(a, warps, blocks, smem, stream); break;
+    case ANN_F16: e = launch<ANN_F16>(a, warps, blocks, smem, stream); break;
+    default: e = launch<ANN_E4M3>(a, warps, blocks, smem, stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "search_kernel launch");
+    return ANN_OK;
+}
+
+}  // namespace ann
+
+extern "C" {
+
+ann_status ann_search(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
+                      const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists, ann_query_stats *stats,
+                      void *stream)
+{
+    if (!ix) { set_error("ann_search: NULL index"); return ANN_EINVAL; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ix->device) cudaSetDevice(ix->device);
+    ann_status s = search_launch(ix, queries, nq, p, given, n_given, ids, dists, stats, (cudaStream_t)stream);
+    if (prev >= 0 && prev != ix->device) cudaSetDevice(prev);
+    return s;
+}
+
+ann_status ann_search_host(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
+                           const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists, void *stream)
+{
+    if (!ix || !p) { set_error("ann_search_host: NULL index or params"); return ANN_EINVAL; }
+    if (nq == 0) return ANN_OK;
+    if (!queries || !ids || !dists) { set_error("ann_search_host: NULL buffers"); return ANN_EINVAL; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ix->device) cudaSetDevice(ix->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t qb = align16((uint32_t)0) + (size_t)nq * ix->dim * 4;
+    const size_t gb = (p->entry == ANN_ENTRY_GIVEN_GHOST && given) ? (size_t)nq * n_given * 4 : 0;
+    const size_t ob = (size_t)nq * p->k * 4;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t need = up(qb) + up(gb) + 2 * up(ob);
+    ann_status s = ANN_OK;
+    if (need > ix->ws_bytes) {
+        if (ix->ws) cudaFree(ix->ws);
+        ix->ws = nullptr;
+        ix->ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&ix->ws, need);
+        if (e != cudaSuccess) s = cuda_fail(e, "ann_search_host workspace");
+        else ix->ws_bytes = need;
+    }
+    if (s == ANN_OK) {
+        uint8_t *w = (uint8_t *)ix->ws;
+        float *dq = (float *)w;
+        uint32_t *dg = gb ? (uint32_t *)(w + up(qb)) : nullptr;
+        uint32_t *di = (uint32_t *)(w + up(qb) + up(gb));
+        float *dd = (float *)(w + up(qb) + up(gb) + up(ob));
+        cudaError_t e = cudaMemcpyAsync(dq, queries, qb, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && gb) e = cudaMemcpyAsync(dg, given, gb, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) s = cuda_fail(e, "ann_search_host upload");
+        if (s == ANN_OK) s = search_launch(ix, dq, nq, p, dg, n_given, di, dd, nullptr, st);
+        if (s == ANN_OK) {
+            e = cudaMemcpyAsync(ids, di, ob, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dists, dd, ob, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = cuda_fail(e, "ann_search_host download");
+        }
+    }
+    if (prev >= 0 && prev != ix->device) cudaSetDevice(prev);
+    return s;
+}
+
+}  // extern "C"
