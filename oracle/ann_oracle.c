@@ -462,11 +462,15 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
     or_graph base = {ix->n, ix->d, ix->deg, ix->Xs, NULL, ix->G, ix->dir};
     int use_ghost = (p->entry == OR_ENTRY_GHOST || p->entry == OR_ENTRY_GIVEN_GHOST) && ix->nS > 0;
     if (!use_ghost) {
-        /* Steps 1-3: m random nodes (counter-based splitmix64), deduplicated
-         * by the visited set without redraw, sorted into the queue. */
+        /* Steps 1-3: m random nodes, deduplicated by the visited set without
+         * redraw, sorted into the queue. Node j of query qid is
+         * splitmix64(key ^ (qid << 32) ^ j) mod n with key = splitmix64(seed):
+         * mixing the seed first keeps seeds that differ in low bits from
+         * drawing permutations of one seed set. */
+        const uint64_t key = oracle_splitmix64(p->seed);
         uint32_t nc = 0;
         for (uint32_t j = 0; j < m; ++j) {
-            uint64_t v = oracle_splitmix64(p->seed ^ (qid << 32) ^ (uint64_t)j) % ix->n;
+            uint64_t v = oracle_splitmix64(key ^ (qid << 32) ^ (uint64_t)j) % ix->n;
             if (bit_get(st.visited, v)) continue;
             bit_set(st.visited, v);
             st.tmp[nc].dist = dist_f32(q, ix->Xs + v * ix->d, ix->d);
@@ -496,8 +500,9 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
                 ++nc; ++cn.ghost_vec_rows;
             }
         } else {
+            const uint64_t gkey = oracle_splitmix64(p->seed ^ OR_GHOST_TAG);
             for (uint32_t j = 0; j < ix->deg_g; ++j) {
-                uint64_t v = oracle_splitmix64(p->seed ^ OR_GHOST_TAG ^ (qid << 32) ^ (uint64_t)j) % ix->nS;
+                uint64_t v = oracle_splitmix64(gkey ^ (qid << 32) ^ (uint64_t)j) % ix->nS;
                 if (bit_get(gvis, v)) continue;
                 bit_set(gvis, v);
                 st.tmp[nc] = (or_entry){dist_f32(q, row_of(&gg, v), ix->d), (uint32_t)v, OR_UNEXPANDED};

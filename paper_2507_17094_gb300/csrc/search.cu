@@ -357,10 +357,12 @@ struct WarpSearch {
     }
 
     // ------------------------------------------------------------- seeding
-    // Random seeds j = 0..m-1 (Step 2), deduplicated without redraw.
+    // Random seeds j = 0..m-1 (Step 2), deduplicated without redraw: node j
+    // is splitmix64(key ^ (qid << 32) ^ j) mod n, key = splitmix64(seed ^ tag).
     template <int RST>
     __device__ bool seed_random(const View &v, uint32_t m, uint64_t tag, uint32_t lcap, uint32_t &rows)
     {
+        const uint64_t key = splitmix64(a.seed ^ tag);
         for (uint32_t j0 = 0; j0 < m; j0 += a.cap_cand) {
             const uint32_t chunk = min(a.cap_cand, m - j0);
             hash_make_room(chunk);
@@ -368,7 +370,7 @@ struct WarpSearch {
             for (uint32_t b = 0; b < chunk; b += 32) {
                 const bool valid = b + lane < chunk;
                 uint32_t id = 0;
-                if (valid) id = (uint32_t)(splitmix64(a.seed ^ tag ^ (qid << 32) ^ (uint64_t)(j0 + b + lane)) % v.n);
+                if (valid) id = (uint32_t)(splitmix64(key ^ (qid << 32) ^ (uint64_t)(j0 + b + lane)) % v.n);
                 nc = collect(valid, id, nc);
             }
             __syncwarp();

@@ -11,8 +11,10 @@ lives here too.
 
 from .mixtures import Mixture, CONFIGS, WorkloadSpec, make_mixture, make_queries
 from .graph import knn_exact, knn_partitioned, prune_by_detours, build_graph, ghost_sample
+from .dataset import Dataset, load_dataset, write_index_file, cache_dir
 
 __all__ = [
     "Mixture", "CONFIGS", "WorkloadSpec", "make_mixture", "make_queries",
     "knn_exact", "knn_partitioned", "prune_by_detours", "build_graph", "ghost_sample",
+    "Dataset", "load_dataset", "write_index_file", "cache_dir",
 ]
