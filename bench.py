@@ -1,0 +1,499 @@
+#!/usr/bin/env python3
+"""Benchmark: batched graph beam search on one GB300 (PathWeaver's hot path).
+
+Metric: queries per second at recall@10 >= 0.95 (tie-aware, against the FP64
+exact kNN of the CPU oracle), on the 1M x 96-d workload (1,000 anisotropic
+Gaussians, L2-normalised, degree-64 graph, 10,000 queries, k = 10). The
+queue size itopk is swept over {32, 64, 128, 256} and the fastest setting
+reaching the recall target is timed.
+
+A step is one batched search of all queries: entry (ghost staging), the
+iterations with DGS, merges and output, in the library's search kernel,
+launched through the C ABI. Inputs are resident in HBM when the timed region
+starts; L2 is flushed between steps (a 256 MB write outside the timed
+events). ``e2e`` repeats the measurement through ann_search_host with host
+buffers, so host<->device copies are inside its timed region.
+
+``--impl reference`` times the CPU oracle (the same search, plain C, all host
+cores) on a bounded sample of the same workload and prints the same line.
+Under torchrun with N > 1 every rank searches its own replica and the value
+is the whole job's queries over the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10>=0.95 on 1 GB300: plain FP32 vs FP16/FP8+learned entry"
+UNIT = "queries/s"
+RECALL_TARGET = 0.95
+SWEEP = (32, 64, 128, 256)
+KERNEL_SOURCES = ("paper_2507_17094_gb300/csrc/search.cu", "paper_2507_17094_gb300/csrc/ann_internal.cuh")
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The slowest rank's time (the job finishes with it)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value: float, dist, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, form: str):
+    """DRAM bytes per launch of the search kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(workload, {}).get(form)
+        if e and e.get("kernel_hash") == kernel_hash():
+            return e
+    except (ValueError, OSError):
+        return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ forms
+def forms_for(spec):
+    """Search configurations compared (each swept over itopk)."""
+    base = dict(k=10, search_width=1, dgs_cooldown=0.3, ghost_max_iters=16)
+    return {
+        # the paper's method: ghost staging + DGS, FP32 storage (headline)
+        "paper_fp32": dict(storage=0, entry=1, dgs_discard=0.5, rerank=0, **base),
+        # the method without its two techniques (CAGRA-style random entry)
+        "plain_fp32": dict(storage=0, entry=0, dgs_discard=0.0, rerank=0, **base),
+        # low-precision storage with FP32 rerank of the final queue
+        "f16_rerank": dict(storage=1, entry=1, dgs_discard=0.5, rerank=1, **base),
+        "e4m3_rerank": dict(storage=2, entry=1, dgs_discard=0.5, rerank=1, **base),
+    }
+
+
+def params_for(form: dict, L: int, seed: int) -> dict:
+    p = {k: v for k, v in form.items() if k != "storage"}
+    p.update(itopk=L, max_iters=2 * L // form["search_width"] + 32, seed=seed)
+    return p
+
+
+def algorithmic_bytes(st, spec, storage: int, rerank: bool) -> np.ndarray:
+    """Bytes the search must move per query (from the kernel's own exact
+    counters): query + adjacency rows + direction rows + gathered vector rows
+    (ghost and base, with the per-vector scale) + FP32 rerank rows + results."""
+    d, deg, k = spec.d, spec.degree, 10
+    w = (d + 31) // 32
+    eb = {0: 4, 1: 2, 2: 1}[storage]
+    row = d * eb + (4 if storage else 0)
+    return (4 * d + st["parents"].astype(np.int64) * 4 * deg
+            + st["dgs_parents"].astype(np.int64) * 4 * deg * w
+            + st["vec_rows"].astype(np.int64) * row
+            + st["ghost_parents"].astype(np.int64) * 4 * spec.ghost_degree
+            + st["ghost_vec_rows"].astype(np.int64) * row
+            + st["rerank_rows"].astype(np.int64) * 4 * d * (1 if rerank else 0)
+            + 8 * k)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import oracle as O
+    import paper_2507_17094_gb300 as A
+    from workloads import CONFIGS, load_dataset
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    spec = CONFIGS[args.workload]
+    if args.nq:
+        import dataclasses
+        spec = dataclasses.replace(spec, nq=args.nq)
+    verbose = rank == 0 and args.verbose
+    A.build()
+    ds = load_dataset(spec, device=dev, verbose=verbose)
+    forms = forms_for(spec)
+    headline = "paper_fp32"
+    seed = spec.seeds["search"]
+
+    gt_sample = min(args.gt_sample, spec.nq)
+    cpu = None
+    gt_ids = gt_d = None
+    if rank == 0:
+        # ground truth first: the recall sweep needs it
+        import oracle as O2
+        t0 = time.time()
+        gt_ids, gt_d = O2.knn_f64(ds.X, ds.Q[:gt_sample], 10)
+        if verbose:
+            print(f"[bench] FP64 ground truth ({gt_sample} queries) in {time.time() - t0:.1f}s",
+                  file=sys.stderr, flush=True)
+
+    indexes = {}
+
+    def index_for(storage):
+        if storage not in indexes:
+            indexes[storage] = A.Index(ds.X, ds.G, storage=storage, ghost_ids=ds.S, ghost_graph=ds.Gg,
+                                       keep_fp32=True, build_dir=True, device=local)
+        return indexes[storage]
+
+    Qd = torch.from_numpy(ds.Q).to(dev)
+    nq = Qd.shape[0]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def timed_steps(ix, params, steps, warm, out):
+        for _ in range(warm):
+            ix.search(Qd, stream=stream, out=out, **params)
+        torch.cuda.synchronize(dev)
+        times = []
+        for _ in range(steps):
+            flush.add_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ix.search(Qd, stream=stream, out=out, **params)
+            e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        return [a.elapsed_time(b) for a, b in times]
+
+    out = (torch.empty((nq, 10), dtype=torch.int32, device=dev), torch.empty((nq, 10), device=dev))
+    results = {}
+    for name, form in forms.items():
+        if args.forms and name not in args.forms.split(","):
+            continue
+        ix = index_for(form["storage"])
+        sweep = []
+        chosen = None
+        for L in SWEEP:
+            p = params_for(form, L, seed)
+            ids, dists, _ = ix.search(Qd, stream=stream, out=out, **p)
+            ms = statistics.median(timed_steps(ix, p, 3, 1, out))
+            rec = None
+            if rank == 0:
+                a_ids = ids[:gt_sample].cpu().numpy().view(np.uint32)
+                rec = O.recall_at_k(a_ids, gt_ids, gt_d, ds.X, ds.Q[:gt_sample], 10)
+            rec = float(max_over_ranks(rec[0] if rec else 0.0, dist, dev))
+            sweep.append({"itopk": L, "recall": rec, "ms": ms, "qps": nq / (ms / 1e3)})
+            if chosen is None and rec >= RECALL_TARGET:
+                chosen = L
+        if chosen is None:
+            chosen = max(sweep, key=lambda s: s["recall"])["itopk"]
+        results[name] = {"storage": {0: "f32", 1: "f16", 2: "e4m3"}[form["storage"]],
+                         "entry": {0: "random", 1: "ghost", 2: "learned"}[form["entry"]],
+                         "dgs_discard": form["dgs_discard"], "rerank": bool(form["rerank"]),
+                         "itopk": chosen, "sweep": sweep}
+        if verbose:
+            print(f"[bench] {name}: " + ", ".join(f"L{s['itopk']} r={s['recall']:.3f} "
+                                                   f"{s['qps'] / 1e6:.2f}M/s" for s in sweep),
+                  file=sys.stderr, flush=True)
+
+    # ---------------------------------------------------- the timed region
+    form = forms[headline]
+    ix = index_for(form["storage"])
+    L = results[headline]["itopk"]
+    p = params_for(form, L, seed)
+    ids, dists, st = ix.search(Qd, stream=stream, stats=True, **p)
+    torch.cuda.synchronize(dev)
+    ix.sync()
+    st_np = A.stats_to_numpy(st)
+    bytes_per_launch = float(algorithmic_bytes(st_np, spec, form["storage"], bool(form["rerank"])).sum())
+    head_recall = next(s["recall"] for s in results[headline]["sweep"] if s["itopk"] == L)
+
+    for _ in range(args.warmup):
+        ix.search(Qd, stream=stream, out=out, **p)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    step_ms = timed_steps(ix, p, args.steps, 0, out)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    total_queries = sum_over_ranks(float(nq * args.steps), dist, dev)
+    value = total_queries / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+    mean_launch_s = statistics.mean(step_ms) / 1e3
+    ix.sync()
+
+    # other forms at their chosen itopk (a few steps each, reported beside)
+    for name, r in results.items():
+        f = forms[name]
+        ixf = index_for(f["storage"])
+        pf = params_for(f, r["itopk"], seed)
+        _, _, stf = ixf.search(Qd, stream=stream, stats=True, **pf)
+        torch.cuda.synchronize(dev)
+        stn = A.stats_to_numpy(stf)
+        ms = statistics.median(timed_steps(ixf, pf, max(5, args.steps // 10), 2, out))
+        b = float(algorithmic_bytes(stn, spec, f["storage"], bool(f["rerank"])).sum())
+        r.update(qps=nq / (ms / 1e3), ms_per_step=ms, recall=next(s["recall"] for s in r["sweep"]
+                                                                   if s["itopk"] == r["itopk"]),
+                 gbs=b / (ms / 1e3) / 1e9, hbm_frac=(b / (ms / 1e3) / 1e9) / measured_peaks()["hbm_gbs"],
+                 mean_vec_rows=float(stn["vec_rows"].mean()), mean_iters=float(stn["iters"].mean()),
+                 hash_resets=int(stn["hash_resets"].sum()))
+        del r["sweep"]
+
+    # ------------------------------------------------------------ e2e (host buffers)
+    Qh = torch.from_numpy(ds.Q).pin_memory().numpy()
+    e2e_steps = max(3, min(args.steps, 50))
+    ix.search_host(Qh, **p)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ix.search_host(Qh, **p)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_value = sum_over_ranks(float(nq * e2e_steps), dist, dev) / e2e_s
+
+    # ------------------------------------------------------------ CPU baseline (rank 0, N = 1 only)
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sample = min(args.cpu_sample, spec.nq)
+        oi = O.OracleIndex(ds.X, ds.G, form["storage"], ds.S, ds.Gg)
+        cores = O.default_threads()
+        t0 = time.perf_counter()
+        o_ids, o_d, o_c = O.search(oi, ds.Q[:sample], threads=cores, **p)
+        dt = time.perf_counter() - t0
+        g_ids = ids[:sample].cpu().numpy().view(np.uint32)
+        match = float((g_ids == o_ids).mean())
+        cpu_baseline = {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                        "sample": f"{sample} of the {spec.nq} queries, same search parameters "
+                                  f"(itopk {L}), plain-C oracle on all host cores, {dt:.2f} s",
+                        "ids_match_gpu": match}
+
+    peaks = measured_peaks()
+    achieved = bytes_per_launch / mean_launch_s / 1e9
+    tr = ncu_traffic(spec.name, headline)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "kernel": "search_kernel<F32>"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Gaussian mixture; no dataset files)",
+        "config": {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "nq": nq,
+                   "k": 10, "itopk": L, "search_width": 1, "max_iters": p["max_iters"], "entry": "ghost",
+                   "ghost_n": spec.ghost_n, "dgs_discard": 0.5, "dgs_cooldown": 0.3, "storage": "f32",
+                   "recall_at_10": head_recall, "recall_target": RECALL_TARGET,
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "parallelism": f"replicas x{world}"},
+        "forms": results,
+        "roofline": roofline,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nq * spec.d * 4),
+                "d2h_bytes_per_step": int(nq * 10 * 8), "steps": e2e_steps,
+                "api": "ann_search_host (pinned host buffers)"},
+        "gpu_launches": args.steps,
+        "cpu_baseline": cpu_baseline,
+    }
+    for ix_ in indexes.values():
+        ix_.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from workloads import CONFIGS, load_dataset
+    spec = CONFIGS[args.workload]
+    if args.nq:
+        import dataclasses
+        spec = dataclasses.replace(spec, nq=args.nq)
+    dev = None
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+    except ImportError:
+        pass
+    ds = load_dataset(spec, device=dev, verbose=args.verbose)   # input generation only
+    form = forms_for(spec)["paper_fp32"]
+    seed = spec.seeds["search"]
+    sample = min(args.cpu_sample, spec.nq)
+    gt_sample = min(args.gt_sample, sample)
+    gt_ids, gt_d = O.knn_f64(ds.X, ds.Q[:gt_sample], 10)
+    oi = O.OracleIndex(ds.X, ds.G, form["storage"], ds.S, ds.Gg)
+    cores = O.default_threads()
+    chosen, rec_at = None, None
+    for L in SWEEP:
+        p = params_for(form, L, seed)
+        ids, _, _ = O.search(oi, ds.Q[:gt_sample], threads=cores, **p)
+        rec = O.recall_at_k(ids, gt_ids, gt_d, ds.X, ds.Q[:gt_sample], 10)[0]
+        if rec >= RECALL_TARGET:
+            chosen, rec_at = L, rec
+            break
+    if chosen is None:
+        chosen, rec_at = SWEEP[-1], rec
+    p = params_for(form, chosen, seed)
+    Qs = ds.Q[:sample]
+    for _ in range(args.warmup):
+        O.search(oi, Qs, threads=cores, **p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.search(oi, Qs, threads=cores, **p)
+    dt = time.perf_counter() - t0
+    value = sample * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+            "config": {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree,
+                       "nq": sample, "k": 10, "itopk": chosen, "search_width": 1, "max_iters": p["max_iters"],
+                       "entry": "ghost", "dgs_discard": 0.5, "storage": "f32", "recall_at_10": rec_at},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} queries per step of the {spec.nq}-query workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--nq", type=int, default=0)
+    ap.add_argument("--forms", default="")
+    ap.add_argument("--gt-sample", type=int, default=1000)
+    ap.add_argument("--cpu-sample", type=int, default=2000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("-v", "--verbose", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -161,6 +161,44 @@ ann_status ann_encode(const float *x, uint64_t n, uint32_t dim, ann_storage stor
 ann_status ann_dir_table(const void *vectors, const float *scales, ann_storage storage, uint64_t n,
                          uint32_t dim, const uint32_t *graph, uint32_t degree, uint32_t *dir, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned entry (not in the paper; builds on the ghost set of Section
+ * 3.2.2): an MLP in_dim -> hidden1 -> hidden2 -> out_dim (ReLU, one logit
+ * per ghost node), BF16 tensor-core GEMMs with FP32 accumulation, FP32
+ * master weights trained with AdamW on softmax cross-entropy. Its top-P
+ * ghost nodes become `given_seeds` of ann_search (ANN_ENTRY_GIVEN_GHOST).
+ * All sizes must be positive multiples of 8. Weights are row-major
+ * (W1: hidden1 x in_dim, W2: hidden2 x hidden1, W3: out_dim x hidden2).
+ * ------------------------------------------------------------------------ */
+typedef struct ann_mlp ann_mlp;
+
+ann_status ann_mlp_create(int device, uint32_t in_dim, uint32_t hidden1, uint32_t hidden2, uint32_t out_dim,
+                          uint32_t max_batch, ann_mlp **out);
+ann_status ann_mlp_free(ann_mlp *mlp);
+/* Host FP32 parameters in; resets the optimizer state and the step count. */
+ann_status ann_mlp_set_params(ann_mlp *mlp, const float *W1, const float *b1, const float *W2, const float *b2,
+                              const float *W3, const float *b3);
+/* Host copies of the parameters (which = 0) or of the last training step's
+ * gradients (which = 1); a NULL pointer skips that array. Synchronises. */
+ann_status ann_mlp_get(const ann_mlp *mlp, int which, float *W1, float *b1, float *W2, float *b2, float *W3,
+                       float *b3);
+/* logits (device, n x out_dim FP32) of queries x (device, n x in_dim FP32); n <= max_batch. */
+ann_status ann_mlp_forward(ann_mlp *mlp, const float *x, uint32_t n, float *logits, void *stream);
+/* One AdamW step on a minibatch: x (device, n x in_dim), labels (device, n
+ * indices < out_dim), n a multiple of 8 <= max_batch; the batch's mean
+ * cross-entropy goes to *loss (device float, may be NULL). */
+ann_status ann_mlp_train_step(ann_mlp *mlp, const float *x, const uint32_t *labels, uint32_t n, float lr,
+                              float beta1, float beta2, float eps, float weight_decay, float *loss, void *stream);
+/* Fused prediction: seeds (device, n x P) = the P highest-logit ghost indices
+ * (ties: smaller index), pmax (device, n, may be NULL) = the largest softmax
+ * probability; a query with pmax < tau gets ANN_INVALID_ID as its first seed
+ * (ann_search then falls back to random ghost seeds). 1 <= P <= 8. The
+ * (n x out_dim) logits are never written to memory. */
+ann_status ann_mlp_predict(ann_mlp *mlp, const float *x, uint32_t n, uint32_t P, float tau, uint32_t *seeds,
+                           float *pmax, void *stream);
+/* Synchronise `stream` and report (then clear) the MLP's device error word. */
+ann_status ann_mlp_sync(ann_mlp *mlp, void *stream);
+
 /* Thread-local message for the last failing call on this thread. */
 const char *ann_last_error(void);
 

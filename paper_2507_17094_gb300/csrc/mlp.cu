@@ -1,0 +1,828 @@
+// Learned entry (not in the paper): an MLP that maps a query to logits over
+// the ghost set (Section 3.2.2), trained on the method's own ghost-staging
+// results, whose top-P ghost nodes seed the ghost stage.
+//
+// Dense contractions run on the 5th-generation tensor cores: one GEMM kernel
+// computes C = A * B^T with A (M x K) and B (N x K) both K-major BF16 in
+// global memory, FP32 accumulation in tensor memory:
+//   - TMA 2-D loads (128-byte swizzle) fill a 4-stage shared-memory ring,
+//     one elected thread issues them; full/empty mbarriers link the stages;
+//   - one elected thread issues tcgen05.mma (M 128, N 128, K 16 per
+//     instruction) reading both operands from shared memory by descriptor;
+//     tcgen05.commit frees a stage when the MMAs reading it are done;
+//   - the accumulator (128 lanes x 128 columns) is read back with
+//     tcgen05.ld by all four warps for the epilogue: plain FP32, bias,
+//     bias + ReLU to BF16, or a fused top-P + online-softmax reduction so
+//     inference never writes the (queries x ghosts) logits.
+// Every mbarrier wait is bounded; on expiry the kernel records a timeout in
+// the error word, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "ann_internal.cuh"
+
+using namespace ann;
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int TILE_A = BM * BK * 2;
+constexpr int TILE_B = BN * BK * 2;
+constexpr int GEMM_SMEM = STAGES * (TILE_A + TILE_B) + 1024 + 256;
+constexpr int TOPP = 8;   // top-P of the fused inference epilogue
+
+enum { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_RELU_BF16 = 2, EPI_TOPP = 3 };
+
+struct EpiArgs {
+    float *c;                 // FP32 output, row stride ldc
+    __nv_bfloat16 *cb;        // BF16 output, row stride ldc
+    const float *bias;        // per output column
+    uint32_t ldc;
+    float *part;              // top-P partials: per (row, column tile) TOPP values, TOPP ids, max, sum
+    uint32_t ntiles;
+    int *err;
+};
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand in the 128-byte swizzle
+// layout TMA writes: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
+    d |= (uint64_t)1 << 16;                           // leading byte offset (unused in this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                           // descriptor version of this architecture
+    d |= (uint64_t)2 << 61;                           // swizzle: 128 bytes
+    return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M 128, N BN.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t m, uint32_t n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ bool better(float va, uint32_t ia, float vb, uint32_t ib)
+{
+    return va > vb || (va == vb && ia < ib);
+}
+
+// ------------------------------------------------------------------ GEMM
+template <int EPI>
+__global__ void __launch_bounds__(128, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, uint32_t M,
+                uint32_t N, uint32_t K, EpiArgs e)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t pad = (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;
+    uint8_t *smem = smem_raw + pad;
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * TILE_A;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * (TILE_A + TILE_B));
+    uint64_t *empty = full + STAGES;
+    uint64_t *accb = empty + STAGES;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accb + 1);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const uint32_t nkb = (K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer: TMA tiles of A and B into the ring
+        for (uint32_t kb = 0; kb < nkb; ++kb) {
+            const uint32_t s = kb % STAGES, r = kb / STAGES;
+            if (!mbar_wait_bounded(&empty[s], (r & 1) ^ 1, e.err)) break;
+            mbar_arrive_expect_tx(&full[s], TILE_A + TILE_B);
+            tma_load_2d(sA + s * TILE_A, &tA, (int)(kb * BK), (int)m0, &full[s]);
+            tma_load_2d(sB + s * TILE_B, &tB, (int)(kb * BK), (int)n0, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(BM, BN);
+        bool ok = true;
+        for (uint32_t kb = 0; kb < nkb && ok; ++kb) {
+            const uint32_t s = kb % STAGES, r = kb / STAGES;
+            ok = mbar_wait_bounded(&full[s], r & 1, e.err);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t a0 = smem_addr(sA + s * TILE_A), b0 = smem_addr(sB + s * TILE_B);
+#pragma unroll
+            for (uint32_t k = 0; k < BK / 16; ++k)
+                mma_bf16(tmem, desc_sw128(a0 + k * 32), desc_sw128(b0 + k * 32), idesc, (kb | k) != 0);
+            mma_commit(&empty[s]);
+        }
+        mma_commit(accb);
+    }
+    __syncwarp();
+
+    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
+    const bool ok = mbar_wait_bounded(accb, 0, e.err);
+    tc_fence_after();
+    const uint32_t row = warp * 32 + lane;
+    const uint32_t m = m0 + row;
+    float tv[TOPP];
+    uint32_t ti[TOPP];
+    float mx = -INFINITY, sm = 0.0f;
+    if (EPI == EPI_TOPP) {
+#pragma unroll
+        for (int p = 0; p < TOPP; ++p) { tv[p] = -INFINITY; ti[p] = 0xFFFFFFFFu; }
+    }
+    if (ok) {
+#pragma unroll 1
+        for (uint32_t c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            __syncwarp();
+            tmem_ld32(tmem + ((warp * 32u) << 16) + c0, v);
+            const uint32_t nb = n0 + c0;
+            if (m >= M) {
+                // rows past M: nothing to store
+            } else if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
+                float *out = e.c + (size_t)m * e.ldc + nb;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (nb + j < N) out[j] = v[j] + (EPI == EPI_BIAS_F32 ? e.bias[nb + j] : 0.0f);
+            } else if (EPI == EPI_BIAS_RELU_BF16) {
+                __nv_bfloat16 *out = e.cb + (size_t)m * e.ldc + nb;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (nb + j < N) out[j] = __float2bfloat16_rn(fmaxf(v[j] + e.bias[nb + j], 0.0f));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t n = nb + j;
+                    if (n >= N) continue;
+                    const float x = v[j] + e.bias[n];
+                    if (x > mx) {
+                        sm = sm * __expf(mx - x) + 1.0f;
+                        mx = x;
+                    } else {
+                        sm += __expf(x - mx);
+                    }
+                    if (better(x, n, tv[TOPP - 1], ti[TOPP - 1])) {
+                        tv[TOPP - 1] = x;
+                        ti[TOPP - 1] = n;
+#pragma unroll
+                        for (int p = TOPP - 1; p > 0; --p) {
+                            if (better(tv[p], ti[p], tv[p - 1], ti[p - 1])) {
+                                const float t = tv[p]; tv[p] = tv[p - 1]; tv[p - 1] = t;
+                                const uint32_t u = ti[p]; ti[p] = ti[p - 1]; ti[p - 1] = u;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (EPI == EPI_TOPP && m < M) {
+            float *o = e.part + ((size_t)m * e.ntiles + blockIdx.x) * (2 * TOPP + 2);
+#pragma unroll
+            for (int p = 0; p < TOPP; ++p) {
+                o[p] = tv[p];
+                o[TOPP + p] = __uint_as_float(ti[p]);
+            }
+            o[2 * TOPP] = mx;
+            o[2 * TOPP + 1] = sm;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ helpers
+__global__ void to_bf16_kernel(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// out (C x R) = in (R x C)^T, BF16, 32 x 32 tiles through shared memory
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out,
+                                      uint32_t R, uint32_t C)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const uint32_t c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (uint32_t i = threadIdx.y; i < 32; i += blockDim.y) {
+        const uint32_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[i][threadIdx.x] = in[(size_t)r * C + c];
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.y; i < 32; i += blockDim.y) {
+        const uint32_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[(size_t)c * R + r] = t[threadIdx.x][i];
+    }
+}
+
+// g' = g * [mask > 0] (mask optional), as BF16 (optional) and BF16^T (optional)
+__global__ void post_grad_kernel(const float *__restrict__ g, const __nv_bfloat16 *__restrict__ mask,
+                                 float *__restrict__ gm, __nv_bfloat16 *__restrict__ gb,
+                                 __nv_bfloat16 *__restrict__ gT, uint32_t R, uint32_t C)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const uint32_t c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (uint32_t i = threadIdx.y; i < 32; i += blockDim.y) {
+        const uint32_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) {
+            const size_t at = (size_t)r * C + c;
+            float v = g[at];
+            if (mask && !(__bfloat162float(mask[at]) > 0.0f)) v = 0.0f;
+            if (gm) gm[at] = v;
+            const __nv_bfloat16 b = __float2bfloat16_rn(v);
+            if (gb) gb[at] = b;
+            t[i][threadIdx.x] = b;
+        }
+    }
+    if (!gT) return;
+    __syncthreads();
+    for (uint32_t i = threadIdx.y; i < 32; i += blockDim.y) {
+        const uint32_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) gT[(size_t)c * R + r] = t[threadIdx.x][i];
+    }
+}
+
+// Column sums of an R x C FP32 matrix, rows in order (deterministic).
+__global__ void colsum_kernel(const float *__restrict__ g, float *__restrict__ out, uint32_t R, uint32_t C)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.0f;
+    for (uint32_t r = 0; r < R; ++r) s += g[(size_t)r * C + c];
+    out[c] = s;
+}
+
+// Row-wise softmax cross-entropy over z (B x N): z <- (softmax(z) - onehot(y)) / B,
+// loss += mean_i(logsumexp(z_i) - z_i[y_i]). One warp per row.
+__global__ void softmax_ce_kernel(float *__restrict__ z, const uint32_t *__restrict__ y, uint32_t B, uint32_t N,
+                                  float *__restrict__ loss)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= B) return;
+    float *zr = z + (size_t)r * N;
+    float mx = -INFINITY;
+    for (uint32_t c = lane; c < N; c += 32) mx = fmaxf(mx, zr[c]);
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float s = 0.0f;
+    for (uint32_t c = lane; c < N; c += 32) s += expf(zr[c] - mx);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float lse = mx + logf(s);
+    const uint32_t yr = y[r];
+    const float zy = zr[yr];
+    const float inv = 1.0f / (float)B;
+    for (uint32_t c = lane; c < N; c += 32) zr[c] = (expf(zr[c] - lse) - (c == yr ? 1.0f : 0.0f)) * inv;
+    if (lane == 0) atomicAdd(loss, (lse - zy) * inv);
+}
+
+struct AdamHP {
+    float lr, b1, b2, eps, wd, c1, c2;
+};
+
+// AdamW (decoupled weight decay) on FP32 masters; refreshes the BF16 copy.
+__global__ void adamw_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                             float *__restrict__ v, __nv_bfloat16 *__restrict__ wb, size_t n, AdamHP h)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = h.b1 * m[i] + (1.0f - h.b1) * gi;
+        const float vi = h.b2 * v[i] + (1.0f - h.b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - h.lr * ((mi / h.c1) / (sqrtf(vi / h.c2) + h.eps) + h.wd * w[i]);
+        w[i] = wi;
+        if (wb) wb[i] = __float2bfloat16_rn(wi);
+    }
+}
+
+// Merge the per-tile top-P partials of each row; seeds = ghost ids of the
+// top P (ties: smaller id), pmax = the largest softmax probability; a row
+// with pmax < tau gets ANN_INVALID_ID as its first seed (fall back to
+// random ghost seeds). One warp per row.
+__global__ void topp_merge_kernel(const float *__restrict__ part, uint32_t M, uint32_t ntiles, uint32_t P,
+                                  float tau, uint32_t *__restrict__ seeds, float *__restrict__ pmax)
+{
+    __shared__ float sv[4][32 * TOPP];
+    __shared__ uint32_t si[4][32 * TOPP];
+    const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const uint32_t r = blockIdx.x * 4 + wl;
+    if (r >= M) return;
+    float tv[TOPP];
+    uint32_t ti[TOPP];
+#pragma unroll
+    for (int p = 0; p < TOPP; ++p) { tv[p] = -INFINITY; ti[p] = 0xFFFFFFFFu; }
+    float mx = -INFINITY, sm = 0.0f;
+    for (uint32_t t = lane; t < ntiles; t += 32) {
+        const float *o = part + ((size_t)r * ntiles + t) * (2 * TOPP + 2);
+        const float tm = o[2 * TOPP], ts = o[2 * TOPP + 1];
+        if (ts > 0.0f) {
+            if (tm > mx) { sm = sm * __expf(mx - tm) + ts; mx = tm; }
+            else sm += ts * __expf(tm - mx);
+        }
+        for (int p = 0; p < TOPP; ++p) {
+            const float x = o[p];
+            const uint32_t n = __float_as_uint(o[TOPP + p]);
+            if (n == 0xFFFFFFFFu || !better(x, n, tv[TOPP - 1], ti[TOPP - 1])) continue;
+            tv[TOPP - 1] = x;
+            ti[TOPP - 1] = n;
+#pragma unroll
+            for (int q = TOPP - 1; q > 0; --q)
+                if (better(tv[q], ti[q], tv[q - 1], ti[q - 1])) {
+                    const float a = tv[q]; tv[q] = tv[q - 1]; tv[q - 1] = a;
+                    const uint32_t u = ti[q]; ti[q] = ti[q - 1]; ti[q - 1] = u;
+                }
+        }
+    }
+    // softmax normaliser across lanes
+    float gm = mx;
+    for (int o = 16; o; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    float gs = (sm > 0.0f) ? sm * __expf(mx - gm) : 0.0f;
+    for (int o = 16; o; o >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, o);
+    // top-P across lanes by rank
+#pragma unroll
+    for (int p = 0; p < TOPP; ++p) {
+        sv[wl][lane * TOPP + p] = tv[p];
+        si[wl][lane * TOPP + p] = ti[p];
+    }
+    __syncwarp();
+    for (uint32_t e = lane; e < 32 * TOPP; e += 32) {
+        const float x = sv[wl][e];
+        const uint32_t n = si[wl][e];
+        if (n == 0xFFFFFFFFu) continue;
+        uint32_t rank = 0;
+        for (uint32_t f = 0; f < 32 * TOPP; ++f)
+            rank += si[wl][f] != 0xFFFFFFFFu && better(sv[wl][f], si[wl][f], x, n);
+        if (rank < P) seeds[(size_t)r * P + rank] = n;
+    }
+    __syncwarp();
+    const float pm = gs > 0.0f ? 1.0f / gs : 0.0f;
+    if (lane == 0) {
+        if (pmax) pmax[r] = pm;
+        if (pm < tau) seeds[(size_t)r * P] = ANN_INVALID_ID;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+struct ann_mlp {
+    int device = 0;
+    uint32_t d = 0, h1 = 0, h2 = 0, out = 0, maxb = 0;
+    float *W[3] = {}, *b[3] = {}, *mW[3] = {}, *vW[3] = {}, *mb[3] = {}, *vb[3] = {}, *gW[3] = {}, *gb[3] = {};
+    __nv_bfloat16 *Wb[3] = {}, *WT[3] = {};
+    __nv_bfloat16 *xb = nullptr, *xT = nullptr, *h1b = nullptr, *h1T = nullptr, *h2b = nullptr, *h2T = nullptr;
+    __nv_bfloat16 *dzb = nullptr, *dzT = nullptr, *da2b = nullptr, *da2T = nullptr, *da1T = nullptr;
+    float *z = nullptr, *dh = nullptr, *dm = nullptr, *loss = nullptr, *part = nullptr;
+    size_t part_cap = 0;
+    uint32_t step = 0;
+    int *d_error = nullptr;
+    int num_sms = 0;
+};
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+ann_status get_encoder()
+{
+    if (g_encode) return ANN_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return ANN_ECUDA;
+    }
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return ANN_OK;
+}
+
+// Tensor map of a row-major BF16 matrix (rows x K, row stride K elements),
+// box BK x 128, 128-byte swizzle; out-of-range elements read as zero.
+ann_status make_map(CUtensorMap *map, const void *ptr, uint32_t rows, uint32_t K)
+{
+    ann_status s = get_encoder();
+    if (s != ANN_OK) return s;
+    const cuuint64_t dims[2] = {K, rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {BK, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for %u x %u", (int)r, rows, K);
+        return ANN_ECUDA;
+    }
+    return ANN_OK;
+}
+
+template <int EPI>
+ann_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, uint32_t M, uint32_t N, uint32_t K, EpiArgs e,
+                cudaStream_t st)
+{
+    if (M == 0 || N == 0) return ANN_OK;
+    if (K % 8) {
+        set_error("gemm: K = %u must be a multiple of 8", K);
+        return ANN_EINVAL;
+    }
+    CUtensorMap ta, tb;
+    ann_status s = make_map(&ta, A, M, K);
+    if (s == ANN_OK) s = make_map(&tb, B, N, K);
+    if (s != ANN_OK) return s;
+    static bool attr = false;
+    if (!attr) {
+        ANN_CUDA(cudaFuncSetAttribute(gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
+        attr = true;
+    }
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    gemm_kernel<EPI><<<grid, 128, GEMM_SMEM, st>>>(ta, tb, M, N, K, e);
+    ANN_CUDA(cudaGetLastError());
+    return ANN_OK;
+}
+
+int grid1d(size_t n, int num_sms) { return (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms * 8); }
+
+ann_status transpose(const __nv_bfloat16 *in, __nv_bfloat16 *out, uint32_t R, uint32_t C, cudaStream_t st)
+{
+    dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+    transpose_bf16_kernel<<<grid, block, 0, st>>>(in, out, R, C);
+    ANN_CUDA(cudaGetLastError());
+    return ANN_OK;
+}
+
+ann_status forward(ann_mlp *m, const float *x, uint32_t n, cudaStream_t st, int logits_epi, float *logits,
+                   float *part, uint32_t ntiles)
+{
+    to_bf16_kernel<<<grid1d((size_t)n * m->d, m->num_sms), 256, 0, st>>>(x, m->xb, (size_t)n * m->d);
+    ANN_CUDA(cudaGetLastError());
+    EpiArgs e{};
+    e.err = m->d_error;
+    e.bias = m->b[0]; e.cb = m->h1b; e.ldc = m->h1;
+    ann_status s = gemm<EPI_BIAS_RELU_BF16>(m->xb, m->Wb[0], n, m->h1, m->d, e, st);
+    if (s != ANN_OK) return s;
+    e.bias = m->b[1]; e.cb = m->h2b; e.ldc = m->h2;
+    s = gemm<EPI_BIAS_RELU_BF16>(m->h1b, m->Wb[1], n, m->h2, m->h1, e, st);
+    if (s != ANN_OK) return s;
+    e.bias = m->b[2]; e.cb = nullptr;
+    if (logits_epi == EPI_BIAS_F32) {
+        e.c = logits; e.ldc = m->out;
+        return gemm<EPI_BIAS_F32>(m->h2b, m->Wb[2], n, m->out, m->h2, e, st);
+    }
+    e.part = part; e.ntiles = ntiles;
+    return gemm<EPI_TOPP>(m->h2b, m->Wb[2], n, m->out, m->h2, e, st);
+}
+
+void mlp_free_all(ann_mlp *m)
+{
+    for (int l = 0; l < 3; ++l) {
+        void *p[] = {m->W[l], m->b[l], m->mW[l], m->vW[l], m->mb[l], m->vb[l], m->gW[l], m->gb[l], m->Wb[l], m->WT[l]};
+        for (void *x : p) if (x) cudaFree(x);
+    }
+    void *q[] = {m->xb, m->xT, m->h1b, m->h1T, m->h2b, m->h2T, m->dzb, m->dzT, m->da2b, m->da2T, m->da1T,
+                 m->z, m->dh, m->dm, m->loss, m->part, m->d_error};
+    for (void *x : q) if (x) cudaFree(x);
+}
+
+}  // namespace
+
+extern "C" {
+
+ann_status ann_mlp_create(int device, uint32_t in_dim, uint32_t hidden1, uint32_t hidden2, uint32_t out_dim,
+                          uint32_t max_batch, ann_mlp **out)
+{
+    if (!out) { set_error("ann_mlp_create: out is NULL"); return ANN_EINVAL; }
+    *out = nullptr;
+    if (!in_dim || !hidden1 || !hidden2 || !out_dim || !max_batch || in_dim % 8 || hidden1 % 8 || hidden2 % 8 ||
+        out_dim % 8 || max_batch % 8) {
+        set_error("ann_mlp_create: sizes must be positive multiples of 8");
+        return ANN_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        set_error("ann_mlp_create: no CUDA device %d", device);
+        return ANN_EDEVICE;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    ann_mlp *m = new ann_mlp();
+    m->device = device;
+    m->d = in_dim; m->h1 = hidden1; m->h2 = hidden2; m->out = out_dim; m->maxb = max_batch;
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, device);
+    const uint32_t rows[3] = {hidden1, hidden2, out_dim}, cols[3] = {in_dim, hidden1, hidden2};
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes); };
+    for (int l = 0; l < 3; ++l) {
+        const size_t nw = (size_t)rows[l] * cols[l];
+        al((void **)&m->W[l], nw * 4); al((void **)&m->mW[l], nw * 4); al((void **)&m->vW[l], nw * 4);
+        al((void **)&m->gW[l], nw * 4); al((void **)&m->Wb[l], nw * 2); al((void **)&m->WT[l], nw * 2);
+        al((void **)&m->b[l], rows[l] * 4); al((void **)&m->mb[l], rows[l] * 4); al((void **)&m->vb[l], rows[l] * 4);
+        al((void **)&m->gb[l], rows[l] * 4);
+    }
+    const size_t B = max_batch;
+    al((void **)&m->xb, B * in_dim * 2); al((void **)&m->xT, B * in_dim * 2);
+    al((void **)&m->h1b, B * hidden1 * 2); al((void **)&m->h1T, B * hidden1 * 2);
+    al((void **)&m->h2b, B * hidden2 * 2); al((void **)&m->h2T, B * hidden2 * 2);
+    al((void **)&m->dzb, B * out_dim * 2); al((void **)&m->dzT, B * out_dim * 2);
+    al((void **)&m->da2b, B * hidden2 * 2); al((void **)&m->da2T, B * hidden2 * 2);
+    al((void **)&m->da1T, B * hidden1 * 2);
+    al((void **)&m->z, B * out_dim * 4);
+    al((void **)&m->dh, B * std::max(hidden1, hidden2) * 4);
+    al((void **)&m->dm, B * std::max(hidden1, hidden2) * 4);
+    al((void **)&m->loss, 64);
+    al((void **)&m->d_error, 64);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        mlp_free_all(m);
+        delete m;
+        return cuda_fail(e, "ann_mlp_create");
+    }
+    *out = m;
+    return ANN_OK;
+}
+
+ann_status ann_mlp_free(ann_mlp *m)
+{
+    if (!m) return ANN_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    mlp_free_all(m);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete m;
+    return ANN_OK;
+}
+
+// Host FP32 parameters in; resets the optimizer state and step count.
+ann_status ann_mlp_set_params(ann_mlp *m, const float *W1, const float *b1, const float *W2, const float *b2,
+                              const float *W3, const float *b3)
+{
+    if (!m || !W1 || !b1 || !W2 || !b2 || !W3 || !b3) { set_error("ann_mlp_set_params: NULL argument"); return ANN_EINVAL; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    const float *Ws[3] = {W1, W2, W3}, *bs[3] = {b1, b2, b3};
+    const uint32_t rows[3] = {m->h1, m->h2, m->out}, cols[3] = {m->d, m->h1, m->h2};
+    ann_status s = ANN_OK;
+    for (int l = 0; l < 3 && s == ANN_OK; ++l) {
+        const size_t nw = (size_t)rows[l] * cols[l];
+        cudaError_t e = cudaMemcpy(m->W[l], Ws[l], nw * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(m->b[l], bs[l], rows[l] * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(m->mW[l], 0, nw * 4);
+        if (e == cudaSuccess) e = cudaMemset(m->vW[l], 0, nw * 4);
+        if (e == cudaSuccess) e = cudaMemset(m->mb[l], 0, rows[l] * 4);
+        if (e == cudaSuccess) e = cudaMemset(m->vb[l], 0, rows[l] * 4);
+        if (e != cudaSuccess) { s = cuda_fail(e, "ann_mlp_set_params"); break; }
+        to_bf16_kernel<<<grid1d(nw, m->num_sms), 256>>>(m->W[l], m->Wb[l], nw);
+        if (l > 0) s = transpose(m->Wb[l], m->WT[l], rows[l], cols[l], 0);
+    }
+    m->step = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (s == ANN_OK && e != cudaSuccess) s = cuda_fail(e, "ann_mlp_set_params");
+    if (prev >= 0) cudaSetDevice(prev);
+    return s;
+}
+
+// Host copies of the FP32 parameters (which = 0) or of the last step's
+// gradients (which = 1), each pointer NULL to skip.
+ann_status ann_mlp_get(const ann_mlp *m, int which, float *W1, float *b1, float *W2, float *b2, float *W3, float *b3)
+{
+    if (!m || (which != 0 && which != 1)) { set_error("ann_mlp_get: bad arguments"); return ANN_EINVAL; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    float *Ws[3] = {W1, W2, W3}, *bs[3] = {b1, b2, b3};
+    const uint32_t rows[3] = {m->h1, m->h2, m->out}, cols[3] = {m->d, m->h1, m->h2};
+    ann_status s = ANN_OK;
+    cudaDeviceSynchronize();
+    for (int l = 0; l < 3; ++l) {
+        cudaError_t e = cudaSuccess;
+        if (Ws[l]) e = cudaMemcpy(Ws[l], which ? m->gW[l] : m->W[l], (size_t)rows[l] * cols[l] * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && bs[l]) e = cudaMemcpy(bs[l], which ? m->gb[l] : m->b[l], rows[l] * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { s = cuda_fail(e, "ann_mlp_get"); break; }
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return s;
+}
+
+// Logits z = MLP(x) (device x: n x in_dim FP32; device logits: n x out_dim).
+ann_status ann_mlp_forward(ann_mlp *m, const float *x, uint32_t n, float *logits, void *stream)
+{
+    if (!m || !x || !logits) { set_error("ann_mlp_forward: NULL argument"); return ANN_EINVAL; }
+    if (n > m->maxb) { set_error("ann_mlp_forward: n = %u > max_batch %u", n, m->maxb); return ANN_EINVAL; }
+    if (n == 0) return ANN_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    ann_status s = forward(m, x, n, (cudaStream_t)stream, EPI_BIAS_F32, logits, nullptr, 0);
+    if (prev >= 0) cudaSetDevice(prev);
+    return s;
+}
+
+// One AdamW step on a minibatch (device x: n x in_dim, labels: n ghost
+// indices < out_dim); writes the mean loss of the batch to *loss_out (device,
+// may be NULL). Gradients stay available to ann_mlp_get(which = 1).
+ann_status ann_mlp_train_step(ann_mlp *m, const float *x, const uint32_t *labels, uint32_t n, float lr, float beta1,
+                              float beta2, float eps, float weight_decay, float *loss_out, void *stream)
+{
+    if (!m || !x || !labels) { set_error("ann_mlp_train_step: NULL argument"); return ANN_EINVAL; }
+    if (n == 0 || n > m->maxb || n % 8) {
+        set_error("ann_mlp_train_step: batch %u must be a positive multiple of 8 <= %u", n, m->maxb);
+        return ANN_EINVAL;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    ann_status s = ANN_OK;
+    auto chk = [&]() { cudaError_t e = cudaGetLastError(); if (e != cudaSuccess && s == ANN_OK) s = cuda_fail(e, "ann_mlp_train_step"); };
+    if (cudaMemsetAsync(m->loss, 0, 4, st) != cudaSuccess) s = ANN_ECUDA;
+    if (s == ANN_OK) s = forward(m, x, n, st, EPI_BIAS_F32, m->z, nullptr, 0);
+    const dim3 tb(32, 8);
+    EpiArgs e{};
+    e.err = m->d_error;
+    if (s == ANN_OK) {
+        softmax_ce_kernel<<<(n + 7) / 8, 256, 0, st>>>(m->z, labels, n, m->out, m->loss);
+        chk();
+        post_grad_kernel<<<dim3((m->out + 31) / 32, (n + 31) / 32), tb, 0, st>>>(m->z, nullptr, nullptr, m->dzb, m->dzT, n, m->out);
+        chk();
+        colsum_kernel<<<(m->out + 255) / 256, 256, 0, st>>>(m->z, m->gb[2], n, m->out);
+        chk();
+    }
+    if (s == ANN_OK) s = transpose(m->h2b, m->h2T, n, m->h2, st);
+    e.c = m->gW[2]; e.ldc = m->h2;
+    if (s == ANN_OK) s = gemm<EPI_F32>(m->dzT, m->h2T, m->out, m->h2, n, e, st);
+    e.c = m->dh; e.ldc = m->h2;
+    if (s == ANN_OK) s = gemm<EPI_F32>(m->dzb, m->WT[2], n, m->h2, m->out, e, st);
+    if (s == ANN_OK) {
+        post_grad_kernel<<<dim3((m->h2 + 31) / 32, (n + 31) / 32), tb, 0, st>>>(m->dh, m->h2b, m->dm, m->da2b, m->da2T, n, m->h2);
+        chk();
+        colsum_kernel<<<(m->h2 + 255) / 256, 256, 0, st>>>(m->dm, m->gb[1], n, m->h2);
+        chk();
+    }
+    if (s == ANN_OK) s = transpose(m->h1b, m->h1T, n, m->h1, st);
+    e.c = m->gW[1]; e.ldc = m->h1;
+    if (s == ANN_OK) s = gemm<EPI_F32>(m->da2T, m->h1T, m->h2, m->h1, n, e, st);
+    e.c = m->dh; e.ldc = m->h1;
+    if (s == ANN_OK) s = gemm<EPI_F32>(m->da2b, m->WT[1], n, m->h1, m->h2, e, st);
+    if (s == ANN_OK) {
+        post_grad_kernel<<<dim3((m->h1 + 31) / 32, (n + 31) / 32), tb, 0, st>>>(m->dh, m->h1b, m->dm, nullptr, m->da1T, n, m->h1);
+        chk();
+        colsum_kernel<<<(m->h1 + 255) / 256, 256, 0, st>>>(m->dm, m->gb[0], n, m->h1);
+        chk();
+    }
+    if (s == ANN_OK) s = transpose(m->xb, m->xT, n, m->d, st);
+    e.c = m->gW[0]; e.ldc = m->d;
+    if (s == ANN_OK) s = gemm<EPI_F32>(m->da1T, m->xT, m->h1, m->d, n, e, st);
+    if (s == ANN_OK) {
+        m->step++;
+        AdamHP h{lr, beta1, beta2, eps, weight_decay, (float)(1.0 - std::pow((double)beta1, (double)m->step)),
+                 (float)(1.0 - std::pow((double)beta2, (double)m->step))};
+        const uint32_t rows[3] = {m->h1, m->h2, m->out}, cols[3] = {m->d, m->h1, m->h2};
+        for (int l = 0; l < 3; ++l) {
+            const size_t nw = (size_t)rows[l] * cols[l];
+            adamw_kernel<<<grid1d(nw, m->num_sms), 256, 0, st>>>(m->W[l], m->gW[l], m->mW[l], m->vW[l], m->Wb[l], nw, h);
+            adamw_kernel<<<grid1d(rows[l], m->num_sms), 256, 0, st>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], nullptr, rows[l], h);
+            chk();
+            if (l > 0 && s == ANN_OK) s = transpose(m->Wb[l], m->WT[l], rows[l], cols[l], st);
+        }
+    }
+    if (s == ANN_OK && loss_out) {
+        cudaError_t ce = cudaMemcpyAsync(loss_out, m->loss, 4, cudaMemcpyDeviceToDevice, st);
+        if (ce != cudaSuccess) s = cuda_fail(ce, "ann_mlp_train_step loss");
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return s;
+}
+
+// Entry prediction (fused): the top-P ghost indices per query by logit
+// (ties: smaller index), and the largest softmax probability; a query whose
+// probability is below tau gets ANN_INVALID_ID as its first seed, which
+// ann_search treats as "fall back to random ghost seeds". P <= 8.
+ann_status ann_mlp_predict(ann_mlp *m, const float *x, uint32_t n, uint32_t P, float tau, uint32_t *seeds,
+                           float *pmax, void *stream)
+{
+    if (!m || !x || !seeds || P == 0 || P > TOPP || P > m->out) {
+        set_error("ann_mlp_predict: bad arguments (1 <= P <= %d)", TOPP);
+        return ANN_EINVAL;
+    }
+    if (n == 0) return ANN_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    ann_status s = ANN_OK;
+    const uint32_t ntiles = (m->out + BN - 1) / BN;
+    for (uint32_t r0 = 0; r0 < n && s == ANN_OK; r0 += m->maxb) {
+        const uint32_t rows = std::min(m->maxb, n - r0);
+        const size_t need = (size_t)rows * ntiles * (2 * TOPP + 2) * 4;
+        if (need > m->part_cap) {
+            if (m->part) cudaFree(m->part);
+            m->part = nullptr;
+            m->part_cap = 0;
+            cudaError_t e = cudaMalloc(&m->part, need);
+            if (e != cudaSuccess) { s = cuda_fail(e, "ann_mlp_predict"); break; }
+            m->part_cap = need;
+        }
+        s = forward(m, x + (size_t)r0 * m->d, rows, st, EPI_TOPP, nullptr, m->part, ntiles);
+        if (s == ANN_OK) {
+            topp_merge_kernel<<<(rows + 3) / 4, 128, 0, st>>>(m->part, rows, ntiles, P, tau, seeds + (size_t)r0 * P,
+                                                               pmax ? pmax + r0 : nullptr);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) s = cuda_fail(e, "topp_merge_kernel");
+        }
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return s;
+}
+
+// Synchronise `stream` and report (then clear) the MLP's device error word.
+ann_status ann_mlp_sync(ann_mlp *m, void *stream)
+{
+    if (!m) { set_error("ann_mlp_sync: NULL"); return ANN_EINVAL; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    ann_status s = ANN_OK;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, m->d_error, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(e, "ann_mlp_sync");
+    else if (err) {
+        cudaMemset(m->d_error, 0, 4);
+        set_error("a bounded device wait ran out in an MLP kernel");
+        s = ANN_ETIMEOUT;
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return s;
+}
+
+}  // extern "C"

@@ -5,20 +5,26 @@
 //   - persistent CTAs of 4 warps; each warp owns one query at a time and pulls
 //     the next query index from a device counter, so long and short searches
 //     balance across the 152 SMs;
-//   - per warp, shared memory holds the query, two copies of the priority
-//     queue (merge writes the other copy), the candidate list, the adjacency
-//     and direction rows of the current parents, 32 staged vector rows and an
-//     open-addressing visited table;
+//   - per warp, a small shared-memory region (about 14 KB for itopk 64) holds
+//     the query, the priority queue, the candidate list, the parents'
+//     adjacency / direction / vector rows, 16 staged rows and the visited
+//     table, so 16 warps share an SM and hide each other's memory latency;
 //   - every random global read (adjacency rows, direction rows, vector rows,
 //     FP32 rerank rows) is a 1-D TMA bulk copy into shared memory completing
-//     on the warp's mbarrier, so a warp keeps up to 32 rows in flight with one
-//     instruction per row;
+//     on the warp's mbarrier: one instruction per row, all rows of a round in
+//     flight together;
 //   - distances are computed lane-per-row from shared memory, elements in
-//     index order with one fused multiply-add each, so they are bit-identical
-//     to the FP32 reference definition; the query's sign bits relative to each
-//     evaluated node (for DGS) fall out of the same pass;
-//   - merges are rank-based: each entry's output slot is its rank among the
-//     candidates plus its rank in the queue, so any itopk up to 512 works.
+//     index order with one fused multiply-add each, so they equal the FP32
+//     reference definition bit for bit;
+//   - DGS needs the query's sign bits relative to each parent; they are
+//     recomputed from the parent's row, which arrives in the same bulk-copy
+//     round as its adjacency and direction rows (one ballot per 32 dims);
+//   - DGS keeps its top n neighbours by a ballot binary search on the score
+//     threshold, not by sorting;
+//   - the merge works in place: candidates no better than the queue's last
+//     entry are dropped first, each survivor's slot is its rank among the
+//     candidates plus its insertion point in the queue, and only queue
+//     entries behind the first insertion point move.
 //
 // Visited set: the table is exact between resets. It is cleared (and refilled
 // with the queue's ids) only when it would pass half full. Forgetting a node
@@ -28,6 +34,7 @@
 // only the work counters can grow (counted in hash_resets).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "ann_internal.cuh"
 
@@ -38,7 +45,7 @@ namespace {
 constexpr uint32_t kUnexpanded = 0, kPartial = 1, kExpanded = 2;
 constexpr uint64_t kGhostTag = 0x67686F7374ull;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
-constexpr uint32_t kStageRows = 32;
+constexpr uint32_t kMaxDegWords = ANN_MAX_DEGREE / 32;
 
 struct View {
     const uint8_t *codes;
@@ -51,7 +58,7 @@ struct View {
 };
 
 struct Layout {  // byte offsets inside one warp's shared-memory region
-    uint32_t q, bd[2], bi[2], bs[2], bq[2], cd, ci, cq, cs, ck, adj, dir, par, stage, hash, bar, total;
+    uint32_t q, bd, bi, bs, cd, ci, cs, adj, dir, prow, pqb, par, stage, hash, bar, total;
 };
 
 struct Args {
@@ -66,12 +73,12 @@ struct Args {
     uint32_t *out_ids;
     float *out_dists;
     ann_query_stats *stats;
-    uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank, want_bits;
+    uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank;
     uint64_t seed, qid_base;
     uint32_t *counter;
     int *err;
     Layout lay;
-    uint32_t cap_cand, hash_bits, stage_stride;
+    uint32_t cap_cand, hash_bits, stage_rows, stage_stride, prow_bytes;
 };
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
@@ -94,265 +101,299 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
-// One element of the distance: df = q - x, acc += df * df (one rounding),
-// and the DGS sign bit [q > x] == [df > 0].
-__device__ __forceinline__ void step(float qv, float xv, float &acc, uint32_t &word, uint32_t bit)
+// One element: df = q - x, acc += df * df with a single rounding.
+__device__ __forceinline__ void step(float qv, float xv, float &acc)
 {
     const float df = __fsub_rn(qv, xv);
     acc = __fmaf_rn(df, df, acc);
-    word |= (uint32_t)(df > 0.0f) << bit;
 }
 
-// Squared L2 between the staged row and the query (both in shared memory),
-// elements in index order; writes ceil(d/32) sign words when `bits`.
+// Squared L2 between a staged row and the query (both in shared memory),
+// elements in index order.
 template <int ST>
-__device__ __forceinline__ float row_dist(const uint8_t *row, const float *q, float scale, uint32_t d,
-                                          uint32_t *qb, bool bits)
+__device__ __forceinline__ float row_dist(const uint8_t *row, const float *q, float scale, uint32_t d)
 {
     float acc = 0.0f;
-    const uint32_t nw = (d + 31) >> 5;
-    for (uint32_t t = 0; t < nw; ++t) {
-        uint32_t word = 0;
-        const uint32_t base = t * 32;
-        if (ST == ANN_F32) {
+    if (ST == ANN_F32) {
+        uint32_t i = 0;
+        for (; i + 4 <= d; i += 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(row + (size_t)i * 4);
+            const float4 y = *reinterpret_cast<const float4 *>(q + i);
+            step(y.x, x.x, acc);
+            step(y.y, x.y, acc);
+            step(y.z, x.z, acc);
+            step(y.w, x.w, acc);
+        }
+        for (; i < d; ++i) step(q[i], reinterpret_cast<const float *>(row)[i], acc);
+    } else if (ST == ANN_F16) {
+        uint32_t i = 0;
+        for (; i + 8 <= d; i += 8) {
+            const uint4 raw = *reinterpret_cast<const uint4 *>(row + (size_t)i * 2);
+            const float4 y0 = *reinterpret_cast<const float4 *>(q + i);
+            const float4 y1 = *reinterpret_cast<const float4 *>(q + i + 4);
+            const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+            const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+            const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
+            const float2 f3 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
+            step(y0.x, __fmul_rn(scale, f0.x), acc);
+            step(y0.y, __fmul_rn(scale, f0.y), acc);
+            step(y0.z, __fmul_rn(scale, f1.x), acc);
+            step(y0.w, __fmul_rn(scale, f1.y), acc);
+            step(y1.x, __fmul_rn(scale, f2.x), acc);
+            step(y1.y, __fmul_rn(scale, f2.y), acc);
+            step(y1.z, __fmul_rn(scale, f3.x), acc);
+            step(y1.w, __fmul_rn(scale, f3.y), acc);
+        }
+        for (; i < d; ++i)
+            step(q[i], __fmul_rn(scale, __half2float(reinterpret_cast<const __half *>(row)[i])), acc);
+    } else {
+        uint32_t i = 0;
+        for (; i + 16 <= d; i += 16) {
+            const uint4 raw = *reinterpret_cast<const uint4 *>(row + i);
+            const uint32_t wds[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
-            for (uint32_t c = 0; c < 8; ++c) {
-                const uint32_t i = base + c * 4;
-                if (i < d) {
-                    const float4 x = *reinterpret_cast<const float4 *>(row + (size_t)i * 4);
-                    const float4 y = *reinterpret_cast<const float4 *>(q + i);
-                    step(y.x, x.x, acc, word, c * 4 + 0);
-                    if (i + 1 < d) step(y.y, x.y, acc, word, c * 4 + 1);
-                    if (i + 2 < d) step(y.z, x.z, acc, word, c * 4 + 2);
-                    if (i + 3 < d) step(y.w, x.w, acc, word, c * 4 + 3);
-                }
-            }
-        } else if (ST == ANN_F16) {
-#pragma unroll
-            for (uint32_t c = 0; c < 4; ++c) {
-                const uint32_t i = base + c * 8;
-                if (i < d) {
-                    const uint4 raw = *reinterpret_cast<const uint4 *>(row + (size_t)i * 2);
-                    const __half2 *h = reinterpret_cast<const __half2 *>(&raw);
-                    const float4 y0 = *reinterpret_cast<const float4 *>(q + i);
-                    const float4 y1 = *reinterpret_cast<const float4 *>(q + i + 4);
-                    const float ys[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-#pragma unroll
-                    for (uint32_t e = 0; e < 4; ++e) {
-                        const float2 f = __half22float2(h[e]);
-                        if (i + 2 * e < d) step(ys[2 * e], __fmul_rn(scale, f.x), acc, word, c * 8 + 2 * e);
-                        if (i + 2 * e + 1 < d)
-                            step(ys[2 * e + 1], __fmul_rn(scale, f.y), acc, word, c * 8 + 2 * e + 1);
-                    }
-                }
-            }
-        } else {
-#pragma unroll
-            for (uint32_t c = 0; c < 2; ++c) {
-                const uint32_t i = base + c * 16;
-                if (i < d) {
-                    const uint4 raw = *reinterpret_cast<const uint4 *>(row + i);
-                    const uint16_t *pr = reinterpret_cast<const uint16_t *>(&raw);
-#pragma unroll
-                    for (uint32_t e = 0; e < 8; ++e) {
-                        const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pr[e], __NV_E4M3);
-                        const float2 f = __half22float2(__half2(hr));
-                        const uint32_t ii = i + 2 * e;
-                        if (ii < d) step(q[ii], __fmul_rn(scale, f.x), acc, word, c * 16 + 2 * e);
-                        if (ii + 1 < d) step(q[ii + 1], __fmul_rn(scale, f.y), acc, word, c * 16 + 2 * e + 1);
-                    }
-                }
+            for (int e = 0; e < 4; ++e) {
+                const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wds[e] & 0xffffu), __NV_E4M3);
+                const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wds[e] >> 16), __NV_E4M3);
+                const float2 a = __half22float2(__half2(lo));
+                const float2 b = __half22float2(__half2(hi));
+                const float4 y = *reinterpret_cast<const float4 *>(q + i + 4 * e);
+                step(y.x, __fmul_rn(scale, a.x), acc);
+                step(y.y, __fmul_rn(scale, a.y), acc);
+                step(y.z, __fmul_rn(scale, b.x), acc);
+                step(y.w, __fmul_rn(scale, b.y), acc);
             }
         }
-        if (bits) qb[t] = word;
+        for (; i < d; ++i) {
+            const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[i], __NV_E4M3);
+            step(q[i], __fmul_rn(scale, __half2float(__half(h))), acc);
+        }
     }
     return acc;
+}
+
+// Stored value of element i (for the parent's sign bits).
+template <int ST>
+__device__ __forceinline__ float stored_elem(const uint8_t *row, uint32_t i, float scale)
+{
+    if (ST == ANN_F32) return reinterpret_cast<const float *>(row)[i];
+    if (ST == ANN_F16) return __fmul_rn(scale, __half2float(reinterpret_cast<const __half *>(row)[i]));
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[i], __NV_E4M3);
+    return __fmul_rn(scale, __half2float(__half(h)));
 }
 
 template <int ST>
 struct WarpSearch {
     const Args &a;
+    uint8_t *base;
     uint32_t lane;
-    float *q;
-    float *bd[2];
-    uint32_t *bi[2];
-    uint8_t *bs[2];
-    uint32_t *bq[2];
-    float *cd;
-    uint32_t *ci, *cq;
-    int *cs;
-    uint8_t *ck;
-    uint32_t *adj, *dirs, *par;
-    uint8_t *stage;
-    uint32_t *hash;
-    uint64_t *bar;
-    uint32_t cur = 0, cnt = 0, phase = 0, hash_count = 0;
+    uint32_t cnt = 0, phase = 0, hash_count = 0;
     bool failed = false;
-    uint32_t qi = 0;
     uint64_t qid = 0;
     ann_query_stats st;
 
-    __device__ WarpSearch(const Args &args, uint8_t *base) : a(args), lane(threadIdx.x & 31)
-    {
-        const Layout &L = a.lay;
-        q = reinterpret_cast<float *>(base + L.q);
-        for (int s = 0; s < 2; ++s) {
-            bd[s] = reinterpret_cast<float *>(base + L.bd[s]);
-            bi[s] = reinterpret_cast<uint32_t *>(base + L.bi[s]);
-            bs[s] = base + L.bs[s];
-            bq[s] = reinterpret_cast<uint32_t *>(base + L.bq[s]);
-        }
-        cd = reinterpret_cast<float *>(base + L.cd);
-        ci = reinterpret_cast<uint32_t *>(base + L.ci);
-        cq = reinterpret_cast<uint32_t *>(base + L.cq);
-        cs = reinterpret_cast<int *>(base + L.cs);
-        ck = base + L.ck;
-        adj = reinterpret_cast<uint32_t *>(base + L.adj);
-        dirs = reinterpret_cast<uint32_t *>(base + L.dir);
-        par = reinterpret_cast<uint32_t *>(base + L.par);
-        stage = base + L.stage;
-        hash = reinterpret_cast<uint32_t *>(base + L.hash);
-        bar = reinterpret_cast<uint64_t *>(base + L.bar);
-    }
+    __device__ WarpSearch(const Args &args, uint8_t *b) : a(args), base(b), lane(threadIdx.x & 31) {}
+
+    // shared-memory arrays of this warp
+    __device__ __forceinline__ float *q() const { return reinterpret_cast<float *>(base + a.lay.q); }
+    __device__ __forceinline__ float *bd() const { return reinterpret_cast<float *>(base + a.lay.bd); }
+    __device__ __forceinline__ uint32_t *bi() const { return reinterpret_cast<uint32_t *>(base + a.lay.bi); }
+    __device__ __forceinline__ uint8_t *bs() const { return base + a.lay.bs; }
+    __device__ __forceinline__ float *cd() const { return reinterpret_cast<float *>(base + a.lay.cd); }
+    __device__ __forceinline__ uint32_t *ci() const { return reinterpret_cast<uint32_t *>(base + a.lay.ci); }
+    __device__ __forceinline__ uint32_t *cs() const { return reinterpret_cast<uint32_t *>(base + a.lay.cs); }
+    __device__ __forceinline__ uint32_t *adj() const { return reinterpret_cast<uint32_t *>(base + a.lay.adj); }
+    __device__ __forceinline__ uint32_t *dirs() const { return reinterpret_cast<uint32_t *>(base + a.lay.dir); }
+    __device__ __forceinline__ uint8_t *prow() const { return base + a.lay.prow; }
+    __device__ __forceinline__ uint32_t *pqb() const { return reinterpret_cast<uint32_t *>(base + a.lay.pqb); }
+    __device__ __forceinline__ uint32_t *par() const { return reinterpret_cast<uint32_t *>(base + a.lay.par); }
+    __device__ __forceinline__ uint8_t *stage() const { return base + a.lay.stage; }
+    __device__ __forceinline__ uint32_t *hash() const { return reinterpret_cast<uint32_t *>(base + a.lay.hash); }
+    __device__ __forceinline__ uint64_t *bar() const { return reinterpret_cast<uint64_t *>(base + a.lay.bar); }
 
     // ---------------------------------------------------------- visited set
     __device__ bool hash_insert(uint32_t v)
     {
+        uint32_t *h = hash();
         const uint32_t mask = (1u << a.hash_bits) - 1;
-        uint32_t h = (v * 2654435761u) >> (32 - a.hash_bits);
+        uint32_t s = (v * 2654435761u) >> (32 - a.hash_bits);
         for (uint32_t probe = 0; probe <= mask; ++probe) {
-            const uint32_t old = atomicCAS(&hash[h], kEmpty, v);
+            const uint32_t old = atomicCAS(&h[s], kEmpty, v);
             if (old == kEmpty) return true;
             if (old == v) return false;
-            h = (h + 1) & mask;
+            s = (s + 1) & mask;
         }
         return true;  // unreachable: the table is never more than half full
     }
 
     __device__ void hash_clear()
     {
+        uint32_t *h = hash();
         const uint32_t H = 1u << a.hash_bits;
-        for (uint32_t i = lane; i < H; i += 32) hash[i] = kEmpty;
+        for (uint32_t i = lane; i < H; i += 32) h[i] = kEmpty;
         __syncwarp();
         hash_count = 0;
     }
 
-    // Forget everything but the queue (see the file comment for why the
-    // result cannot change).
+    // Forget everything but the queue (why this cannot change the result is
+    // in the file comment).
     __device__ void hash_reset()
     {
         hash_clear();
-        for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi[cur][i]);
+        for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi()[i]);
         __syncwarp();
         hash_count = cnt;
         st.hash_resets++;
     }
 
-    __device__ void hash_make_room(uint32_t incoming)
+    __device__ __forceinline__ void hash_make_room(uint32_t incoming)
     {
         if (hash_count + incoming > (1u << (a.hash_bits - 1))) hash_reset();
     }
 
     // ------------------------------------------------ bulk copies + waiting
-    // Every lane waits; the outcome is made warp-uniform so that the warp's
-    // later collectives never see a partial warp.
+    // Every lane waits; the outcome is made warp-uniform so the warp's later
+    // collectives never see a partial warp.
     __device__ bool wait_copies()
     {
-        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, phase, a.err));
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar(), phase, a.err));
         phase ^= 1;
         if (!ok) {
             failed = true;
-            // let the copies still in flight land before this warp leaves
-            mbar_wait_bounded(bar, phase ^ 1, a.err);
+            mbar_wait_bounded(bar(), phase ^ 1, a.err);  // let copies in flight land
             __syncwarp();
         }
         return ok;
     }
 
     // ----------------------------------------------------- evaluate rows
-    // Distances (and sign words) of candidates [0, nc) of view `v`.
+    // Distances of rows ids[0, n) of `codes` into out[0, n), stage_rows rows
+    // per bulk-copy round.
     template <int RST>
-    __device__ bool evaluate(const uint8_t *codes, const float *scales, uint32_t row_bytes, uint32_t nc,
-                             float *out_d, bool bits)
+    __device__ bool evaluate(const uint8_t *codes, const float *scales, uint32_t row_bytes, const uint32_t *ids,
+                             uint32_t n, float *out)
     {
-        for (uint32_t b0 = 0; b0 < nc; b0 += kStageRows) {
-            const uint32_t rows = min(kStageRows, nc - b0);
-            uint32_t v = 0;
+        const uint32_t R = a.stage_rows;
+        for (uint32_t b0 = 0; b0 < n; b0 += R) {
+            const uint32_t rows = min(R, n - b0);
             float scale = 1.0f;
             if (lane == 0) {
                 fence_proxy_async();
-                mbar_arrive_expect_tx(bar, rows * row_bytes);
+                mbar_arrive_expect_tx(bar(), rows * row_bytes);
             }
             __syncwarp();
             if (lane < rows) {
-                v = ci[b0 + lane];
-                bulk_g2s(stage + lane * a.stage_stride, codes + (uint64_t)v * row_bytes, row_bytes, bar);
+                const uint32_t v = ids[b0 + lane];
+                bulk_g2s(stage() + lane * a.stage_stride, codes + (uint64_t)v * row_bytes, row_bytes, bar());
                 if (RST != ANN_F32) scale = __ldg(scales + v);
             }
             if (!wait_copies()) return false;
-            if (lane < rows) {
-                const float dd = row_dist<RST>(stage + lane * a.stage_stride, q, scale, a.d,
-                                               cq + (b0 + lane) * a.w, bits);
-                out_d[b0 + lane] = dd;
-            }
+            if (lane < rows) out[b0 + lane] = row_dist<RST>(stage() + lane * a.stage_stride, q(), scale, a.d);
             __syncwarp();
         }
         return true;
     }
 
     // --------------------------------------------------------------- merge
-    // Rank-based merge of candidates [0, nc) into the queue, keeping the
-    // first lcap entries by (dist, id). New entries are UNEXPANDED.
+    // In-place merge of candidates [0, nc) into the queue, keeping the first
+    // lcap entries by (dist, id). New entries are UNEXPANDED.
     __device__ void merge(uint32_t nc, uint32_t lcap)
     {
-        const uint32_t s = cur, t = cur ^ 1, w = a.w;
-        const bool bits = a.want_bits;
+        float *qd = bd();
+        uint32_t *qi = bi();
+        uint8_t *qs = bs();
+        float *kd = cd();
+        uint32_t *kid = ci();
+        uint32_t *ks = cs();
+        // 1. drop candidates no better than the last entry of a full queue
+        if (cnt == lcap && nc) {
+            const float wd = qd[cnt - 1];
+            const uint32_t wi = qi[cnt - 1];
+            uint32_t kept = 0;
+            for (uint32_t b = 0; b < nc; b += 32) {
+                const uint32_t c = b + lane;
+                float dd = 0.0f;
+                uint32_t id = 0;
+                bool keep = false;
+                if (c < nc) {
+                    dd = kd[c];
+                    id = kid[c];
+                    keep = key_less(dd, id, wd, wi);
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, keep);
+                __syncwarp();
+                if (keep) {
+                    const uint32_t at = kept + __popc(m & lanemask_lt());
+                    kd[at] = dd;
+                    kid[at] = id;
+                }
+                kept += __popc(m);
+                __syncwarp();
+            }
+            nc = kept;
+        }
+        if (nc == 0) return;
+        // 2. insertion point in the queue and rank among the candidates
+        uint32_t min_lb = 0xffffffffu;
         for (uint32_t c = lane; c < nc; c += 32) {
-            const float kd = cd[c];
-            const uint32_t kid = ci[c];
+            const float dd = kd[c];
+            const uint32_t id = kid[c];
             uint32_t r = 0;
-            for (uint32_t c2 = 0; c2 < nc; ++c2) r += key_less(cd[c2], ci[c2], kd, kid);
+            for (uint32_t c2 = 0; c2 < nc; ++c2) r += key_less(kd[c2], kid[c2], dd, id);
             uint32_t lo = 0, hi = cnt;
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (key_less(bd[s][mid], bi[s][mid], kd, kid)) lo = mid + 1;
+                if (key_less(qd[mid], qi[mid], dd, id)) lo = mid + 1;
                 else hi = mid;
             }
-            const uint32_t pos = r + lo;
-            if (pos < lcap) {
-                bd[t][pos] = kd;
-                bi[t][pos] = kid;
-                bs[t][pos] = kUnexpanded;
-                if (bits)
-                    for (uint32_t x = 0; x < w; ++x) bq[t][pos * w + x] = cq[c * w + x];
+            ks[c] = lo | (r << 16);
+            min_lb = min(min_lb, lo);
+        }
+        for (int o = 16; o; o >>= 1) min_lb = min(min_lb, __shfl_xor_sync(0xffffffffu, min_lb, o));
+        __syncwarp();
+        // 3. shift queue entries [min_lb, cnt) by the number of candidates
+        //    inserted before them, last chunk first (in place)
+        if (cnt > min_lb) {
+            for (int32_t top = (int32_t)cnt - 1; top >= (int32_t)min_lb; top -= 32) {
+                const int32_t b = top - (int32_t)lane;
+                float dd = 0.0f;
+                uint32_t id = 0, s = 0, shift = 0;
+                const bool mine = b >= (int32_t)min_lb;
+                if (mine) {
+                    dd = qd[b];
+                    id = qi[b];
+                    s = qs[b];
+                    for (uint32_t c = 0; c < nc; ++c) shift += (ks[c] & 0xffffu) <= (uint32_t)b;
+                }
+                __syncwarp();
+                if (mine && (uint32_t)b + shift < lcap) {
+                    qd[b + shift] = dd;
+                    qi[b + shift] = id;
+                    qs[b + shift] = (uint8_t)s;
+                }
+                __syncwarp();
             }
         }
-        for (uint32_t b = lane; b < cnt; b += 32) {
-            const float kd = bd[s][b];
-            const uint32_t kid = bi[s][b];
-            uint32_t r = 0;
-            for (uint32_t c2 = 0; c2 < nc; ++c2) r += key_less(cd[c2], ci[c2], kd, kid);
-            const uint32_t pos = b + r;
+        // 4. candidates into their slots
+        for (uint32_t c = lane; c < nc; c += 32) {
+            const uint32_t pos = (ks[c] & 0xffffu) + (ks[c] >> 16);
             if (pos < lcap) {
-                bd[t][pos] = kd;
-                bi[t][pos] = kid;
-                bs[t][pos] = bs[s][b];
-                if (bits)
-                    for (uint32_t x = 0; x < w; ++x) bq[t][pos * w + x] = bq[s][b * w + x];
+                qd[pos] = kd[c];
+                qi[pos] = kid[c];
+                qs[pos] = kUnexpanded;
             }
         }
         cnt = min(lcap, cnt + nc);
-        cur = t;
         __syncwarp();
     }
 
     // Collect a lane's id into the candidate list if it is new to the
     // visited set; returns the warp's new count.
-    __device__ uint32_t collect(bool valid, uint32_t v, uint32_t nc)
+    __device__ __forceinline__ uint32_t collect(bool valid, uint32_t v, uint32_t nc)
     {
         const bool isnew = valid && hash_insert(v);
         const uint32_t m = __ballot_sync(0xffffffffu, isnew);
-        if (isnew) ci[nc + __popc(m & lanemask_lt())] = v;
+        if (isnew) ci()[nc + __popc(m & lanemask_lt())] = v;
         return nc + __popc(m);
     }
 
@@ -375,9 +416,9 @@ struct WarpSearch {
             }
             __syncwarp();
             hash_count += nc;
-            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, nc, cd, a.want_bits)) return false;
-            merge(nc, lcap);
+            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
             rows += nc;
+            merge(nc, lcap);
         }
         return true;
     }
@@ -391,14 +432,14 @@ struct WarpSearch {
             hash_make_room(chunk);
             uint32_t nc = 0;
             for (uint32_t b = 0; b < chunk; b += 32) {
-                uint32_t id = (b + lane < chunk) ? ids[j0 + b + lane] : kEmpty;
+                const uint32_t id = (b + lane < chunk) ? ids[j0 + b + lane] : kEmpty;
                 nc = collect(id < v.n, id, nc);
             }
             __syncwarp();
             hash_count += nc;
-            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, nc, cd, a.want_bits)) return false;
-            merge(nc, lcap);
+            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
             rows += nc;
+            merge(nc, lcap);
         }
         return true;
     }
@@ -408,18 +449,19 @@ struct WarpSearch {
     __device__ uint32_t select_parents(uint32_t W, bool cool)
     {
         uint32_t np = 0;
-        for (uint32_t base = 0; base < cnt && np < W; base += 32) {
-            const uint32_t i = base + lane;
+        const uint8_t *s8 = bs();
+        for (uint32_t b = 0; b < cnt && np < W; b += 32) {
+            const uint32_t i = b + lane;
             bool e = false;
             if (i < cnt) {
-                const uint32_t s = bs[cur][i];
+                const uint32_t s = s8[i];
                 e = s == kUnexpanded || (cool && s == kPartial);
             }
             uint32_t m = __ballot_sync(0xffffffffu, e);
             while (m && np < W) {
-                const uint32_t b = __ffs(m) - 1;
+                const uint32_t bit = __ffs(m) - 1;
                 m &= m - 1;
-                if (lane == 0) par[np] = base + b;
+                if (lane == 0) par()[np] = b + bit;
                 ++np;
             }
         }
@@ -430,8 +472,56 @@ struct WarpSearch {
     __device__ bool any_partial()
     {
         bool p = false;
-        for (uint32_t i = lane; i < cnt; i += 32) p |= bs[cur][i] == kPartial;
+        for (uint32_t i = lane; i < cnt; i += 32) p |= bs()[i] == kPartial;
         return __any_sync(0xffffffffu, p);
+    }
+
+    // DGS keep-mask of parent pi (bit r of the result: slot lane + 32 r is
+    // kept). Score = matching sign bits; keep the top n_keep by (score desc,
+    // slot asc): find the threshold score t by binary search with ballots,
+    // keep scores above t and the first ties at t.
+    __device__ uint32_t dgs_keep(const View &v, uint32_t pi, uint32_t n_keep)
+    {
+        const uint32_t w = a.w, deg = v.deg;
+        const uint32_t *pq = pqb() + pi * w;
+        int sc[kMaxDegWords];
+#pragma unroll
+        for (uint32_t r = 0; r < kMaxDegWords; ++r) {
+            const uint32_t j = lane + 32 * r;
+            sc[r] = -2;  // beyond the degree: never kept
+            if (j < deg) {
+                const uint32_t nb = adj()[pi * v.deg_pad + j];
+                sc[r] = -1;
+                if (nb != ANN_INVALID_ID) {
+                    const uint32_t *db = dirs() + (pi * v.deg_pad + j) * w;
+                    int diff = 0;
+                    for (uint32_t x = 0; x < w; ++x) diff += __popc(pq[x] ^ db[x]);
+                    sc[r] = (int)a.d - diff;
+                }
+            }
+        }
+        int lo = -1, hi = (int)a.d + 1;  // count(score >= lo) >= n_keep > count(score >= hi)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            uint32_t c = 0;
+#pragma unroll
+            for (uint32_t r = 0; r < kMaxDegWords; ++r) c += __popc(__ballot_sync(0xffffffffu, sc[r] >= mid));
+            if (c >= n_keep) lo = mid;
+            else hi = mid;
+        }
+        uint32_t above = 0;
+#pragma unroll
+        for (uint32_t r = 0; r < kMaxDegWords; ++r) above += __popc(__ballot_sync(0xffffffffu, sc[r] > lo));
+        const uint32_t need = n_keep - above;
+        uint32_t keep = 0, ties_before = 0;
+#pragma unroll
+        for (uint32_t r = 0; r < kMaxDegWords; ++r) {
+            const uint32_t tm = __ballot_sync(0xffffffffu, sc[r] == lo);
+            const bool tie_kept = sc[r] == lo && ties_before + __popc(tm & lanemask_lt()) < need;
+            if (sc[r] > lo || tie_kept) keep |= 1u << r;
+            ties_before += __popc(tm);
+        }
+        return keep;
     }
 
     // Steps 3-4 repeated, with DGS and its cool-down (Section 3.3.2).
@@ -454,75 +544,63 @@ struct WarpSearch {
             if (np == 0) break;
             ++c_iters;
             const bool dgs_now = dgs_on && !cool;
-            // mark parents and fetch their adjacency (and direction) rows
+            // mark the parents; fetch adjacency (and, under DGS, direction
+            // and vector) rows in one bulk-copy round
             const uint32_t adj_bytes = v.deg_pad * 4;
             const uint32_t dir_bytes = v.deg_pad * w * 4;
             uint32_t pid = 0;
+            float pscale = 1.0f;
             if (lane < np) {
-                const uint32_t bidx = par[lane];
-                pid = bi[cur][bidx];
-                bs[cur][bidx] = (dgs_now && reexpand) ? kPartial : kExpanded;
+                const uint32_t b = par()[lane];
+                pid = bi()[b];
+                bs()[b] = (dgs_now && reexpand) ? kPartial : kExpanded;
             }
             if (lane == 0) {
                 fence_proxy_async();
-                mbar_arrive_expect_tx(bar, np * (adj_bytes + (dgs_now ? dir_bytes : 0)));
+                mbar_arrive_expect_tx(bar(), np * (adj_bytes + (dgs_now ? dir_bytes + v.row_bytes : 0)));
             }
             __syncwarp();
             if (lane < np) {
-                bulk_g2s(adj + lane * v.deg_pad, v.graph + (uint64_t)pid * v.deg_pad, adj_bytes, bar);
-                if (dgs_now)
-                    bulk_g2s(dirs + lane * v.deg_pad * w, v.dir + (uint64_t)pid * v.deg_pad * w, dir_bytes, bar);
+                bulk_g2s(adj() + lane * v.deg_pad, v.graph + (uint64_t)pid * v.deg_pad, adj_bytes, bar());
+                if (dgs_now) {
+                    bulk_g2s(dirs() + lane * v.deg_pad * w, v.dir + (uint64_t)pid * v.deg_pad * w, dir_bytes, bar());
+                    bulk_g2s(prow() + lane * a.prow_bytes, v.codes + (uint64_t)pid * v.row_bytes, v.row_bytes, bar());
+                    if (RST != ANN_F32) pscale = __ldg(v.scales + pid);
+                }
             }
             if (!wait_copies()) return false;
             c_parents += np;
-            const uint32_t total = np * deg;
+            uint32_t keep[ANN_MAX_WIDTH];
             if (dgs_now) {
                 c_dgs += np;
-                // score = matching sign bits between the query's bits
-                // relative to the parent and the edge's stored bits
-                for (uint32_t e = lane; e < total; e += 32) {
-                    const uint32_t pi = e / deg, j = e - pi * deg;
-                    const uint32_t nb = adj[pi * v.deg_pad + j];
-                    int sc = -1;
-                    if (nb != ANN_INVALID_ID) {
-                        const uint32_t *qb = bq[cur] + par[pi] * w;
-                        const uint32_t *db = dirs + (pi * v.deg_pad + j) * w;
-                        int diff = 0;
-                        for (uint32_t x = 0; x < w; ++x) diff += __popc(qb[x] ^ db[x]);
-                        sc = (int)a.d - diff;
+                // the query's sign bits relative to each parent: [q > x_parent]
+                for (uint32_t pi = 0; pi < np; ++pi) {
+                    const float ps = __shfl_sync(0xffffffffu, pscale, pi);
+                    const uint8_t *pr = prow() + pi * a.prow_bytes;
+                    for (uint32_t t = 0; t < w; ++t) {
+                        const uint32_t i = 32 * t + lane;
+                        const bool bit = i < a.d && q()[i] > stored_elem<RST>(pr, i, ps);
+                        const uint32_t word = __ballot_sync(0xffffffffu, bit);
+                        if (lane == 0) pqb()[pi * w + t] = word;
                     }
-                    cs[e] = sc;
                 }
                 __syncwarp();
-                // keep the top n_keep per parent (ties: earlier adjacency slot)
-                for (uint32_t e = lane; e < total; e += 32) {
-                    const uint32_t pi = e / deg, j = e - pi * deg;
-                    const int sj = cs[e];
-                    uint32_t rank = 0;
-                    for (uint32_t i2 = 0; i2 < deg; ++i2) {
-                        const int si = cs[pi * deg + i2];
-                        rank += (si > sj) || (si == sj && i2 < j);
-                    }
-                    ck[e] = rank < n_keep;
-                }
-                __syncwarp();
+                for (uint32_t pi = 0; pi < np; ++pi) keep[pi] = dgs_keep(v, pi, n_keep);
             }
-            hash_make_room(total);
+            hash_make_room(np * deg);
             uint32_t nc = 0;
-            for (uint32_t b = 0; b < total; b += 32) {
-                const uint32_t e = b + lane;
-                bool valid = e < total;
-                uint32_t nb = ANN_INVALID_ID;
-                if (valid) {
-                    const uint32_t pi = e / deg, j = e - pi * deg;
-                    nb = adj[pi * v.deg_pad + j];
-                    valid = nb != ANN_INVALID_ID && (!dgs_now || ck[e]);
+            for (uint32_t pi = 0; pi < np; ++pi) {
+                const uint32_t km = dgs_now ? keep[pi] : 0xffffffffu;
+                for (uint32_t r = 0; r * 32 < deg; ++r) {
+                    const uint32_t j = lane + 32 * r;
+                    uint32_t nb = ANN_INVALID_ID;
+                    if (j < deg) nb = adj()[pi * v.deg_pad + j];
+                    nc = collect(j < deg && nb != ANN_INVALID_ID && ((km >> r) & 1u), nb, nc);
                 }
-                nc = collect(valid, nb, nc);
             }
             __syncwarp();
             hash_count += nc;
-            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, nc, cd, a.want_bits)) return false;
+            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
             c_rows += nc;
             merge(nc, lcap);
         }
@@ -532,24 +610,21 @@ struct WarpSearch {
     // ------------------------------------------------------------- a query
     __device__ void run(uint32_t query)
     {
-        qi = query;
         qid = a.qid_base + query;
         st = ann_query_stats{};
         cnt = 0;
-        cur = 0;
-        const float *qg = a.queries + (uint64_t)qi * a.d;
+        const float *qg = a.queries + (uint64_t)query * a.d;
         const uint32_t dpad = (a.d + 31) & ~31u;
-        for (uint32_t i = lane; i < dpad; i += 32) q[i] = i < a.d ? qg[i] : 0.0f;
+        for (uint32_t i = lane; i < dpad; i += 32) q()[i] = i < a.d ? qg[i] : 0.0f;
         __syncwarp();
         hash_clear();
         bool ok = true;
-        const bool use_ghost = a.entry != ANN_ENTRY_RANDOM;
-        if (!use_ghost) {
+        if (a.entry == ANN_ENTRY_RANDOM) {
             ok = seed_random<ST>(a.base, a.m, 0, a.L, st.vec_rows);
         } else {
             const uint32_t *given = nullptr;
             if (a.entry == ANN_ENTRY_GIVEN_GHOST && a.given) {
-                given = a.given + (uint64_t)qi * a.n_given;
+                given = a.given + (uint64_t)query * a.n_given;
                 if (given[0] == ANN_INVALID_ID) given = nullptr;  // fall back to random ghost seeds
             }
             uint32_t Tg = a.Tg;
@@ -561,20 +636,20 @@ struct WarpSearch {
             }
             uint32_t no_dgs = 0;
             if (ok)
-                ok = iterate<ST>(a.ghost, a.Lg, 1, Tg, a.ghost.deg, 0, 0, st.ghost_iters, st.ghost_parents,
-                                 no_dgs, st.ghost_vec_rows);
+                ok = iterate<ST>(a.ghost, a.Lg, 1, Tg, a.ghost.deg, 0, 0, st.ghost_iters, st.ghost_parents, no_dgs,
+                                 st.ghost_vec_rows);
             if (ok) {
                 // transition: the top g ghost results become the base queue;
                 // ghost ids are ascending, so the (dist, id) order carries over
                 const uint32_t g = min(min(a.g, cnt), a.L);
                 for (uint32_t i = lane; i < g; i += 32) {
-                    bi[cur][i] = __ldg(a.ghost_ids + bi[cur][i]);
-                    bs[cur][i] = kUnexpanded;
+                    bi()[i] = __ldg(a.ghost_ids + bi()[i]);
+                    bs()[i] = kUnexpanded;
                 }
                 __syncwarp();
                 cnt = g;
                 hash_clear();
-                for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi[cur][i]);
+                for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi()[i]);
                 __syncwarp();
                 hash_count = cnt;
             }
@@ -582,24 +657,18 @@ struct WarpSearch {
         if (ok)
             ok = iterate<ST>(a.base, a.L, a.W, a.T, a.n_keep, a.it_cool, a.reexpand, st.iters, st.parents,
                              st.dgs_parents, st.vec_rows);
-        uint32_t *oid = a.out_ids + (uint64_t)qi * a.k;
-        float *odist = a.out_dists + (uint64_t)qi * a.k;
+        uint32_t *oid = a.out_ids + (uint64_t)query * a.k;
+        float *odist = a.out_dists + (uint64_t)query * a.k;
         if (ok && a.rerank) {
-            // FP32 distances of the whole queue on the originals, then sort
-            float *rd = bd[cur ^ 1];
-            for (uint32_t b0 = 0; b0 < cnt && ok; b0 += kStageRows) {
-                const uint32_t rows = min(kStageRows, cnt - b0);
-                for (uint32_t i = lane; i < rows; i += 32) ci[i] = bi[cur][b0 + i];
-                __syncwarp();
-                ok = evaluate<ANN_F32>(a.x32, nullptr, a.row32_bytes, rows, rd + b0, false);
-            }
+            // FP32 distances of the whole queue on the originals, then the top k
+            ok = evaluate<ANN_F32>(a.x32, nullptr, a.row32_bytes, bi(), cnt, bd());
             st.rerank_rows += cnt;
             if (ok) {
                 for (uint32_t e = lane; e < cnt; e += 32) {
-                    const float kd = rd[e];
-                    const uint32_t kid = bi[cur][e];
+                    const float kd = bd()[e];
+                    const uint32_t kid = bi()[e];
                     uint32_t r = 0;
-                    for (uint32_t e2 = 0; e2 < cnt; ++e2) r += key_less(rd[e2], bi[cur][e2], kd, kid);
+                    for (uint32_t e2 = 0; e2 < cnt; ++e2) r += key_less(bd()[e2], bi()[e2], kd, kid);
                     if (r < a.k) {
                         oid[r] = kid;
                         odist[r] = kd;
@@ -612,8 +681,8 @@ struct WarpSearch {
             }
         } else if (ok) {
             for (uint32_t j = lane; j < a.k; j += 32) {
-                oid[j] = j < cnt ? bi[cur][j] : ANN_INVALID_ID;
-                odist[j] = j < cnt ? bd[cur][j] : INFINITY;
+                oid[j] = j < cnt ? bi()[j] : ANN_INVALID_ID;
+                odist[j] = j < cnt ? bd()[j] : INFINITY;
             }
         }
         if (!ok) {
@@ -623,7 +692,7 @@ struct WarpSearch {
             }
             st.status = 1;
         }
-        if (a.stats && lane == 0) a.stats[qi] = st;
+        if (a.stats && lane == 0) a.stats[query] = st;
         __syncwarp();
     }
 };
@@ -633,9 +702,8 @@ __global__ void __launch_bounds__(128) search_kernel(const Args a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint8_t *base = smem + (size_t)warp * a.lay.total;
-    WarpSearch<ST> ws(a, base);
-    if (lane == 0) mbar_init(ws.bar, 1);
+    WarpSearch<ST> ws(a, smem + (size_t)warp * a.lay.total);
+    if (lane == 0) mbar_init(ws.bar(), 1);
     fence_mbar_init();
     __syncwarp();
     while (true) {
@@ -650,8 +718,9 @@ __global__ void __launch_bounds__(128) search_kernel(const Args a)
 
 uint32_t align16(uint32_t x) { return (x + 15) & ~15u; }
 
-Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, uint32_t par_cap,
-                   uint32_t adj_words, uint32_t dir_words, uint32_t stage_stride, uint32_t hash_bits)
+Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, uint32_t W, uint32_t adj_words,
+                   uint32_t dir_words, uint32_t prow_bytes, uint32_t stage_rows, uint32_t stage_stride,
+                   uint32_t hash_bits)
 {
     Layout L{};
     uint32_t o = 0;
@@ -661,28 +730,25 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
         return at;
     };
     L.q = take(((d + 31) & ~31u) * 4);
-    for (int s = 0; s < 2; ++s) {
-        L.bd[s] = take(cap_buf * 4);
-        L.bi[s] = take(cap_buf * 4);
-        L.bs[s] = take(cap_buf);
-        L.bq[s] = take(cap_buf * w * 4);
-    }
-    L.cd = take(cap_cand * 4);
+    L.bd = take(cap_buf * 4);
+    L.bi = take(cap_buf * 4);
+    L.bs = take(cap_buf);
+    L.cd = take(std::max(cap_cand, cap_buf) * 4);
     L.ci = take(cap_cand * 4);
-    L.cq = take(cap_cand * w * 4);
     L.cs = take(cap_cand * 4);
-    L.ck = take(cap_cand);
     L.adj = take(adj_words * 4);
     L.dir = take(dir_words * 4);
-    L.par = take(par_cap * 4);
-    L.stage = take(kStageRows * stage_stride);
+    L.prow = take(dir_words ? W * prow_bytes : 0);
+    L.pqb = take(W * w * 4);
+    L.par = take(W * 4);
+    L.stage = take(stage_rows * stage_stride);
     L.hash = take((1u << hash_bits) * 4);
     L.bar = take(16);
     L.total = align16(o);
     return L;
 }
 
-uint32_t next_pow2_bits(uint32_t x)
+uint32_t bits_for(uint32_t x)
 {
     uint32_t b = 0;
     while ((1u << b) < x) ++b;
@@ -705,6 +771,12 @@ int blocks_per_sm(int warps, size_t smem)
     cudaFuncSetAttribute(search_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<ST>, warps * 32, smem);
     return nb;
+}
+
+int env_int(const char *name, int dflt)
+{
+    const char *s = getenv(name);
+    return s ? atoi(s) : dflt;
 }
 
 }  // namespace
@@ -793,7 +865,6 @@ ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const
     a.Tg_given = p->ghost_max_iters_given;
     a.g = p->ghost_seeds_out ? p->ghost_seeds_out : Lg;
     a.rerank = p->rerank ? 1 : 0;
-    a.want_bits = (n_keep < deg) ? 1 : 0;
     a.seed = p->seed;
     a.qid_base = p->qid_base;
     a.counter = ix->d_counter;
@@ -805,24 +876,34 @@ ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const
     cap_cand = round_up(cap_cand, 32);
     a.cap_cand = cap_cand;
     const uint32_t adj_words = std::max(W * ix->deg_pad, ix->gdeg_pad);
-    const uint32_t dir_words = n_keep < deg ? W * ix->deg_pad * ix->words : 0;
+    const bool dgs = n_keep < deg;
+    const uint32_t dir_words = dgs ? W * ix->deg_pad * ix->words : 0;
+    a.prow_bytes = ix->row_bytes;
     const uint32_t stage_bytes = std::max(ix->row_bytes, a.rerank ? a.row32_bytes : 0u);
     a.stage_stride = smem_row_stride(stage_bytes);
-    // visited table: at least twice (queue + one iteration's candidates), and
-    // room for a typical search's visits so resets stay rare
+    a.stage_rows = (uint32_t)std::min(32, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
+    // visited table: at least twice (queue + one iteration's candidates);
+    // beyond that as large as fits 16 warps per SM (up to 4096 entries), so
+    // resets stay rare
     const uint32_t need = 2 * (cap_buf + cap_cand);
-    uint32_t hb = std::max(next_pow2_bits(need), next_pow2_bits(std::min(4096u, 32u * L)));
-    if (const char *env = getenv("ANN_HASH_BITS")) {
-        const int v = atoi(env);
-        if (v > 0 && (1u << v) >= need) hb = (uint32_t)v;
+    const uint32_t hb_min = std::max(8u, bits_for(need));
+    uint32_t hb = hb_min;
+    const size_t warp_budget = ix->smem_optin / 4 / 4;  // 4 CTAs of 4 warps
+    while (hb < 12) {
+        const Layout t = make_layout(ix->dim, ix->words, cap_buf, cap_cand, W, adj_words, dir_words, a.prow_bytes,
+                                     a.stage_rows, a.stage_stride, hb + 1);
+        if (t.total > warp_budget) break;
+        ++hb;
     }
+    if (const int v = env_int("ANN_HASH_BITS", 0); v > 0 && (uint32_t)v >= hb_min) hb = (uint32_t)v;
     int warps = 4;
     Layout lay{};
     for (;;) {
-        lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, W, adj_words, dir_words, a.stage_stride, hb);
+        lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, W, adj_words, dir_words, a.prow_bytes, a.stage_rows,
+                          a.stage_stride, hb);
         if ((size_t)lay.total * warps <= ix->smem_optin) break;
         if (warps > 1) { warps /= 2; continue; }
-        if ((1u << (hb - 1)) >= need) { --hb; continue; }
+        if (hb > hb_min) { --hb; continue; }
         set_error("ann_search: per-query state (%u bytes) exceeds shared memory", lay.total);
         return ANN_EINVAL;
     }
@@ -879,7 +960,7 @@ ann_status ann_search_host(ann_index *ix, const float *queries, uint32_t nq, con
     cudaGetDevice(&prev);
     if (prev != ix->device) cudaSetDevice(ix->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t qb = align16((uint32_t)0) + (size_t)nq * ix->dim * 4;
+    const size_t qb = (size_t)nq * ix->dim * 4;
     const size_t gb = (p->entry == ANN_ENTRY_GIVEN_GHOST && given) ? (size_t)nq * n_given * 4 : 0;
     const size_t ob = (size_t)nq * p->k * 4;
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
