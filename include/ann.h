@@ -144,6 +144,24 @@ ann_status ann_search_host(ann_index *index, const float *queries, uint32_t nq,
                            const ann_search_params *params, const uint32_t *given_seeds, uint32_t n_given,
                            uint32_t *ids, float *dists, void *stream);
 
+/* The paper has no counterpart to this call. ann_search_host without any
+ * device allocation, for callers that must not allocate device memory on
+ * their request path (a server that reserves all device memory at start-up,
+ * code under an external memory budget, a host thread with a deadline that
+ * cannot afford the device synchronisation cudaMalloc/cudaFree may cause).
+ * Queries, results, the kernel's work counter and its error word live in one
+ * fixed device array of ANN_NOALLOC_SCRATCH_BYTES per GPU, held until the
+ * process exits. A call needing more staging than that (256 + nq*dim*4 +
+ * 2*nq*k*4 bytes, parts rounded up to 256) returns ANN_EINVAL: split the
+ * batch. All calls on a device share the array, so calls that overlap on the
+ * GPU (other streams or host threads) race; each call clears what it relies
+ * on. The first call on a device looks up the array's address there; make it
+ * before any stream capture. Given ghost seeds are not supported here.
+ * Synchronous: returns after the results are in the host buffers. */
+#define ANN_NOALLOC_SCRATCH_BYTES (8u << 20)
+ann_status ann_search_host_noalloc(ann_index *index, const float *queries, uint32_t nq,
+                                   const ann_search_params *params, uint32_t *ids, float *dists, void *stream);
+
 /* Synchronise `stream` and report (then clear) the index's device error
  * word: ANN_OK, or ANN_ETIMEOUT if a bounded device wait ran out. */
 ann_status ann_sync(ann_index *index, void *stream);

@@ -57,6 +57,12 @@ ann_status cuda_fail(cudaError_t e, const char *what);
 
 inline uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
 
+// The search launch (search.cu) with caller-chosen device scratch: the work
+// counter (zeroed on `stream` before the launch) and the error word.
+ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
+                            const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
+                            ann_query_stats *stats, cudaStream_t stream, uint32_t *counter, int *err);
+
 // Device row stride for `bytes` of payload: a multiple of 16 bytes (the
 // bulk-copy granule).
 inline uint32_t row_stride(uint32_t bytes) { return round_up(bytes, 16); }

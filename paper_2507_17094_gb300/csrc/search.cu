@@ -783,10 +783,11 @@ int env_int(const char *name, int dflt)
 
 namespace ann {
 
-// Validates parameters, derives the method's counts and launches the search.
-ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
-                         const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
-                         ann_query_stats *stats, cudaStream_t stream)
+// Validates parameters, derives the method's counts and launches the search
+// with the given work counter and error word (device memory).
+ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
+                            const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
+                            ann_query_stats *stats, cudaStream_t stream, uint32_t *counter, int *err)
 {
     if (!ix || !p) { set_error("ann_search: NULL index or params"); return ANN_EINVAL; }
     const uint32_t L = p->itopk, W = p->search_width, deg = ix->degree;
@@ -867,8 +868,8 @@ ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const
     a.rerank = p->rerank ? 1 : 0;
     a.seed = p->seed;
     a.qid_base = p->qid_base;
-    a.counter = ix->d_counter;
-    a.err = ix->d_error;
+    a.counter = counter;
+    a.err = err;
 
     const uint32_t cap_buf = std::max(L, a.entry != ANN_ENTRY_RANDOM ? Lg : 1u);
     uint32_t cap_cand = std::max(W * deg, 32u);
@@ -922,7 +923,7 @@ ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const
     }
     const uint64_t want = ((uint64_t)nq + warps - 1) / warps;
     const int blocks = (int)std::min<uint64_t>(want, (uint64_t)nb * ix->num_sms);
-    ANN_CUDA(cudaMemsetAsync(ix->d_counter, 0, sizeof(uint32_t), stream));
+    ANN_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream));
     cudaError_t e;
     switch (ix->storage) {
     case ANN_F32: e = launch<ANN_F32>(a, warps, blocks, smem, stream); break;
@@ -931,6 +932,16 @@ ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const
     }
     if (e != cudaSuccess) return cuda_fail(e, "search_kernel launch");
     return ANN_OK;
+}
+
+// The search with the index's own work counter and error word.
+ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
+                         const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
+                         ann_query_stats *stats, cudaStream_t stream)
+{
+    if (!ix) { set_error("ann_search: NULL index or params"); return ANN_EINVAL; }
+    return search_launch_ex(ix, queries, nq, p, given, n_given, ids, dists, stats, stream, ix->d_counter,
+                            ix->d_error);
 }
 
 }  // namespace ann
