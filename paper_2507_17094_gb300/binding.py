@@ -25,8 +25,9 @@ STATUS = {0: "ANN_OK", 1: "ANN_EINVAL", 2: "ANN_ENOMEM", 3: "ANN_ECUDA", 4: "ANN
 
 # Every symbol include/ann.h declares (checked by the tests).
 EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_index_free", "ann_index_info",
-           "ann_index_export", "ann_search", "ann_search_host", "ann_sync", "ann_encode", "ann_dir_table",
-           "ann_last_error")
+           "ann_index_export", "ann_search", "ann_search_host", "ann_search_host_noalloc", "ann_sync",
+           "ann_encode", "ann_dir_table", "ann_mlp_create", "ann_mlp_free", "ann_mlp_set_params", "ann_mlp_get",
+           "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_predict", "ann_mlp_sync", "ann_last_error")
 
 
 class AnnError(RuntimeError):
@@ -71,12 +72,23 @@ def lib() -> C.CDLL:
             L.ann_index_export.argtypes = [vp, C.c_int, vp, u64]
             L.ann_search.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp, vp]
             L.ann_search_host.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp]
+            L.ann_search_host_noalloc.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, vp, vp]
             L.ann_sync.argtypes = [vp, vp]
+            f32 = C.c_float
+            L.ann_mlp_create.argtypes = [C.c_int, u32, u32, u32, u32, u32, C.POINTER(vp)]
+            L.ann_mlp_free.argtypes = [vp]
+            L.ann_mlp_set_params.argtypes = [vp] * 7
+            L.ann_mlp_get.argtypes = [vp, C.c_int] + [vp] * 6
+            L.ann_mlp_forward.argtypes = [vp, vp, u32, vp, vp]
+            L.ann_mlp_train_step.argtypes = [vp, vp, vp, u32, f32, f32, f32, f32, f32, vp, vp]
+            L.ann_mlp_predict.argtypes = [vp, vp, u32, u32, f32, vp, vp, vp]
+            L.ann_mlp_sync.argtypes = [vp, vp]
             L.ann_encode.argtypes = [vp, u64, u32, C.c_int, vp, vp, vp]
             L.ann_dir_table.argtypes = [vp, vp, C.c_int, u64, u32, vp, u32, vp, vp]
             L.ann_last_error.restype = C.c_char_p
-            for f in ("ann_index_create", "ann_index_load", "ann_index_free", "ann_index_info", "ann_index_export",
-                      "ann_search", "ann_search_host", "ann_sync", "ann_encode", "ann_dir_table"):
+            for f in EXPORTS:
+                if f in ("ann_default_params", "ann_last_error"):
+                    continue
                 getattr(L, f).restype = st
             _lib = L
         return _lib
@@ -198,8 +210,82 @@ class Index:
                                      _stream_ptr(stream)))
         return ids, dists
 
+    def search_host_noalloc(self, queries: np.ndarray, stream=None, **params):
+        """The host-buffer search through the entry point that allocates no
+        device memory (fixed per-device scratch; see include/ann.h)."""
+        p = make_params(**params)
+        Q = np.ascontiguousarray(queries, dtype=np.float32)
+        nq = Q.shape[0]
+        ids = np.empty((nq, p.k), dtype=np.uint32)
+        dists = np.empty((nq, p.k), dtype=np.float32)
+        _check(lib().ann_search_host_noalloc(self._h, _np_ptr(Q), nq, C.byref(p), _np_ptr(ids), _np_ptr(dists),
+                                             _stream_ptr(stream)))
+        return ids, dists
+
     def sync(self, stream=None):
         _check(lib().ann_sync(self._h, _stream_ptr(stream)))
+
+
+class MLP:
+    """The learned-entry network (device-resident; see include/ann.h)."""
+
+    def __init__(self, in_dim: int, hidden1: int, hidden2: int, out_dim: int, max_batch: int, device: int = 0):
+        self._h = C.c_void_p()
+        _check(lib().ann_mlp_create(device, in_dim, hidden1, hidden2, out_dim, max_batch, C.byref(self._h)))
+        self.dims = (in_dim, hidden1, hidden2, out_dim)
+        self.max_batch = max_batch
+
+    def close(self):
+        if self._h:
+            lib().ann_mlp_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shapes(self):
+        d, h1, h2, o = self.dims
+        return [(h1, d), (h1,), (h2, h1), (h2,), (o, h2), (o,)]
+
+    def set_params(self, W1, b1, W2, b2, W3, b3):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (W1, b1, W2, b2, W3, b3)]
+        for a, shp in zip(arrs, self._shapes()):
+            assert a.shape == shp, (a.shape, shp)
+        _check(lib().ann_mlp_set_params(self._h, *[_np_ptr(a) for a in arrs]))
+
+    def get(self, which: int = 0):
+        """Parameters (0) or last gradients (1) as six float32 arrays."""
+        out = [np.empty(shp, dtype=np.float32) for shp in self._shapes()]
+        _check(lib().ann_mlp_get(self._h, which, *[_np_ptr(a) for a in out]))
+        return out
+
+    def forward(self, x, stream=None):
+        import torch
+        n = x.shape[0]
+        z = torch.empty((n, self.dims[3]), dtype=torch.float32, device=x.device)
+        _check(lib().ann_mlp_forward(self._h, x.data_ptr(), n, z.data_ptr(), _stream_ptr(stream)))
+        return z
+
+    def train_step(self, x, labels, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, loss=None,
+                   stream=None):
+        _check(lib().ann_mlp_train_step(self._h, x.data_ptr(), labels.data_ptr(), x.shape[0], lr, beta1, beta2,
+                                        eps, weight_decay, None if loss is None else loss.data_ptr(),
+                                        _stream_ptr(stream)))
+
+    def predict(self, x, P: int = 8, tau: float = 0.0, stream=None):
+        import torch
+        n = x.shape[0]
+        seeds = torch.empty((n, P), dtype=torch.int32, device=x.device)
+        pmax = torch.empty((n,), dtype=torch.float32, device=x.device)
+        _check(lib().ann_mlp_predict(self._h, x.data_ptr(), n, P, tau, seeds.data_ptr(), pmax.data_ptr(),
+                                     _stream_ptr(stream)))
+        return seeds, pmax
+
+    def sync(self, stream=None):
+        _check(lib().ann_mlp_sync(self._h, _stream_ptr(stream)))
 
 
 def stats_to_numpy(st) -> np.ndarray:

@@ -1,0 +1,153 @@
+"""Learned-entry MLP on the GPU (tcgen05 GEMMs) against the FP64 oracle.
+
+Tolerances. The GPU and the oracle feed identical BF16 operands to every
+contraction; the GPU accumulates in FP32 (error <= K * 2^-24 relative to the
+sum of |products|) and the oracle in FP64. Hidden activations are rounded to
+BF16 on both sides, so where the two sums straddle a BF16 rounding boundary
+an activation differs by one BF16 ulp (2^-8 relative). Logits are therefore
+checked elementwise against 2^-7 times the sum of |products| of the last
+layer, and gradients (which pass through two such roundings) by relative
+Frobenius norm 1e-2.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import paper_2507_17094_gb300 as A
+    assert torch.cuda.is_available()
+    A.build()
+
+
+def make_model(d, h1, h2, out, seed):
+    rng = np.random.default_rng(seed)
+    he = lambda fan: np.sqrt(2.0 / fan)  # noqa: E731
+    return M.MLP((rng.standard_normal((h1, d)) * he(d)).astype(np.float32),
+                 (rng.standard_normal(h1) * 0.1).astype(np.float32),
+                 (rng.standard_normal((h2, h1)) * he(h1)).astype(np.float32),
+                 (rng.standard_normal(h2) * 0.1).astype(np.float32),
+                 (rng.standard_normal((out, h2)) * he(h2)).astype(np.float32),
+                 (rng.standard_normal(out) * 0.1).astype(np.float32))
+
+
+def gpu_mlp(m, max_batch):
+    import paper_2507_17094_gb300 as A
+    d, h1, h2, out = m.W1.shape[1], m.W1.shape[0], m.W2.shape[0], m.W3.shape[0]
+    g = A.MLP(d, h1, h2, out, max_batch)
+    g.set_params(m.W1, m.b1, m.W2, m.b2, m.W3, m.b3)
+    return g
+
+
+@pytest.mark.parametrize("dims", [(96, 256, 128, 1000, 300), (256, 512, 512, 2048, 1024), (64, 128, 128, 128, 8)])
+def test_forward_logits_vs_oracle(dims):
+    d, h1, h2, out, n = dims
+    m = make_model(d, h1, h2, out, seed=1)
+    X = np.random.default_rng(2).standard_normal((n, d)).astype(np.float32)
+    g = gpu_mlp(m, max(8, (n + 7) // 8 * 8))
+    z = g.forward(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    g.sync()
+    f = M.forward(m, X)
+    scale = np.abs(f["h2q"]) @ np.abs(M.bf16_round(m.W3).astype(np.float64)).T + np.abs(m.b3)
+    err = np.abs(z.cpu().numpy().astype(np.float64) - f["z"])
+    assert (err <= 2.0 ** -7 * scale + 1e-5).all(), float((err / (scale + 1e-12)).max())
+    g.close()
+
+
+def test_gradients_vs_oracle():
+    d, h1, h2, out, n = 96, 256, 128, 1000, 64
+    m = make_model(d, h1, h2, out, seed=3)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    y = rng.integers(0, out, n).astype(np.uint32)
+    g = gpu_mlp(m, n)
+    loss = torch.zeros(1, device="cuda")
+    g.train_step(torch.from_numpy(X).cuda(), torch.from_numpy(y.view(np.int32)).cuda(), lr=0.0, loss=loss)
+    torch.cuda.synchronize()
+    g.sync()
+    want = M.gradients(m, X, y.astype(np.int64))
+    got = dict(zip(M.LAYERS, g.get(1)))
+    for k in M.LAYERS:
+        rel = np.linalg.norm(got[k] - want[k]) / (np.linalg.norm(want[k]) + 1e-30)
+        assert rel < 1e-2, (k, rel)
+    assert abs(loss.item() - M.loss(m, X, y.astype(np.int64))) < 1e-3 * max(1.0, M.loss(m, X, y.astype(np.int64)))
+    # lr = 0 leaves the parameters unchanged
+    p = g.get(0)
+    assert all(np.array_equal(a, b) for a, b in zip(p, m.params().values()))
+    g.close()
+
+
+def test_adamw_matches_oracle_on_the_gpu_gradients():
+    d, h1, h2, out, n = 64, 128, 128, 256, 32
+    m = make_model(d, h1, h2, out, seed=5)
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    y = rng.integers(0, out, n).astype(np.uint32)
+    g = gpu_mlp(m, n)
+    opt = M.AdamW(lr=1e-2, wd=0.01)
+    ref = m.copy()
+    Xt, yt = torch.from_numpy(X).cuda(), torch.from_numpy(y.view(np.int32)).cuda()
+    for _ in range(3):
+        g.train_step(Xt, yt, lr=1e-2, weight_decay=0.01)
+        torch.cuda.synchronize()
+        grads = dict(zip(M.LAYERS, g.get(1)))
+        opt.step(ref, grads)
+        got = dict(zip(M.LAYERS, g.get(0)))
+        for k in M.LAYERS:
+            np.testing.assert_allclose(got[k], getattr(ref, k), rtol=1e-5, atol=1e-6)
+        ref = M.MLP(**{k: got[k].copy() for k in M.LAYERS})   # continue from the GPU's own weights
+    g.close()
+
+
+@pytest.mark.parametrize("P", [1, 8])
+def test_fused_top_p_equals_top_p_of_materialised_logits(P):
+    d, h1, h2, out, n = 96, 256, 256, 3000, 500
+    m = make_model(d, h1, h2, out, seed=7)
+    X = np.random.default_rng(8).standard_normal((n, d)).astype(np.float32)
+    g = gpu_mlp(m, 512)
+    Xt = torch.from_numpy(X).cuda()
+    z = g.forward(Xt).cpu().numpy()
+    seeds, pmax = g.predict(Xt, P=P, tau=0.0)
+    torch.cuda.synchronize()
+    g.sync()
+    ids, pm = M.top_p(z.astype(np.float64), P)
+    assert np.array_equal(seeds.cpu().numpy().view(np.uint32), ids)
+    np.testing.assert_allclose(pmax.cpu().numpy(), pm, rtol=1e-4)
+    # fallback: rows below tau start with ANN_INVALID_ID
+    tau = float(np.median(pm))
+    s2, p2 = g.predict(Xt, P=P, tau=tau)
+    s2 = s2.cpu().numpy().view(np.uint32)
+    low = p2.cpu().numpy() < tau
+    assert low.any() and (~low).any()
+    assert (s2[low, 0] == 0xFFFFFFFF).all() and np.array_equal(s2[~low], ids[~low])
+    g.close()
+
+
+def test_training_reduces_loss():
+    # labels = the nearest of 64 random prototypes: learnable
+    d, out, n = 96, 64, 1024
+    rng = np.random.default_rng(9)
+    protos = rng.standard_normal((out, d)).astype(np.float32)
+    X = (protos[rng.integers(0, out, 4096)] + 0.3 * rng.standard_normal((4096, d))).astype(np.float32)
+    y = np.argmin(((X[:, None, :] - protos[None]) ** 2).sum(-1), axis=1).astype(np.uint32)
+    m = make_model(d, 256, 256, out, seed=10)
+    g = gpu_mlp(m, n)
+    Xt, yt = torch.from_numpy(X).cuda(), torch.from_numpy(y.view(np.int32)).cuda()
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for ep in range(15):
+        for b in range(0, 4096, n):
+            g.train_step(Xt[b:b + n], yt[b:b + n], lr=2e-3, loss=loss)
+        losses.append(loss.item())
+    g.sync()
+    assert losses[-1] < 0.2 * losses[0], losses
+    seeds, _ = g.predict(Xt, P=1)
+    acc = (seeds.cpu().numpy()[:, 0].view(np.uint32) == y).mean()
+    assert acc > 0.9, acc
+    g.close()
