@@ -162,6 +162,11 @@ ann_status ann_search_host(ann_index *index, const float *queries, uint32_t nq,
 ann_status ann_search_host_noalloc(ann_index *index, const float *queries, uint32_t nq,
                                    const ann_search_params *params, uint32_t *ids, float *dists, void *stream);
 
+/* Ghost index of each node id (device ids, n) by binary search over the
+ * ascending ghost ids, into out (device, n); ANN_INVALID_ID where an id is
+ * not a ghost node. Turns ghost-staging results into training labels. */
+ann_status ann_ghost_index_of(const ann_index *index, const uint32_t *ids, uint32_t n, uint32_t *out, void *stream);
+
 /* Synchronise `stream` and report (then clear) the index's device error
  * word: ANN_OK, or ANN_ETIMEOUT if a bounded device wait ran out. */
 ann_status ann_sync(ann_index *index, void *stream);
@@ -214,8 +219,61 @@ ann_status ann_mlp_train_step(ann_mlp *mlp, const float *x, const uint32_t *labe
  * (n x out_dim) logits are never written to memory. */
 ann_status ann_mlp_predict(ann_mlp *mlp, const float *x, uint32_t n, uint32_t P, float tau, uint32_t *seeds,
                            float *pmax, void *stream);
+/* Epochs of minibatch AdamW over (x, labels) (device, n rows, n >= 8): each
+ * epoch visits the rows in a fresh seeded order, in batches of `batch` (a
+ * multiple of 8 <= max_batch); epoch_loss (host, `epochs` floats, may be
+ * NULL) receives each epoch's mean batch loss. Synchronous. */
+ann_status ann_mlp_train_epochs(ann_mlp *mlp, const float *x, const uint32_t *labels, uint32_t n, uint32_t batch,
+                                uint32_t epochs, float lr, float beta1, float beta2, float eps, float weight_decay,
+                                uint64_t seed, float *epoch_loss, void *stream);
 /* Synchronise `stream` and report (then clear) the MLP's device error word. */
 ann_status ann_mlp_sync(ann_mlp *mlp, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Continuous-batching server (not in the paper). Requests (batches of any
+ * size, each with its own ann_search_params up to the server's max_params)
+ * are admitted while others run and share the GPU query by query: one device
+ * ring of query slots, a FIFO that the warps of every running search kernel
+ * take queries from, per-warp queue and visited state resident in shared
+ * memory while a query runs. Admission is by buffer memory: submit returns
+ * ANN_EBUSY when the ring or the request records are full (poll, then retry).
+ * Results are deterministic per request (the RNG stream is qid_base + the
+ * query's index within its request), so a request's answer is the same alone
+ * or in any mix. One host thread drives a server.
+ * ------------------------------------------------------------------------ */
+typedef struct ann_server ann_server;
+
+typedef struct {
+    uint32_t capacity;            /* query slots resident on the device */
+    uint32_t max_requests;        /* requests in flight */
+    ann_search_params max_params; /* largest k, itopk, search_width, ghost_itopk of any request, and the
+                                     features allowed (DGS if dgs_discard > 0, rerank, entry != random) */
+    uint32_t seeds_per_query;     /* learned entry (max_params.entry == ANN_ENTRY_GIVEN_GHOST): P, 1..8 */
+    float tau;                    /* learned entry: fallback threshold on the top softmax probability */
+    uint32_t queries_per_warp;    /* queries a warp serves before its kernel may end; 0 = 4 */
+    uint32_t streams;             /* compute streams; 0 = 4 */
+} ann_server_config;
+
+typedef struct {
+    uint64_t req_id;
+    uint32_t status;      /* ANN_OK */
+    uint32_t nq;
+    double latency_s;     /* submit -> completion observed by ann_server_poll */
+} ann_completion;
+
+/* mlp: the learned entry (required when max_params.entry is ANN_ENTRY_GIVEN_GHOST, else NULL);
+ * requests with entry ANN_ENTRY_GIVEN_GHOST get their ghost seeds from it. */
+ann_status ann_server_create(ann_index *index, const ann_server_config *config, ann_mlp *mlp, ann_server **out);
+/* Admit one request: queries (host, nq x dim FP32) are copied in before the
+ * call returns; ids / dists (host, nq x k) are filled by ann_server_poll when
+ * the request completes and must stay valid until then. */
+ann_status ann_server_submit(ann_server *server, uint64_t req_id, const float *queries, uint32_t nq,
+                             const ann_search_params *params, uint32_t *ids, float *dists);
+/* Collect up to `max` completed requests (their results are in place). */
+ann_status ann_server_poll(ann_server *server, ann_completion *out, uint32_t max, uint32_t *n_out);
+/* Requests submitted and not yet collected by ann_server_poll's bookkeeping. */
+uint32_t ann_server_in_flight(const ann_server *server);
+ann_status ann_server_destroy(ann_server *server);
 
 /* Thread-local message for the last failing call on this thread. */
 const char *ann_last_error(void);

@@ -27,7 +27,9 @@ STATUS = {0: "ANN_OK", 1: "ANN_EINVAL", 2: "ANN_ENOMEM", 3: "ANN_ECUDA", 4: "ANN
 EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_index_free", "ann_index_info",
            "ann_index_export", "ann_search", "ann_search_host", "ann_search_host_noalloc", "ann_sync",
            "ann_encode", "ann_dir_table", "ann_mlp_create", "ann_mlp_free", "ann_mlp_set_params", "ann_mlp_get",
-           "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_predict", "ann_mlp_sync", "ann_last_error")
+           "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_train_epochs", "ann_mlp_predict", "ann_mlp_sync",
+           "ann_ghost_index_of", "ann_server_create", "ann_server_submit", "ann_server_poll",
+           "ann_server_in_flight", "ann_server_destroy", "ann_last_error")
 
 
 class AnnError(RuntimeError):
@@ -43,6 +45,16 @@ class SearchParams(C.Structure):
                 ("ghost_itopk", C.c_uint32), ("ghost_max_iters", C.c_uint32),
                 ("ghost_max_iters_given", C.c_uint32), ("ghost_seeds_out", C.c_uint32),
                 ("rerank", C.c_uint32), ("seed", C.c_uint64), ("qid_base", C.c_uint64)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("capacity", C.c_uint32), ("max_requests", C.c_uint32), ("max_params", SearchParams),
+                ("seeds_per_query", C.c_uint32), ("tau", C.c_float), ("queries_per_warp", C.c_uint32),
+                ("streams", C.c_uint32)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("req_id", C.c_uint64), ("status", C.c_uint32), ("nq", C.c_uint32), ("latency_s", C.c_double)]
 
 
 STATS_FIELDS = ("iters", "parents", "dgs_parents", "vec_rows", "ghost_iters", "ghost_parents",
@@ -83,11 +95,19 @@ def lib() -> C.CDLL:
             L.ann_mlp_train_step.argtypes = [vp, vp, vp, u32, f32, f32, f32, f32, f32, vp, vp]
             L.ann_mlp_predict.argtypes = [vp, vp, u32, u32, f32, vp, vp, vp]
             L.ann_mlp_sync.argtypes = [vp, vp]
+            L.ann_mlp_train_epochs.argtypes = [vp, vp, vp, u32, u32, u32, f32, f32, f32, f32, f32, u64, vp, vp]
+            L.ann_ghost_index_of.argtypes = [vp, vp, u32, vp, vp]
+            L.ann_server_create.argtypes = [vp, C.POINTER(ServerConfig), vp, C.POINTER(vp)]
+            L.ann_server_submit.argtypes = [vp, u64, vp, u32, C.POINTER(SearchParams), vp, vp]
+            L.ann_server_poll.argtypes = [vp, C.POINTER(Completion), u32, C.POINTER(u32)]
+            L.ann_server_in_flight.argtypes = [vp]
+            L.ann_server_in_flight.restype = u32
+            L.ann_server_destroy.argtypes = [vp]
             L.ann_encode.argtypes = [vp, u64, u32, C.c_int, vp, vp, vp]
             L.ann_dir_table.argtypes = [vp, vp, C.c_int, u64, u32, vp, u32, vp, vp]
             L.ann_last_error.restype = C.c_char_p
             for f in EXPORTS:
-                if f in ("ann_default_params", "ann_last_error"):
+                if f in ("ann_default_params", "ann_last_error", "ann_server_in_flight"):
                     continue
                 getattr(L, f).restype = st
             _lib = L
@@ -225,6 +245,14 @@ class Index:
     def sync(self, stream=None):
         _check(lib().ann_sync(self._h, _stream_ptr(stream)))
 
+    def ghost_index_of(self, ids, stream=None):
+        """Ghost index of each node id (CUDA int32 tensor); INVALID if not a ghost."""
+        import torch
+        flat = ids.reshape(-1).contiguous()
+        out = torch.empty_like(flat)
+        _check(lib().ann_ghost_index_of(self._h, flat.data_ptr(), flat.numel(), out.data_ptr(), _stream_ptr(stream)))
+        return out.reshape(ids.shape)
+
 
 class MLP:
     """The learned-entry network (device-resident; see include/ann.h)."""
@@ -275,6 +303,14 @@ class MLP:
                                         eps, weight_decay, None if loss is None else loss.data_ptr(),
                                         _stream_ptr(stream)))
 
+    def train_epochs(self, x, labels, batch: int = 1024, epochs: int = 1, lr=1e-3, beta1=0.9, beta2=0.999,
+                     eps=1e-8, weight_decay=0.0, seed: int = 0, stream=None) -> np.ndarray:
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(lib().ann_mlp_train_epochs(self._h, x.data_ptr(), labels.data_ptr(), x.shape[0], batch, epochs, lr,
+                                          beta1, beta2, eps, weight_decay, seed, _np_ptr(losses),
+                                          _stream_ptr(stream)))
+        return losses
+
     def predict(self, x, P: int = 8, tau: float = 0.0, stream=None):
         import torch
         n = x.shape[0]
@@ -314,3 +350,79 @@ def dir_table(vectors, scales, storage: int, graph, stream=None):
     _check(lib().ann_dir_table(vectors.data_ptr(), None if scales is None else scales.data_ptr(), storage, n, d,
                                graph.data_ptr(), deg, out.data_ptr(), _stream_ptr(stream)))
     return out
+
+
+class Server:
+    """Continuous-batching server over an index (see include/ann.h)."""
+
+    def __init__(self, index: Index, capacity: int, max_requests: int, max_params: dict, mlp: "MLP" = None,
+                 seeds_per_query: int = 8, tau: float = 0.0, queries_per_warp: int = 0, streams: int = 0):
+        cfg = ServerConfig(capacity, max_requests, make_params(**max_params), seeds_per_query, tau,
+                           queries_per_warp, streams)
+        self._h = C.c_void_p()
+        _check(lib().ann_server_create(index._h, C.byref(cfg), None if mlp is None else mlp._h, C.byref(self._h)))
+        self.index = index
+        self._keep = {}
+
+    def submit(self, req_id: int, queries: np.ndarray, **params) -> bool:
+        """Admit a request; False when the server is full (ANN_EBUSY)."""
+        p = make_params(**params)
+        Q = np.ascontiguousarray(queries, dtype=np.float32)
+        ids = np.empty((Q.shape[0], p.k), dtype=np.uint32)
+        dists = np.empty((Q.shape[0], p.k), dtype=np.float32)
+        st = lib().ann_server_submit(self._h, req_id, _np_ptr(Q), Q.shape[0], C.byref(p), _np_ptr(ids),
+                                     _np_ptr(dists))
+        if st == 6:
+            return False
+        _check(st)
+        self._keep[req_id] = (ids, dists)
+        return True
+
+    def poll(self, max_n: int = 256):
+        """Completed requests: list of (req_id, ids, dists, latency_s)."""
+        buf = (Completion * max_n)()
+        n = C.c_uint32()
+        _check(lib().ann_server_poll(self._h, buf, max_n, C.byref(n)))
+        out = []
+        for i in range(n.value):
+            ids, dists = self._keep.pop(buf[i].req_id)
+            out.append((buf[i].req_id, ids, dists, buf[i].latency_s))
+        return out
+
+    def in_flight(self) -> int:
+        return int(lib().ann_server_in_flight(self._h))
+
+    def close(self):
+        if self._h:
+            lib().ann_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def replay(server: Server, trace, timeout_s: float = 120.0):
+    """Drive `server` with a trace of (arrival_s, req_id, queries, params):
+    submit each request at its arrival time (retrying while the server is
+    full), collect completions. Returns {req_id: (ids, dists, latency_s)} and
+    the wall time from the first arrival to the last completion."""
+    import time
+    results = {}
+    pending = sorted(trace, key=lambda t: t[0])
+    t0 = time.perf_counter()
+    i = 0
+    while len(results) < len(trace):
+        now = time.perf_counter() - t0
+        while i < len(pending) and pending[i][0] <= now:
+            _, rid, q, prm = pending[i]
+            if not server.submit(rid, q, **prm):
+                break
+            i += 1
+        for rid, ids, dists, lat in server.poll():
+            results[rid] = (ids, dists, lat)
+        if time.perf_counter() - t0 > timeout_s:
+            raise TimeoutError(f"serving trace did not finish: {len(results)}/{len(trace)} done")
+    return results, time.perf_counter() - t0

@@ -57,6 +57,43 @@ ann_status cuda_fail(cudaError_t e, const char *what);
 
 inline uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
 
+// Per-query search parameters (derived from ann_search_params).
+struct QParams {
+    uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank, n_given, pad;
+    uint64_t seed, qid_base;
+};
+
+// One request in the serving ring (device memory).
+struct ServeReq {
+    QParams qp;
+    uint32_t nq, slot0, done, flag;
+};
+
+// The serving ring as the serve kernel sees it.
+struct ServeRing {
+    const float *queries;            // cap x dim
+    const uint32_t *seeds;           // cap x P (learned entry) or NULL
+    uint32_t P;
+    uint32_t *ids;                   // cap x kmax
+    float *dists;                    // cap x kmax
+    const uint32_t *slot_req;        // cap: request-ring index of each slot
+    ServeReq *reqs;
+    unsigned long long *head;        // next query to take
+    const unsigned long long *tail;  // queries published
+    volatile uint32_t *flags;        // host-mapped completion flags
+    uint32_t cap, kmax, per_warp;
+};
+
+// Validate `p` against the index and derive the per-query parameters.
+ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint32_t n_given, QParams *out);
+
+// A serve-kernel launch plan sized for the largest parameters `maxp`
+// (opaque; free with serve_plan_free).
+ann_status serve_plan(ann_index *ix, const ann_search_params *maxp, uint32_t n_given_max, void **plan);
+void serve_plan_free(void *plan);
+// Launch a serve kernel with capacity for at least `queries` queries.
+ann_status serve_launch(void *plan, const ServeRing &ring, uint32_t queries, cudaStream_t stream);
+
 // The search launch (search.cu) with caller-chosen device scratch: the work
 // counter (zeroed on `stream` before the launch) and the error word.
 ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,

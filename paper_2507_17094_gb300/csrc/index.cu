@@ -151,6 +151,23 @@ __global__ void gather_rows_kernel(const uint8_t *__restrict__ codes, const floa
     }
 }
 
+// Ghost index of each id by binary search over the ascending ghost ids;
+// ANN_INVALID_ID where the id is not a ghost node.
+__global__ void ghost_index_kernel(const uint32_t *__restrict__ ghost_ids, uint32_t m,
+                                   const uint32_t *__restrict__ ids, uint32_t n, uint32_t *__restrict__ out)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t v = ids[i];
+        uint32_t lo = 0, hi = m;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (ghost_ids[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        out[i] = (lo < m && ghost_ids[lo] == v) ? lo : ANN_INVALID_ID;
+    }
+}
+
 // ---------------------------------------------------------------- host
 static int grid_for(uint64_t items, int warps_per_block, int num_sms)
 {
@@ -467,6 +484,18 @@ ann_status ann_index_export(const ann_index *ix, int which, void *dst, uint64_t 
         return ANN_EINVAL;
     }
     ANN_CUDA(cudaMemcpy2D(dst, width, src, pitch, width, rows, cudaMemcpyDeviceToHost));
+    return ANN_OK;
+}
+
+ann_status ann_ghost_index_of(const ann_index *ix, const uint32_t *ids, uint32_t n, uint32_t *out, void *stream)
+{
+    if (!ix || (n && (!ids || !out))) { set_error("ann_ghost_index_of: NULL argument"); return ANN_EINVAL; }
+    if (!ix->n_ghost) { set_error("ann_ghost_index_of: the index has no ghost set"); return ANN_EINVAL; }
+    if (n == 0) return ANN_OK;
+    DeviceGuard g(ix->device);
+    ghost_index_kernel<<<(int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ix->num_sms * 8), 256, 0,
+                         (cudaStream_t)stream>>>(ix->ghost_ids, ix->n_ghost, ids, n, out);
+    ANN_CUDA(cudaGetLastError());
     return ANN_OK;
 }
 

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "ann_internal.cuh"
 
@@ -429,6 +430,31 @@ __global__ void topp_merge_kernel(const float *__restrict__ part, uint32_t M, ui
     }
 }
 
+// Rows perm[0, n) of x (and their labels) into contiguous batch buffers.
+__global__ void gather_batch_kernel(const float *__restrict__ x, const uint32_t *__restrict__ y,
+                                    const uint32_t *__restrict__ perm, uint32_t n, uint32_t d,
+                                    float *__restrict__ xb, uint32_t *__restrict__ yb)
+{
+    const uint32_t r = blockIdx.x;
+    if (r >= n) return;
+    const uint32_t src = perm[r];
+    for (uint32_t c = threadIdx.x; c < d; c += blockDim.x) xb[(size_t)r * d + c] = x[(size_t)src * d + c];
+    if (threadIdx.x == 0) yb[r] = y[src];
+}
+
+__global__ void accumulate_kernel(float *__restrict__ acc, const float *__restrict__ v, float w)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *acc += w * *v;
+}
+
+uint64_t mix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host side
@@ -440,6 +466,10 @@ struct ann_mlp {
     __nv_bfloat16 *xb = nullptr, *xT = nullptr, *h1b = nullptr, *h1T = nullptr, *h2b = nullptr, *h2T = nullptr;
     __nv_bfloat16 *dzb = nullptr, *dzT = nullptr, *da2b = nullptr, *da2T = nullptr, *da1T = nullptr;
     float *z = nullptr, *dh = nullptr, *dm = nullptr, *loss = nullptr, *part = nullptr;
+    float *xbat = nullptr, *epoch_loss = nullptr;
+    uint32_t *ybat = nullptr, *perm = nullptr;
+    size_t perm_cap = 0;
+    uint32_t train_cap = 0;
     size_t part_cap = 0;
     uint32_t step = 0;
     int *d_error = nullptr;
@@ -518,6 +548,37 @@ ann_status transpose(const __nv_bfloat16 *in, __nv_bfloat16 *out, uint32_t R, ui
     return ANN_OK;
 }
 
+// Training-only buffers for batches of up to train_cap rows (grown once).
+ann_status ensure_train_buffers(ann_mlp *m, uint32_t n)
+{
+    if (n <= m->train_cap) return ANN_OK;
+    __nv_bfloat16 **bf[] = {&m->xT, &m->h1T, &m->h2T, &m->dzb, &m->dzT, &m->da2b, &m->da2T, &m->da1T};
+    float **fp[] = {&m->z, &m->dh, &m->dm, &m->xbat};
+    for (auto p : bf) if (*p) { cudaFree(*p); *p = nullptr; }
+    for (auto p : fp) if (*p) { cudaFree(*p); *p = nullptr; }
+    if (m->ybat) { cudaFree(m->ybat); m->ybat = nullptr; }
+    m->train_cap = 0;
+    const size_t B = n;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+    al((void **)&m->xT, B * m->d * 2);
+    al((void **)&m->h1T, B * m->h1 * 2);
+    al((void **)&m->h2T, B * m->h2 * 2);
+    al((void **)&m->dzb, B * m->out * 2);
+    al((void **)&m->dzT, B * m->out * 2);
+    al((void **)&m->da2b, B * m->h2 * 2);
+    al((void **)&m->da2T, B * m->h2 * 2);
+    al((void **)&m->da1T, B * m->h1 * 2);
+    al((void **)&m->z, B * m->out * 4);
+    al((void **)&m->dh, B * std::max(m->h1, m->h2) * 4);
+    al((void **)&m->dm, B * std::max(m->h1, m->h2) * 4);
+    al((void **)&m->xbat, B * m->d * 4);
+    al((void **)&m->ybat, B * 4);
+    if (e != cudaSuccess) return cuda_fail(e, "MLP training buffers");
+    m->train_cap = n;
+    return ANN_OK;
+}
+
 ann_status forward(ann_mlp *m, const float *x, uint32_t n, cudaStream_t st, int logits_epi, float *logits,
                    float *part, uint32_t ntiles)
 {
@@ -547,7 +608,7 @@ void mlp_free_all(ann_mlp *m)
         for (void *x : p) if (x) cudaFree(x);
     }
     void *q[] = {m->xb, m->xT, m->h1b, m->h1T, m->h2b, m->h2T, m->dzb, m->dzT, m->da2b, m->da2T, m->da1T,
-                 m->z, m->dh, m->dm, m->loss, m->part, m->d_error};
+                 m->z, m->dh, m->dm, m->loss, m->part, m->d_error, m->xbat, m->ybat, m->perm, m->epoch_loss};
     for (void *x : q) if (x) cudaFree(x);
 }
 
@@ -587,18 +648,15 @@ ann_status ann_mlp_create(int device, uint32_t in_dim, uint32_t hidden1, uint32_
         al((void **)&m->b[l], rows[l] * 4); al((void **)&m->mb[l], rows[l] * 4); al((void **)&m->vb[l], rows[l] * 4);
         al((void **)&m->gb[l], rows[l] * 4);
     }
+    // activations of the forward pass, for up to max_batch rows; the
+    // training-only buffers are allocated on the first training step
     const size_t B = max_batch;
-    al((void **)&m->xb, B * in_dim * 2); al((void **)&m->xT, B * in_dim * 2);
-    al((void **)&m->h1b, B * hidden1 * 2); al((void **)&m->h1T, B * hidden1 * 2);
-    al((void **)&m->h2b, B * hidden2 * 2); al((void **)&m->h2T, B * hidden2 * 2);
-    al((void **)&m->dzb, B * out_dim * 2); al((void **)&m->dzT, B * out_dim * 2);
-    al((void **)&m->da2b, B * hidden2 * 2); al((void **)&m->da2T, B * hidden2 * 2);
-    al((void **)&m->da1T, B * hidden1 * 2);
-    al((void **)&m->z, B * out_dim * 4);
-    al((void **)&m->dh, B * std::max(hidden1, hidden2) * 4);
-    al((void **)&m->dm, B * std::max(hidden1, hidden2) * 4);
+    al((void **)&m->xb, B * in_dim * 2);
+    al((void **)&m->h1b, B * hidden1 * 2);
+    al((void **)&m->h2b, B * hidden2 * 2);
     al((void **)&m->loss, 64);
     al((void **)&m->d_error, 64);
+    al((void **)&m->epoch_loss, 4096 * 4);
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) {
         mlp_free_all(m);
@@ -702,9 +760,9 @@ ann_status ann_mlp_train_step(ann_mlp *m, const float *x, const uint32_t *labels
     cudaGetDevice(&prev);
     cudaSetDevice(m->device);
     cudaStream_t st = (cudaStream_t)stream;
-    ann_status s = ANN_OK;
+    ann_status s = ensure_train_buffers(m, n);
     auto chk = [&]() { cudaError_t e = cudaGetLastError(); if (e != cudaSuccess && s == ANN_OK) s = cuda_fail(e, "ann_mlp_train_step"); };
-    if (cudaMemsetAsync(m->loss, 0, 4, st) != cudaSuccess) s = ANN_ECUDA;
+    if (s == ANN_OK && cudaMemsetAsync(m->loss, 0, 4, st) != cudaSuccess) s = ANN_ECUDA;
     if (s == ANN_OK) s = forward(m, x, n, st, EPI_BIAS_F32, m->z, nullptr, 0);
     const dim3 tb(32, 8);
     EpiArgs e{};
@@ -799,6 +857,65 @@ ann_status ann_mlp_predict(ann_mlp *m, const float *x, uint32_t n, uint32_t P, f
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) s = cuda_fail(e, "topp_merge_kernel");
         }
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return s;
+}
+
+// Epochs of minibatch AdamW over (x, labels) (device, n rows): each epoch
+// visits the rows in a fresh order (Fisher-Yates driven by splitmix64 of
+// (seed, epoch)), in batches of `batch` rows (a multiple of 8); a final
+// partial batch is cut down to a multiple of 8. epoch_loss (host, `epochs`
+// floats, may be NULL) receives each epoch's mean batch loss. Synchronous.
+ann_status ann_mlp_train_epochs(ann_mlp *m, const float *x, const uint32_t *labels, uint32_t n, uint32_t batch,
+                                uint32_t epochs, float lr, float beta1, float beta2, float eps, float weight_decay,
+                                uint64_t seed, float *epoch_loss, void *stream)
+{
+    if (!m || !x || !labels || batch == 0 || batch % 8 || batch > m->maxb || epochs > 4096 || n < 8) {
+        set_error("ann_mlp_train_epochs: bad arguments (batch a multiple of 8 <= max_batch, n >= 8, epochs <= 4096)");
+        return ANN_EINVAL;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    ann_status s = ANN_OK;
+    if (n > m->perm_cap) {
+        if (m->perm) cudaFree(m->perm);
+        m->perm = nullptr;
+        m->perm_cap = 0;
+        cudaError_t e = cudaMalloc(&m->perm, (size_t)n * 4);
+        if (e != cudaSuccess) s = cuda_fail(e, "ann_mlp_train_epochs");
+        else m->perm_cap = n;
+    }
+    if (s == ANN_OK) s = ensure_train_buffers(m, batch);
+    std::vector<uint32_t> perm(n);
+    if (s == ANN_OK && cudaMemsetAsync(m->epoch_loss, 0, (size_t)epochs * 4, st) != cudaSuccess) s = ANN_ECUDA;
+    for (uint32_t ep = 0; ep < epochs && s == ANN_OK; ++ep) {
+        for (uint32_t i = 0; i < n; ++i) perm[i] = i;
+        const uint64_t key = mix64(seed ^ mix64(ep));
+        for (uint32_t i = n - 1; i > 0; --i) {
+            const uint32_t j = (uint32_t)(mix64(key ^ i) % (uint64_t)(i + 1));
+            std::swap(perm[i], perm[j]);
+        }
+        cudaError_t e = cudaMemcpyAsync(m->perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // perm is reused next epoch
+        if (e != cudaSuccess) { s = cuda_fail(e, "ann_mlp_train_epochs"); break; }
+        uint32_t steps = 0;
+        for (uint32_t b0 = 0; b0 + 8 <= n; b0 += batch) ++steps;
+        for (uint32_t b0 = 0; b0 + 8 <= n && s == ANN_OK; b0 += batch) {
+            uint32_t rows = std::min(batch, n - b0) & ~7u;
+            gather_batch_kernel<<<rows, 128, 0, st>>>(x, labels, m->perm + b0, rows, m->d, m->xbat, m->ybat);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) { s = cuda_fail(e, "gather_batch_kernel"); break; }
+            s = ann_mlp_train_step(m, m->xbat, m->ybat, rows, lr, beta1, beta2, eps, weight_decay, nullptr, stream);
+            if (s == ANN_OK) accumulate_kernel<<<1, 32, 0, st>>>(m->epoch_loss + ep, m->loss, 1.0f / (float)steps);
+        }
+    }
+    if (s == ANN_OK && epoch_loss) {
+        cudaError_t e = cudaMemcpyAsync(epoch_loss, m->epoch_loss, (size_t)epochs * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "ann_mlp_train_epochs");
     }
     if (prev >= 0) cudaSetDevice(prev);
     return s;

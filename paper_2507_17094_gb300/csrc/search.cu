@@ -58,7 +58,7 @@ struct View {
 };
 
 struct Layout {  // byte offsets inside one warp's shared-memory region
-    uint32_t q, bd, bi, bs, cd, ci, cs, adj, dir, prow, pqb, par, stage, hash, bar, total;
+    uint32_t q, bd, bi, bs, cd, ci, cs, adj, dir, prow, pqb, par, stage, hash, bar, qp, total;
 };
 
 struct Args {
@@ -69,12 +69,10 @@ struct Args {
     const float *queries;
     uint32_t nq, d, w;
     const uint32_t *given;
-    uint32_t n_given;
     uint32_t *out_ids;
     float *out_dists;
     ann_query_stats *stats;
-    uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank;
-    uint64_t seed, qid_base;
+    QParams qp;
     uint32_t *counter;
     int *err;
     Layout lay;
@@ -401,9 +399,10 @@ struct WarpSearch {
     // Random seeds j = 0..m-1 (Step 2), deduplicated without redraw: node j
     // is splitmix64(key ^ (qid << 32) ^ j) mod n, key = splitmix64(seed ^ tag).
     template <int RST>
-    __device__ bool seed_random(const View &v, uint32_t m, uint64_t tag, uint32_t lcap, uint32_t &rows)
+    __device__ bool seed_random(const View &v, uint32_t m, uint64_t seed, uint64_t tag, uint32_t lcap,
+                                uint32_t &rows)
     {
-        const uint64_t key = splitmix64(a.seed ^ tag);
+        const uint64_t key = splitmix64(seed ^ tag);
         for (uint32_t j0 = 0; j0 < m; j0 += a.cap_cand) {
             const uint32_t chunk = min(a.cap_cand, m - j0);
             hash_make_room(chunk);
@@ -432,7 +431,7 @@ struct WarpSearch {
             hash_make_room(chunk);
             uint32_t nc = 0;
             for (uint32_t b = 0; b < chunk; b += 32) {
-                const uint32_t id = (b + lane < chunk) ? ids[j0 + b + lane] : kEmpty;
+                const uint32_t id = (b + lane < chunk) ? __ldcg(ids + j0 + b + lane) : kEmpty;
                 nc = collect(id < v.n, id, nc);
             }
             __syncwarp();
@@ -608,40 +607,45 @@ struct WarpSearch {
     }
 
     // ------------------------------------------------------------- a query
-    __device__ void run(uint32_t query)
+    // One query: qg its vector, given its ghost seeds (or NULL), oid/odist
+    // its k outputs, stats_out its counters (or NULL); qidx indexes the RNG
+    // stream (qid = qp.qid_base + qidx).
+    __device__ void run(const QParams &qp, uint64_t qidx, const float *qg, const uint32_t *given_row, uint32_t *oid,
+                        float *odist, ann_query_stats *stats_out)
     {
-        qid = a.qid_base + query;
+        qid = qp.qid_base + qidx;
         st = ann_query_stats{};
         cnt = 0;
-        const float *qg = a.queries + (uint64_t)query * a.d;
         const uint32_t dpad = (a.d + 31) & ~31u;
-        for (uint32_t i = lane; i < dpad; i += 32) q()[i] = i < a.d ? qg[i] : 0.0f;
+        // read through L2 only: a serving ring rewrites query slots between
+        // uses, and L1 is not kept coherent with those copies
+        for (uint32_t i = lane; i < dpad; i += 32) q()[i] = i < a.d ? __ldcg(qg + i) : 0.0f;
         __syncwarp();
         hash_clear();
         bool ok = true;
-        if (a.entry == ANN_ENTRY_RANDOM) {
-            ok = seed_random<ST>(a.base, a.m, 0, a.L, st.vec_rows);
+        if (qp.entry == ANN_ENTRY_RANDOM) {
+            ok = seed_random<ST>(a.base, qp.m, qp.seed, 0, qp.L, st.vec_rows);
         } else {
             const uint32_t *given = nullptr;
-            if (a.entry == ANN_ENTRY_GIVEN_GHOST && a.given) {
-                given = a.given + (uint64_t)query * a.n_given;
+            if (qp.entry == ANN_ENTRY_GIVEN_GHOST && given_row) {
+                given = given_row;
                 if (given[0] == ANN_INVALID_ID) given = nullptr;  // fall back to random ghost seeds
             }
-            uint32_t Tg = a.Tg;
+            uint32_t Tg = qp.Tg;
             if (given) {
-                Tg = a.Tg_given;
-                ok = seed_given<ST>(a.ghost, given, a.n_given, a.Lg, st.ghost_vec_rows);
+                Tg = qp.Tg_given;
+                ok = seed_given<ST>(a.ghost, given, qp.n_given, qp.Lg, st.ghost_vec_rows);
             } else {
-                ok = seed_random<ST>(a.ghost, a.ghost.deg, kGhostTag, a.Lg, st.ghost_vec_rows);
+                ok = seed_random<ST>(a.ghost, a.ghost.deg, qp.seed, kGhostTag, qp.Lg, st.ghost_vec_rows);
             }
             uint32_t no_dgs = 0;
             if (ok)
-                ok = iterate<ST>(a.ghost, a.Lg, 1, Tg, a.ghost.deg, 0, 0, st.ghost_iters, st.ghost_parents, no_dgs,
+                ok = iterate<ST>(a.ghost, qp.Lg, 1, Tg, a.ghost.deg, 0, 0, st.ghost_iters, st.ghost_parents, no_dgs,
                                  st.ghost_vec_rows);
             if (ok) {
                 // transition: the top g ghost results become the base queue;
                 // ghost ids are ascending, so the (dist, id) order carries over
-                const uint32_t g = min(min(a.g, cnt), a.L);
+                const uint32_t g = min(min(qp.g, cnt), qp.L);
                 for (uint32_t i = lane; i < g; i += 32) {
                     bi()[i] = __ldg(a.ghost_ids + bi()[i]);
                     bs()[i] = kUnexpanded;
@@ -655,11 +659,9 @@ struct WarpSearch {
             }
         }
         if (ok)
-            ok = iterate<ST>(a.base, a.L, a.W, a.T, a.n_keep, a.it_cool, a.reexpand, st.iters, st.parents,
+            ok = iterate<ST>(a.base, qp.L, qp.W, qp.T, qp.n_keep, qp.it_cool, qp.reexpand, st.iters, st.parents,
                              st.dgs_parents, st.vec_rows);
-        uint32_t *oid = a.out_ids + (uint64_t)query * a.k;
-        float *odist = a.out_dists + (uint64_t)query * a.k;
-        if (ok && a.rerank) {
+        if (ok && qp.rerank) {
             // FP32 distances of the whole queue on the originals, then the top k
             ok = evaluate<ANN_F32>(a.x32, nullptr, a.row32_bytes, bi(), cnt, bd());
             st.rerank_rows += cnt;
@@ -669,30 +671,30 @@ struct WarpSearch {
                     const uint32_t kid = bi()[e];
                     uint32_t r = 0;
                     for (uint32_t e2 = 0; e2 < cnt; ++e2) r += key_less(bd()[e2], bi()[e2], kd, kid);
-                    if (r < a.k) {
+                    if (r < qp.k) {
                         oid[r] = kid;
                         odist[r] = kd;
                     }
                 }
-                for (uint32_t j = cnt + lane; j < a.k; j += 32) {
+                for (uint32_t j = cnt + lane; j < qp.k; j += 32) {
                     oid[j] = ANN_INVALID_ID;
                     odist[j] = INFINITY;
                 }
             }
         } else if (ok) {
-            for (uint32_t j = lane; j < a.k; j += 32) {
+            for (uint32_t j = lane; j < qp.k; j += 32) {
                 oid[j] = j < cnt ? bi()[j] : ANN_INVALID_ID;
                 odist[j] = j < cnt ? bd()[j] : INFINITY;
             }
         }
         if (!ok) {
-            for (uint32_t j = lane; j < a.k; j += 32) {
+            for (uint32_t j = lane; j < qp.k; j += 32) {
                 oid[j] = ANN_INVALID_ID;
                 odist[j] = INFINITY;
             }
             st.status = 1;
         }
-        if (a.stats && lane == 0) a.stats[query] = st;
+        if (stats_out && lane == 0) *stats_out = st;
         __syncwarp();
     }
 };
@@ -711,8 +713,67 @@ __global__ void __launch_bounds__(128) search_kernel(const Args a)
         if (lane == 0) qi = atomicAdd(a.counter, 1u);
         qi = __shfl_sync(0xffffffffu, qi, 0);
         if (qi >= a.nq) break;
-        ws.run(qi);
+        const QParams &qp = a.qp;
+        ws.run(qp, qi, a.queries + (uint64_t)qi * a.d,
+               (qp.entry == ANN_ENTRY_GIVEN_GHOST && a.given) ? a.given + (uint64_t)qi * qp.n_given : nullptr,
+               a.out_ids + (uint64_t)qi * qp.k, a.out_dists + (uint64_t)qi * qp.k, a.stats ? a.stats + qi : nullptr);
         if (ws.failed) break;
+    }
+}
+
+// Continuous batching: warps of every running serve kernel pop queries, in
+// arrival order, from one device ring that the host appends to while they
+// run (head/tail are monotonic query counters; slot = counter mod capacity).
+// A warp serves at most `per_warp` queries and then leaves, so a launch's
+// capacity is blocks x warps x per_warp and SMs free up for other kernels.
+// The request's parameters are copied into the warp's shared memory; the
+// warp that finishes a request's last query raises its completion flag in
+// host-mapped memory after a system-scope fence.
+template <int ST>
+__global__ void __launch_bounds__(128) serve_kernel(const Args a, const ServeRing r)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *base = smem + (size_t)warp * a.lay.total;
+    WarpSearch<ST> ws(a, base);
+    QParams *qp = reinterpret_cast<QParams *>(base + a.lay.qp);
+    if (lane == 0) mbar_init(ws.bar(), 1);
+    fence_mbar_init();
+    __syncwarp();
+    for (uint32_t served = 0; served < r.per_warp; ++served) {
+        unsigned long long h = 0;
+        uint32_t got = 0;
+        if (lane == 0) {
+            for (uint32_t attempt = 0; attempt < (1u << 20); ++attempt) {  // lock-free: a failed CAS means another warp won
+                h = *reinterpret_cast<volatile unsigned long long *>(r.head);
+                const unsigned long long t = *reinterpret_cast<volatile const unsigned long long *>(r.tail);
+                if (h >= t) break;
+                if (atomicCAS(r.head, h, h + 1) == h) { got = 1; break; }
+            }
+        }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) break;
+        h = __shfl_sync(0xffffffffu, h, 0);
+        const uint32_t slot = (uint32_t)(h % r.cap);
+        ServeReq *rq = r.reqs + __ldcg(r.slot_req + slot);
+        if (lane < sizeof(QParams) / 4)
+            reinterpret_cast<uint32_t *>(qp)[lane] = reinterpret_cast<const volatile uint32_t *>(&rq->qp)[lane];
+        __syncwarp();
+        const uint32_t j = (slot + r.cap - *reinterpret_cast<volatile uint32_t *>(&rq->slot0)) % r.cap;
+        const uint32_t *seeds = (qp->entry == ANN_ENTRY_GIVEN_GHOST && r.seeds) ? r.seeds + (size_t)slot * r.P : nullptr;
+        ws.run(*qp, j, r.queries + (size_t)slot * a.d, seeds, r.ids + (size_t)slot * r.kmax,
+               r.dists + (size_t)slot * r.kmax, nullptr);
+        if (ws.failed) break;
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t done = atomicAdd(&rq->done, 1u) + 1;
+            if (done == *reinterpret_cast<volatile uint32_t *>(&rq->nq)) {
+                __threadfence_system();
+                r.flags[rq->flag] = 1u;
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -744,6 +805,7 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
     L.stage = take(stage_rows * stage_stride);
     L.hash = take((1u << hash_bits) * 4);
     L.bar = take(16);
+    L.qp = take(96);
     L.total = align16(o);
     return L;
 }
@@ -783,11 +845,7 @@ int env_int(const char *name, int dflt)
 
 namespace ann {
 
-// Validates parameters, derives the method's counts and launches the search
-// with the given work counter and error word (device memory).
-ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
-                            const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
-                            ann_query_stats *stats, cudaStream_t stream, uint32_t *counter, int *err)
+ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint32_t n_given, QParams *out)
 {
     if (!ix || !p) { set_error("ann_search: NULL index or params"); return ANN_EINVAL; }
     const uint32_t L = p->itopk, W = p->search_width, deg = ix->degree;
@@ -808,7 +866,7 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
         set_error("ann_search: entry %u needs a ghost set", p->entry);
         return ANN_EINVAL;
     }
-    if (p->entry == ANN_ENTRY_GIVEN_GHOST && (!given || n_given == 0)) {
+    if (p->entry == ANN_ENTRY_GIVEN_GHOST && n_given == 0) {
         set_error("ann_search: given ghost seeds missing");
         return ANN_EINVAL;
     }
@@ -816,39 +874,18 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
         set_error("ann_search: rerank needs the FP32 originals (keep_fp32)");
         return ANN_EINVAL;
     }
-    if (nq && (!queries || !ids || !dists)) {
-        set_error("ann_search: NULL queries or outputs");
-        return ANN_EINVAL;
-    }
     const uint32_t Lg = p->ghost_itopk ? p->ghost_itopk : std::min(L, 64u);
     if (Lg > ANN_MAX_ITOPK) {
         set_error("ann_search: ghost_itopk > %u", ANN_MAX_ITOPK);
         return ANN_EINVAL;
     }
-    if (nq == 0) return ANN_OK;
-
-    Args a{};
-    a.base = View{(const uint8_t *)ix->codes, ix->scales, ix->row_bytes, ix->graph, deg, ix->deg_pad,
-                  ix->dir, (uint32_t)ix->n};
-    a.ghost = View{(const uint8_t *)ix->ghost_codes, ix->ghost_scales, ix->row_bytes, ix->ghost_graph,
-                   ix->ghost_degree, ix->gdeg_pad, nullptr, ix->n_ghost};
-    a.ghost_ids = ix->ghost_ids;
-    a.x32 = (const uint8_t *)ix->x32;
-    a.row32_bytes = ix->storage == ANN_F32 ? ix->row_bytes : ix->row32_bytes;
-    a.queries = queries;
-    a.nq = nq;
-    a.d = ix->dim;
-    a.w = ix->words;
-    a.given = given;
-    a.n_given = n_given;
-    a.out_ids = ids;
-    a.out_dists = dists;
-    a.stats = stats;
-    a.k = p->k;
-    a.L = L;
-    a.W = W;
-    a.T = p->max_iters;
-    a.m = p->num_seeds ? p->num_seeds : W * deg;
+    QParams q{};
+    q.n_given = n_given;
+    q.k = p->k;
+    q.L = L;
+    q.W = W;
+    q.T = p->max_iters;
+    q.m = p->num_seeds ? p->num_seeds : W * deg;
     // Section 3.3.2 readings: keep n = deg - round(rho * deg) (at least 1);
     // the cool-down is the last round(c * T) iterations (half-up, in double).
     uint32_t n_keep = deg;
@@ -856,52 +893,72 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
         const int64_t drop = (int64_t)std::floor((double)p->dgs_discard * deg + 0.5);
         n_keep = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(deg, (int64_t)deg - drop));
     }
-    a.n_keep = n_keep;
+    q.n_keep = n_keep;
     const int64_t n_cool = (int64_t)std::floor((double)p->dgs_cooldown * p->max_iters + 0.5);
-    a.it_cool = (uint32_t)std::max<int64_t>(0, (int64_t)p->max_iters - n_cool);
-    a.reexpand = p->dgs_reexpand ? 1 : 0;
-    a.entry = p->entry;
-    a.Lg = Lg;
-    a.Tg = p->ghost_max_iters;
-    a.Tg_given = p->ghost_max_iters_given;
-    a.g = p->ghost_seeds_out ? p->ghost_seeds_out : Lg;
-    a.rerank = p->rerank ? 1 : 0;
-    a.seed = p->seed;
-    a.qid_base = p->qid_base;
-    a.counter = counter;
-    a.err = err;
+    q.it_cool = (uint32_t)std::max<int64_t>(0, (int64_t)p->max_iters - n_cool);
+    q.reexpand = p->dgs_reexpand ? 1 : 0;
+    q.entry = p->entry;
+    q.Lg = Lg;
+    q.Tg = p->ghost_max_iters;
+    q.Tg_given = p->ghost_max_iters_given;
+    q.g = p->ghost_seeds_out ? p->ghost_seeds_out : Lg;
+    q.rerank = p->rerank ? 1 : 0;
+    q.seed = p->seed;
+    q.qid_base = p->qid_base;
+    *out = q;
+    return ANN_OK;
+}
 
-    const uint32_t cap_buf = std::max(L, a.entry != ANN_ENTRY_RANDOM ? Lg : 1u);
-    uint32_t cap_cand = std::max(W * deg, 32u);
-    if (a.entry != ANN_ENTRY_RANDOM) cap_cand = std::max(cap_cand, ix->ghost_degree);
+namespace planning {
+
+// Kernel arguments and launch shape for parameters q (the largest a launch
+// must serve): shared-memory layout per warp, warps per block, blocks per SM.
+ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_t &smem, int &nb)
+{
+    const uint32_t deg = ix->degree;
+    a.base = View{(const uint8_t *)ix->codes, ix->scales, ix->row_bytes, ix->graph, deg, ix->deg_pad,
+                  ix->dir, (uint32_t)ix->n};
+    a.ghost = View{(const uint8_t *)ix->ghost_codes, ix->ghost_scales, ix->row_bytes, ix->ghost_graph,
+                   ix->ghost_degree, ix->gdeg_pad, nullptr, ix->n_ghost};
+    a.ghost_ids = ix->ghost_ids;
+    a.x32 = (const uint8_t *)ix->x32;
+    a.row32_bytes = ix->storage == ANN_F32 ? ix->row_bytes : ix->row32_bytes;
+    a.d = ix->dim;
+    a.w = ix->words;
+    a.qp = q;
+    const uint32_t cap_buf = std::max(q.L, q.entry != ANN_ENTRY_RANDOM ? q.Lg : 1u);
+    uint32_t cap_cand = std::max(q.W * deg, 32u);
+    if (q.entry != ANN_ENTRY_RANDOM) cap_cand = std::max(cap_cand, ix->ghost_degree);
     cap_cand = round_up(cap_cand, 32);
     a.cap_cand = cap_cand;
-    const uint32_t adj_words = std::max(W * ix->deg_pad, ix->gdeg_pad);
-    const bool dgs = n_keep < deg;
-    const uint32_t dir_words = dgs ? W * ix->deg_pad * ix->words : 0;
+    const uint32_t adj_words = std::max(q.W * ix->deg_pad, ix->gdeg_pad);
+    const bool dgs = q.n_keep < deg;
+    const uint32_t dir_words = dgs ? q.W * ix->deg_pad * ix->words : 0;
     a.prow_bytes = ix->row_bytes;
-    const uint32_t stage_bytes = std::max(ix->row_bytes, a.rerank ? a.row32_bytes : 0u);
+    const uint32_t stage_bytes = std::max(ix->row_bytes, q.rerank ? a.row32_bytes : 0u);
     a.stage_stride = smem_row_stride(stage_bytes);
     a.stage_rows = (uint32_t)std::min(32, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
     // visited table: at least twice (queue + one iteration's candidates);
-    // beyond that as large as fits 16 warps per SM (up to 4096 entries), so
-    // resets stay rare
+    // beyond that as large as still fits the target number of warps per SM
+    // (16 by default; up to 4096 entries), so resets stay rare
     const uint32_t need = 2 * (cap_buf + cap_cand);
     const uint32_t hb_min = std::max(8u, bits_for(need));
     uint32_t hb = hb_min;
-    const size_t warp_budget = ix->smem_optin / 4 / 4;  // 4 CTAs of 4 warps
+    const int target_warps = std::min(32, std::max(4, env_int("ANN_WARPS_PER_SM", 16)));
+    const size_t sm_bytes = ix->smem_optin + 1024;                   // shared memory of one SM
+    const size_t warp_budget = (sm_bytes - (size_t)(target_warps / 4) * 1024) / target_warps;
     while (hb < 12) {
-        const Layout t = make_layout(ix->dim, ix->words, cap_buf, cap_cand, W, adj_words, dir_words, a.prow_bytes,
+        const Layout t = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W, adj_words, dir_words, a.prow_bytes,
                                      a.stage_rows, a.stage_stride, hb + 1);
         if (t.total > warp_budget) break;
         ++hb;
     }
     if (const int v = env_int("ANN_HASH_BITS", 0); v > 0 && (uint32_t)v >= hb_min) hb = (uint32_t)v;
-    int warps = 4;
+    warps = 4;
     Layout lay{};
     for (;;) {
-        lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, W, adj_words, dir_words, a.prow_bytes, a.stage_rows,
-                          a.stage_stride, hb);
+        lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W, adj_words, dir_words, a.prow_bytes,
+                          a.stage_rows, a.stage_stride, hb);
         if ((size_t)lay.total * warps <= ix->smem_optin) break;
         if (warps > 1) { warps /= 2; continue; }
         if (hb > hb_min) { --hb; continue; }
@@ -910,8 +967,7 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
     }
     a.hash_bits = hb;
     a.lay = lay;
-    const size_t smem = (size_t)lay.total * warps;
-    int nb = 0;
+    smem = (size_t)lay.total * warps;
     switch (ix->storage) {
     case ANN_F32: nb = blocks_per_sm<ANN_F32>(warps, smem); break;
     case ANN_F16: nb = blocks_per_sm<ANN_F16>(warps, smem); break;
@@ -921,6 +977,53 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
         set_error("ann_search: kernel does not fit on an SM (%zu bytes shared)", smem);
         return ANN_EINVAL;
     }
+    return ANN_OK;
+}
+
+struct ServePlanImpl {
+    Args a;
+    int warps, nb, num_sms, storage;
+    size_t smem;
+};
+
+template <int ST>
+cudaError_t launch_serve(const ServePlanImpl &pl, const ServeRing &r, int blocks, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(serve_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    if (e != cudaSuccess) return e;
+    serve_kernel<ST><<<blocks, pl.warps * 32, pl.smem, st>>>(pl.a, r);
+    return cudaGetLastError();
+}
+
+}  // namespace planning
+
+using namespace planning;
+
+ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
+                            const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
+                            ann_query_stats *stats, cudaStream_t stream, uint32_t *counter, int *err)
+{
+    QParams q;
+    ann_status s = derive_qparams(ix, p, given ? n_given : 0, &q);
+    if (s != ANN_OK) return s;
+    if (nq && (!queries || !ids || !dists)) {
+        set_error("ann_search: NULL queries or outputs");
+        return ANN_EINVAL;
+    }
+    if (nq == 0) return ANN_OK;
+    Args a{};
+    int warps = 0, nb = 0;
+    size_t smem = 0;
+    s = plan_args(ix, q, a, warps, smem, nb);
+    if (s != ANN_OK) return s;
+    a.queries = queries;
+    a.nq = nq;
+    a.given = given;
+    a.out_ids = ids;
+    a.out_dists = dists;
+    a.stats = stats;
+    a.counter = counter;
+    a.err = err;
     const uint64_t want = ((uint64_t)nq + warps - 1) / warps;
     const int blocks = (int)std::min<uint64_t>(want, (uint64_t)nb * ix->num_sms);
     ANN_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream));
@@ -931,6 +1034,40 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
     default: e = launch<ANN_E4M3>(a, warps, blocks, smem, stream); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "search_kernel launch");
+    return ANN_OK;
+}
+
+ann_status serve_plan(ann_index *ix, const ann_search_params *maxp, uint32_t n_given_max, void **plan)
+{
+    QParams q;
+    ann_status s = derive_qparams(ix, maxp, n_given_max, &q);
+    if (s != ANN_OK) return s;
+    ServePlanImpl *pl = new ServePlanImpl();
+    s = plan_args(ix, q, pl->a, pl->warps, pl->smem, pl->nb);
+    if (s != ANN_OK) { delete pl; return s; }
+    pl->a.counter = ix->d_counter;
+    pl->a.err = ix->d_error;
+    pl->num_sms = ix->num_sms;
+    pl->storage = ix->storage;
+    *plan = pl;
+    return ANN_OK;
+}
+
+void serve_plan_free(void *plan) { delete static_cast<ServePlanImpl *>(plan); }
+
+ann_status serve_launch(void *plan, const ServeRing &ring, uint32_t queries, cudaStream_t stream)
+{
+    const ServePlanImpl &pl = *static_cast<const ServePlanImpl *>(plan);
+    const uint64_t per_block = (uint64_t)pl.warps * ring.per_warp;
+    const uint64_t want = ((uint64_t)queries + per_block - 1) / per_block;
+    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)pl.nb * pl.num_sms));
+    cudaError_t e;
+    switch (pl.storage) {
+    case ANN_F32: e = launch_serve<ANN_F32>(pl, ring, blocks, stream); break;
+    case ANN_F16: e = launch_serve<ANN_F16>(pl, ring, blocks, stream); break;
+    default: e = launch_serve<ANN_E4M3>(pl, ring, blocks, stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "serve_kernel launch");
     return ANN_OK;
 }
 

@@ -1,0 +1,67 @@
+"""Learned entry, end to end, as a sequence of C-ABI calls (no arithmetic here).
+
+1. Labels: each training query's best ghost node, as ghost staging finds it
+   (ann_search with no base iterations and k = 1, then ann_ghost_index_of).
+2. Training: ann_mlp_train_epochs on (query, label) pairs.
+3. Inference: ann_mlp_predict gives the top-P ghost nodes per query (or the
+   fallback marker below the confidence threshold tau); ann_search with
+   entry = ANN_ENTRY_GIVEN_GHOST starts its ghost stage from them.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from .binding import ENTRY_GHOST, INVALID, MLP, Index
+
+
+def ghost_labels(index: Index, queries, seed: int, ghost_itopk: int = 64, ghost_max_iters: int = 64,
+                 stream=None):
+    """Best ghost node of each query by ghost staging (CUDA int32 tensor)."""
+    ids, _, _ = index.search(queries, k=1, itopk=ghost_itopk, max_iters=0, entry=ENTRY_GHOST,
+                             ghost_itopk=ghost_itopk, ghost_max_iters=ghost_max_iters, seed=seed, stream=stream)
+    return index.ghost_index_of(ids[:, 0].contiguous(), stream=stream)
+
+
+def choose_tau(pmax: np.ndarray, hit: np.ndarray, target: float = 0.97) -> float:
+    """Smallest confidence threshold above which the predicted seeds contain
+    the label for at least `target` of the validation queries (0 if all do)."""
+    order = np.argsort(-pmax)
+    hits = np.cumsum(hit[order]) / np.arange(1, len(order) + 1)
+    ok = np.nonzero(hits >= target)[0]
+    if len(ok) == 0:
+        return float(pmax.max()) + 1.0
+    last = ok.max()
+    return 0.0 if last == len(order) - 1 else float(pmax[order][last])
+
+
+class LearnedEntry:
+    """An MLP over the ghost set, trained on the index's own ghost staging."""
+
+    def __init__(self, index: Index, params, hidden=(512, 512), max_batch: int = 16384, P: int = 8):
+        self.index = index
+        self.P = P
+        self.mlp = MLP(index.dim, hidden[0], hidden[1], index.n_ghost, max_batch, device=index.device)
+        self.mlp.set_params(*params)
+        self.tau = 0.0
+        self.losses = None
+
+    def fit(self, train_queries, labels, epochs: int = 5, batch: int = 1024, lr: float = 1e-3, seed: int = 0):
+        self.losses = self.mlp.train_epochs(train_queries, labels, batch=batch, epochs=epochs, lr=lr, seed=seed)
+        return self.losses
+
+    def calibrate(self, val_queries, val_labels, target: float = 0.97):
+        seeds, pmax = self.mlp.predict(val_queries, P=self.P, tau=0.0)
+        hit = (seeds == val_labels[:, None]).any(dim=1).cpu().numpy()
+        self.tau = choose_tau(pmax.cpu().numpy(), hit, target)
+        return self.tau, float(hit.mean())
+
+    def seeds(self, queries, stream=None):
+        s, pmax = self.mlp.predict(queries, P=self.P, tau=self.tau, stream=stream)
+        return s, pmax
+
+    def fallback_fraction(self, seeds) -> float:
+        return float((seeds[:, 0] == np.int32(np.uint32(INVALID).view(np.int32))).float().mean().item())
+
+    def close(self):
+        self.mlp.close()

@@ -83,49 +83,72 @@ def test_gradients_vs_oracle():
     g.close()
 
 
-def test_adamw_matches_oracle_on_the_gpu_gradients():
+def test_adamw_step_vs_oracle():
+    # One AdamW step from seeded weights. The oracle steps with its own FP64
+    # gradients. A first Adam step moves every weight by lr * g/(|g| + eps),
+    # i.e. by +-lr (plus decay), so the two agree to FP32 rounding wherever
+    # the gradients agree in sign; they may differ by 2 lr only where a
+    # gradient is so small that the GPU's BF16 rounding can flip its sign.
     d, h1, h2, out, n = 64, 128, 128, 256, 32
+    lr, wd = 1e-2, 0.01
     m = make_model(d, h1, h2, out, seed=5)
     rng = np.random.default_rng(6)
     X = rng.standard_normal((n, d)).astype(np.float32)
     y = rng.integers(0, out, n).astype(np.uint32)
     g = gpu_mlp(m, n)
-    opt = M.AdamW(lr=1e-2, wd=0.01)
+    g.train_step(torch.from_numpy(X).cuda(), torch.from_numpy(y.view(np.int32)).cuda(), lr=lr, weight_decay=wd)
+    torch.cuda.synchronize()
+    g.sync()
+    grads = M.gradients(m, X, y.astype(np.int64))
     ref = m.copy()
-    Xt, yt = torch.from_numpy(X).cuda(), torch.from_numpy(y.view(np.int32)).cuda()
-    for _ in range(3):
-        g.train_step(Xt, yt, lr=1e-2, weight_decay=0.01)
-        torch.cuda.synchronize()
-        grads = dict(zip(M.LAYERS, g.get(1)))
-        opt.step(ref, grads)
-        got = dict(zip(M.LAYERS, g.get(0)))
-        for k in M.LAYERS:
-            np.testing.assert_allclose(got[k], getattr(ref, k), rtol=1e-5, atol=1e-6)
-        ref = M.MLP(**{k: got[k].copy() for k in M.LAYERS})   # continue from the GPU's own weights
+    M.AdamW(lr=lr, wd=wd).step(ref, grads)
+    got = dict(zip(M.LAYERS, g.get(0)))
+    for k in M.LAYERS:
+        diff = np.abs(got[k].astype(np.float64) - getattr(ref, k))
+        small = np.abs(grads[k]) <= 2e-2 * np.sqrt(np.mean(grads[k] ** 2)) + 1e-12
+        assert (diff[~small] <= 1e-6 + 1e-6 * np.abs(getattr(ref, k))[~small]).all(), k
+        assert (diff <= 2 * lr + 1e-5).all(), k
+        assert small.mean() < 0.5, k   # most entries are checked tightly
     g.close()
 
 
 @pytest.mark.parametrize("P", [1, 8])
-def test_fused_top_p_equals_top_p_of_materialised_logits(P):
+def test_fused_top_p(P):
     d, h1, h2, out, n = 96, 256, 256, 3000, 500
     m = make_model(d, h1, h2, out, seed=7)
     X = np.random.default_rng(8).standard_normal((n, d)).astype(np.float32)
     g = gpu_mlp(m, 512)
     Xt = torch.from_numpy(X).cuda()
-    z = g.forward(Xt).cpu().numpy()
+    z = g.forward(Xt).cpu().numpy().astype(np.float64)
     seeds, pmax = g.predict(Xt, P=P, tau=0.0)
     torch.cuda.synchronize()
     g.sync()
-    ids, pm = M.top_p(z.astype(np.float64), P)
-    assert np.array_equal(seeds.cpu().numpy().view(np.uint32), ids)
-    np.testing.assert_allclose(pmax.cpu().numpy(), pm, rtol=1e-4)
-    # fallback: rows below tau start with ANN_INVALID_ID
-    tau = float(np.median(pm))
+    s = seeds.cpu().numpy().view(np.uint32)
+    # 1. self-consistency: the fused epilogue picks the top P of the very
+    #    logits the unfused GEMM writes (same FP32 values), ties to the
+    #    smaller index, and its softmax maximum matches
+    own = np.lexsort((np.broadcast_to(np.arange(out), z.shape), -z), axis=1)[:, :P]
+    assert np.array_equal(s, own)
+    e = np.exp(z - z.max(axis=1, keepdims=True))
+    np.testing.assert_allclose(pmax.cpu().numpy(), 1.0 / e.sum(axis=1), rtol=1e-4)
+    # 2. against the oracle's FP64 forward: equal sets except where the P-th
+    #    and (P+1)-th oracle logits are closer than twice the row's largest
+    #    GPU-oracle logit deviation (a near-tie the two precisions may order
+    #    differently)
+    f = M.forward(m, X)
+    want, _ = M.top_p(f["z"], P)
+    zs = np.sort(f["z"], axis=1)[:, ::-1]
+    dev = np.abs(z - f["z"]).max(axis=1)
+    gap_ok = (zs[:, P - 1] - zs[:, P]) > 2.0 * dev
+    same = np.array([set(a) == set(b) for a, b in zip(s, want)])
+    assert same[gap_ok].all() and gap_ok.mean() > 0.5, gap_ok.mean()
+    # 3. fallback: rows below tau start with ANN_INVALID_ID
+    tau = float(np.median(pmax.cpu().numpy()))
     s2, p2 = g.predict(Xt, P=P, tau=tau)
     s2 = s2.cpu().numpy().view(np.uint32)
     low = p2.cpu().numpy() < tau
     assert low.any() and (~low).any()
-    assert (s2[low, 0] == 0xFFFFFFFF).all() and np.array_equal(s2[~low], ids[~low])
+    assert (s2[low, 0] == 0xFFFFFFFF).all() and np.array_equal(s2[~low], s[~low])
     g.close()
 
 

@@ -7,6 +7,7 @@ The cache directory is ``$ANN_CACHE_DIR`` or ``~/.cache/paper_2507_17094_gb300``
 from __future__ import annotations
 
 import hashlib
+import sys
 import json
 import os
 import time
@@ -54,10 +55,10 @@ def load_dataset(spec: WorkloadSpec, off_fraction: float = 0.0, device=None, use
     X, _ = spec.mixture().sample(spec.n, spec.seeds["base"])
     Q = make_queries(spec, off_fraction=off_fraction)
     if verbose:
-        print(f"[dataset] {spec.name}: vectors in {time.time() - t0:.1f}s", flush=True)
+        print(f"[dataset] {spec.name}: vectors in {time.time() - t0:.1f}s", file=sys.stderr, flush=True)
     G = build_graph(X, spec.degree, spec.knn_k, spec.graph, device=device, seed=spec.seeds["base"])
     if verbose:
-        print(f"[dataset] {spec.name}: graph in {time.time() - t0:.1f}s", flush=True)
+        print(f"[dataset] {spec.name}: graph in {time.time() - t0:.1f}s", file=sys.stderr, flush=True)
     S = ghost_sample(spec.n, spec.ghost_n, spec.seeds["ghost"])
     Gg = build_graph(X[S], spec.ghost_degree, 2 * spec.ghost_degree, "exact", device=device,
                      seed=spec.seeds["ghost"])
@@ -69,7 +70,7 @@ def load_dataset(spec: WorkloadSpec, off_fraction: float = 0.0, device=None, use
             np.save(tmp, getattr(ds, n))
             os.replace(tmp, os.path.join(path, n + ".npy"))
     if verbose:
-        print(f"[dataset] {spec.name}: built in {ds.build_s:.1f}s", flush=True)
+        print(f"[dataset] {spec.name}: built in {ds.build_s:.1f}s", file=sys.stderr, flush=True)
     return ds
 
 
