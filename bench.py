@@ -195,21 +195,21 @@ def params_for(form: dict, L: int, seed: int) -> dict:
     return p
 
 
-def train_entry(ds, spec, index, dev, verbose):
+def train_entry(ds, spec, index, dev, verbose, n_train=200_000, epochs=8):
     """The learned entry for this workload: labels from ghost staging on
     200,000 training queries, 8 epochs of AdamW, tau from a validation split."""
     import torch
     from paper_2507_17094_gb300.entry import LearnedEntry, ghost_labels
     from workloads import init_mlp_params, make_queries
     t0 = time.time()
-    Qtr = torch.from_numpy(make_queries(spec, nq=200_000, seed=spec.seeds["query"] + 100)).to(dev)
+    Qtr = torch.from_numpy(make_queries(spec, nq=n_train, seed=spec.seeds["query"] + 100)).to(dev)
     Qva = torch.from_numpy(make_queries(spec, nq=5_000, seed=spec.seeds["query"] + 200)).to(dev)
     ytr = ghost_labels(index, Qtr, seed=spec.seeds["search"])
     yva = ghost_labels(index, Qva, seed=spec.seeds["search"])
     le = LearnedEntry(index, init_mlp_params(spec.d, 512, 512, spec.ghost_n, spec.seeds["mlp"]))
-    losses = le.fit(Qtr, ytr, epochs=8, batch=1024, lr=1e-3, seed=spec.seeds["mlp"])
+    losses = le.fit(Qtr, ytr, epochs=epochs, batch=1024, lr=1e-3, seed=spec.seeds["mlp"])
     tau, hit = le.calibrate(Qva, yva)
-    info = {"train_queries": 200_000, "epochs": 8, "loss_first_last": [float(losses[0]), float(losses[-1])],
+    info = {"train_queries": n_train, "epochs": epochs, "loss_first_last": [float(losses[0]), float(losses[-1])],
             "val_label_in_top8": hit, "tau": tau, "train_s": time.time() - t0,
             "mlp": f"{spec.d}->512->512->{spec.ghost_n}"}
     if verbose:
@@ -234,6 +234,39 @@ def algorithmic_bytes(st, spec, storage: int, rerank: bool) -> np.ndarray:
             + 8 * k)
 
 
+# ------------------------------------------------------------------ serving leg
+def serve_leg(A, index, entry, ds, spec, args):
+    """Poisson arrivals of query batches (sizes uniform in 1..4,096, k in
+    {10, 100}, itopk in {64, 256}) into the continuous-batching server on the
+    FP16 index, with the learned entry when one was trained (else ghost
+    staging). Reports whole-trace QPS and per-request latency percentiles."""
+    rng = np.random.default_rng(spec.seeds["search"] + 7)
+    learned = entry is not None
+    base = dict(entry=2 if learned else 1, dgs_discard=0.5, ghost_max_iters=64, ghost_max_iters_given=4,
+                rerank=1, seed=spec.seeds["search"])
+    srv = A.Server(index, capacity=65536, max_requests=128,
+                   max_params=dict(k=100, itopk=256, max_iters=544, ghost_itopk=64, **base),
+                   mlp=entry.mlp if learned else None, seeds_per_query=8, tau=entry.tau if learned else 0.0)
+    trace, t = [], 0.0
+    for rid in range(args.serve_requests):
+        n = int(rng.integers(1, 4097))
+        off = int(rng.integers(0, len(ds.Q) - n))
+        L = int(rng.choice([64, 256]))
+        t += float(rng.exponential(1.0 / args.serve_rate))
+        trace.append((t, rid, ds.Q[off:off + n], dict(k=int(rng.choice([10, 100])), itopk=L, max_iters=2 * L + 32,
+                                                       qid_base=rid << 20, **base)))
+    warm = [(0.0, 10**9 + i, ds.Q[:64], dict(trace[0][3], qid_base=0)) for i in range(4)]
+    A.replay(srv, warm)
+    res, wall = A.replay(srv, trace, timeout_s=300)
+    srv.close()
+    lat = np.array([res[r][2] for _, r, _, _ in trace]) * 1e3
+    nq = sum(len(q) for _, _, q, _ in trace)
+    return {"requests": len(trace), "queries": nq, "qps": nq / wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "offered_rate_req_s": args.serve_rate,
+            "entry": "learned" if learned else "ghost", "storage": "f16",
+            "mix": "batch 1-4096 uniform, k {10,100}, itopk {64,256}, Poisson arrivals"}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -254,6 +287,8 @@ def run_ours(args):
     ds = load_dataset(spec, device=dev, verbose=verbose)
     forms = forms_for(spec)
     headline = "paper_fp32"
+    if args.forms and headline not in args.forms.split(","):
+        headline = args.forms.split(",")[0]
     seed = spec.seeds["search"]
 
     gt_sample = min(args.gt_sample, spec.nq)
@@ -318,7 +353,8 @@ def run_ours(args):
             continue
         ix = index_for(form["storage"])
         if form["entry"] == 2 and form["storage"] not in entries:
-            entries[form["storage"]], info = train_entry(ds, spec, ix, dev, verbose)
+            entries[form["storage"]], info = train_entry(ds, spec, ix, dev, verbose, args.train_queries,
+                                                         args.epochs)
             results.setdefault("_learned_entry", {})[form["storage"]] = info
         run = stepper(ix, name, form)
         sweep = []
@@ -404,6 +440,13 @@ def run_ours(args):
                  hash_resets=int(stn["hash_resets"].sum()))
         del r["sweep"]
 
+    # ------------------------------------------------------------ serving (continuous batching)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serve_leg(A, index_for(1), entries.get(1), ds, spec, args)
+        if verbose:
+            print(f"[bench] serving: {serving}", file=sys.stderr, flush=True)
+
     # ------------------------------------------------------------ e2e (host buffers)
     Qh = torch.from_numpy(ds.Q).pin_memory().numpy()
     e2e_steps = max(3, min(args.steps, 50))
@@ -462,6 +505,7 @@ def run_ours(args):
                 "api": "ann_search_host (pinned host buffers)"},
         "gpu_launches": args.steps,
         "cpu_baseline": cpu_baseline,
+        "serving": serving,
     }
     for le in entries.values():
         le.close()
@@ -542,6 +586,11 @@ def main(argv=None):
     ap.add_argument("--gt-sample", type=int, default=1000)
     ap.add_argument("--cpu-sample", type=int, default=10000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--train-queries", type=int, default=200_000)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-rate", type=float, default=400.0)
+    ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("-v", "--verbose", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -940,11 +940,12 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     a.stage_rows = (uint32_t)std::min(32, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
     // visited table: at least twice (queue + one iteration's candidates);
     // beyond that as large as still fits the target number of warps per SM
-    // (16 by default; up to 4096 entries), so resets stay rare
+    // (28 by default, measured best of 16-32 on the 1M x 96 workload; up to
+    // 4096 entries), so resets stay rare
     const uint32_t need = 2 * (cap_buf + cap_cand);
     const uint32_t hb_min = std::max(8u, bits_for(need));
     uint32_t hb = hb_min;
-    const int target_warps = std::min(32, std::max(4, env_int("ANN_WARPS_PER_SM", 16)));
+    const int target_warps = std::min(32, std::max(4, env_int("ANN_WARPS_PER_SM", 28)));
     const size_t sm_bytes = ix->smem_optin + 1024;                   // shared memory of one SM
     const size_t warp_budget = (sm_bytes - (size_t)(target_warps / 4) * 1024) / target_warps;
     while (hb < 12) {

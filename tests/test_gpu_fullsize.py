@@ -1,0 +1,148 @@
+"""Full-size workloads in the benchmark's launch configuration: every query is
+searched on the GPU as one batch; a seeded sample of queries is searched by
+the CPU oracle and must match element by element (ids and distances
+bit-identical); recall is checked against the FP64 ground truth of the
+sample. Datasets are built on the GPU by the input generators and cached."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import paper_2507_17094_gb300 as A
+    assert torch.cuda.is_available()
+    A.build()
+
+
+def sample_rows(n, m, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, size=m, replace=False))
+
+
+def gpu_search(ix, Q, **p):
+    import paper_2507_17094_gb300 as A
+    ids, dists, st = ix.search(torch.from_numpy(Q).cuda(), stats=True, **p)
+    torch.cuda.synchronize()
+    ix.sync()
+    return ids.cpu().numpy().view(np.uint32), dists.cpu().numpy(), A.stats_to_numpy(st)
+
+
+def check_sample(ds, storage, g_ids, g_d, idx, params, recall_min):
+    oi = O.OracleIndex(ds.X, ds.G, storage, ds.S, ds.Gg)
+    Qs = ds.Q[idx]
+    o_ids, o_d, _ = O.search(oi, Qs, **params)
+    assert np.array_equal(g_ids[idx], o_ids)
+    assert np.array_equal(g_d[idx].view(np.uint32), o_d.view(np.uint32))
+    k = params["k"]
+    gt, gd = O.knn_f64(ds.X, Qs, k)
+    rec = O.recall_at_k(g_ids[idx], gt, gd, ds.X, Qs, min(k, 10))[0]
+    assert rec >= recall_min, rec
+    return rec
+
+
+def test_scale_1m_bench_configuration():
+    """Workload 2 (1M x 96, degree 64, 10,000 queries) at the benchmark's
+    headline setting: ghost staging + DGS, FP32, itopk 32."""
+    import paper_2507_17094_gb300 as A
+    from workloads import CONFIGS, load_dataset
+    ds = load_dataset(CONFIGS[2], device="cuda")
+    ix = A.Index(ds.X, ds.G, storage=A.F32, ghost_ids=ds.S, ghost_graph=ds.Gg)
+    p = dict(k=10, itopk=32, search_width=1, max_iters=96, entry=1, dgs_discard=0.5, dgs_cooldown=0.3,
+             ghost_max_iters=64, seed=4002)
+    g_ids, g_d, st = gpu_search(ix, ds.Q, **p)
+    assert (st["status"] == 0).all()
+    check_sample(ds, O.F32, g_ids, g_d, sample_rows(len(ds.Q), 400, 1), p, 0.95)
+    ix.close()
+
+
+@pytest.mark.parametrize("storage,k,itopk", [(O.F16, 10, 128), (O.E4M3, 10, 128), (O.F16, 100, 256)])
+def test_precision_10m(storage, k, itopk):
+    """Workload 3 (10M x 128 integers, degree 32): FP16 and E4M3 storage with
+    FP32 rerank, k = 10 and k = 100."""
+    import paper_2507_17094_gb300 as A
+    from workloads import CONFIGS, load_dataset
+    ds = load_dataset(CONFIGS[3], device="cuda")
+    ix = A.Index(ds.X, ds.G, storage=storage, ghost_ids=ds.S, ghost_graph=ds.Gg)
+    p = dict(k=k, itopk=itopk, max_iters=2 * itopk + 32, entry=1, dgs_discard=0.5, ghost_max_iters=64,
+             rerank=1, seed=4003)
+    g_ids, g_d, st = gpu_search(ix, ds.Q, **p)
+    assert (st["status"] == 0).all()
+    rec = check_sample(ds, storage, g_ids, g_d, sample_rows(len(ds.Q), 150, 2), p, 0.9)
+    print(f"workload 3 storage {storage} k {k} itopk {itopk}: recall {rec:.3f}")
+    ix.close()
+
+
+def test_learned_entry_5m():
+    """Workload 4 (5M x 256, Zipf cluster sizes, ghost set 50,000): the MLP
+    256->512->512->50,000 trained on 200,000 ghost-staging labels, against
+    plain ghost staging on 10,000 held-out queries (20% between clusters)."""
+    import paper_2507_17094_gb300 as A
+    from paper_2507_17094_gb300.entry import LearnedEntry, ghost_labels
+    from workloads import CONFIGS, init_mlp_params, load_dataset, make_queries
+    spec = CONFIGS[4]
+    ds = load_dataset(spec, off_fraction=0.2, device="cuda")
+    ix = A.Index(ds.X, ds.G, storage=A.F16, ghost_ids=ds.S, ghost_graph=ds.Gg)
+    Qtr = torch.from_numpy(make_queries(spec, nq=200_000, seed=spec.seeds["query"] + 100)).cuda()
+    Qva = torch.from_numpy(make_queries(spec, nq=5_000, seed=spec.seeds["query"] + 200)).cuda()
+    le = LearnedEntry(ix, init_mlp_params(spec.d, 512, 512, spec.ghost_n, spec.seeds["mlp"]), max_batch=10_000)
+    losses = le.fit(Qtr, ghost_labels(ix, Qtr, seed=1), epochs=8, seed=3)
+    tau, hit = le.calibrate(Qva, ghost_labels(ix, Qva, seed=1))
+    assert losses[-1] < losses[0] and hit > 0.5
+    Q = torch.from_numpy(ds.Q).cuda()
+    seeds, _ = le.seeds(Q)
+    common = dict(k=10, itopk=64, max_iters=160, dgs_discard=0.5, rerank=1, seed=4004, ghost_max_iters=64)
+    idx = sample_rows(len(ds.Q), 200, 3)
+    gt, gd = O.knn_f64(ds.X, ds.Q[idx], 10)
+    out = {}
+    for name, extra in (("ghost", dict(entry=1)), ("learned", dict(entry=2, given=seeds, ghost_max_iters_given=4))):
+        ids, d, st = ix.search(Q, stats=True, **common, **extra)
+        torch.cuda.synchronize()
+        stn = A.stats_to_numpy(st)
+        rec = O.recall_at_k(ids.cpu().numpy().view(np.uint32)[idx], gt, gd, ds.X, ds.Q[idx], 10)[0]
+        out[name] = (rec, stn["ghost_vec_rows"].mean())
+    print(f"workload 4: ghost staging recall {out['ghost'][0]:.3f} ghost rows {out['ghost'][1]:.0f}; "
+          f"learned recall {out['learned'][0]:.3f} ghost rows {out['learned'][1]:.0f}; tau {tau:.3g}, val hit {hit:.3f}")
+    assert out["learned"][1] < out["ghost"][1]
+    assert out["learned"][0] >= out["ghost"][0] - 0.02
+    le.close()
+    ix.close()
+
+
+def test_serving_20m_poisson():
+    """Workload 5 (20M x 96 FP16, degree 32): Poisson arrivals of batches of
+    1-4,096 queries with k in {10, 100} and itopk in {64, 256}, ghost staging
+    + FP16 distances + rerank; sampled requests match the batch search."""
+    import paper_2507_17094_gb300 as A
+    from workloads import CONFIGS, load_dataset
+    spec = CONFIGS[5]
+    ds = load_dataset(spec, device="cuda")
+    ix = A.Index(ds.X, ds.G, storage=A.F16, ghost_ids=ds.S, ghost_graph=ds.Gg)
+    srv = A.Server(ix, capacity=32768, max_requests=64,
+                   max_params=dict(k=100, itopk=256, max_iters=544, entry=1, dgs_discard=0.5, rerank=1,
+                                   ghost_itopk=64))
+    rng = np.random.default_rng(spec.seeds["search"])
+    trace, t = [], 0.0
+    for rid in range(60):
+        n = int(rng.integers(1, 4097))
+        off = int(rng.integers(0, len(ds.Q) - n))
+        L = int(rng.choice([64, 256]))
+        prm = dict(k=int(rng.choice([10, 100])), itopk=L, max_iters=2 * L + 32, entry=1, dgs_discard=0.5,
+                   ghost_max_iters=64, rerank=1, seed=5, qid_base=rid << 20)
+        t += float(rng.exponential(0.002))
+        trace.append((t, rid, ds.Q[off:off + n], prm))
+    res, wall = A.replay(srv, trace, timeout_s=600)
+    srv.close()
+    lat = np.array([res[r][2] for _, r, _, _ in trace])
+    nq = sum(len(q) for _, _, q, _ in trace)
+    print(f"workload 5 serving: {nq} queries in {wall:.3f} s = {nq / wall:.0f} QPS, "
+          f"p50 {np.percentile(lat, 50) * 1e3:.1f} ms, p99 {np.percentile(lat, 99) * 1e3:.1f} ms")
+    for _, rid, q, prm in trace[:: 15]:
+        ids, d, _ = gpu_search(ix, q, **prm)
+        assert np.array_equal(ids, res[rid][0]) and np.array_equal(d, res[rid][1])
+    ix.close()
