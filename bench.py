@@ -251,9 +251,10 @@ def serve_leg(A, index, entry, ds, spec, args):
     for rid in range(args.serve_requests):
         n = int(rng.integers(1, 4097))
         off = int(rng.integers(0, len(ds.Q) - n))
-        L = int(rng.choice([64, 256]))
+        k = int(rng.choice([10, 100]))
+        L = max(k, int(rng.choice([64, 256])))      # a queue holds at least the k results
         t += float(rng.exponential(1.0 / args.serve_rate))
-        trace.append((t, rid, ds.Q[off:off + n], dict(k=int(rng.choice([10, 100])), itopk=L, max_iters=2 * L + 32,
+        trace.append((t, rid, ds.Q[off:off + n], dict(k=k, itopk=L, max_iters=2 * L + 32,
                                                        qid_base=rid << 20, **base)))
     warm = [(0.0, 10**9 + i, ds.Q[:64], dict(trace[0][3], qid_base=0)) for i in range(4)]
     A.replay(srv, warm)
@@ -264,7 +265,7 @@ def serve_leg(A, index, entry, ds, spec, args):
     return {"requests": len(trace), "queries": nq, "qps": nq / wall, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "offered_rate_req_s": args.serve_rate,
             "entry": "learned" if learned else "ghost", "storage": "f16",
-            "mix": "batch 1-4096 uniform, k {10,100}, itopk {64,256}, Poisson arrivals"}
+            "mix": "batch 1-4096 uniform, k {10,100}, itopk {64,256} raised to k, Poisson arrivals"}
 
 
 # ------------------------------------------------------------------ our arm
@@ -388,7 +389,7 @@ def run_ours(args):
     head_run = stepper(ix, headline, form)
     L = results[headline]["itopk"]
     p = params_for(form, L, seed)
-    ids, dists, st = ix.search(Qd, stream=stream, stats=True, **p)
+    ids, dists, st = head_run(p, out=None, stats=True)
     torch.cuda.synchronize(dev)
     ix.sync()
     st_np = A.stats_to_numpy(st)

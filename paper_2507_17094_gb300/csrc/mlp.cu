@@ -113,14 +113,90 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool better(float va, uint32_t ia, float vb, uint32_t ib)
 {
     return va > vb || (va == vb && ia < ib);
 }
 
 // ------------------------------------------------------------------ GEMM
+// Persistent and warp-specialised: one CTA per SM walks the output tiles
+// (tile = blockIdx.x + i * gridDim.x, row-block-major so neighbouring CTAs
+// share A tiles in L2). Warp 0 streams A/B tiles with TMA into the stage ring,
+// warp 1 issues the MMAs into one of two tensor-memory accumulators, warps
+// 2-5 run the epilogue of the previous tile from the other accumulator, so
+// loads, MMAs and epilogues of consecutive tiles overlap.
+constexpr int GEMM_THREADS = 192;
+
 template <int EPI>
-__global__ void __launch_bounds__(128, 1)
+__device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m, uint32_t M, uint32_t nb, uint32_t N,
+                                               const EpiArgs &e, float (&tv)[TOPP], uint32_t (&ti)[TOPP], float &mx,
+                                               float &sm)
+{
+    if (m >= M) return;
+    if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
+        float *out = e.c + (size_t)m * e.ldc + nb;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (nb + j < N) out[j] = v[j] + (EPI == EPI_BIAS_F32 ? e.bias[nb + j] : 0.0f);
+    } else if (EPI == EPI_BIAS_RELU_BF16) {
+        __nv_bfloat16 *out = e.cb + (size_t)m * e.ldc + nb;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (nb + j < N) out[j] = __float2bfloat16_rn(fmaxf(v[j] + e.bias[nb + j], 0.0f));
+    } else {
+        // logits of the chunk, their max and exp-sum by trees (no serial
+        // chain), one online-softmax combine, then top-P insertion behind a
+        // threshold test
+        float x[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x[j] = (nb + j < N) ? v[j] + e.bias[nb + j] : -INFINITY;
+        float t[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) t[j] = fmaxf(x[j], x[j + 16]);
+#pragma unroll
+        for (int w = 8; w; w >>= 1)
+#pragma unroll
+            for (int j = 0; j < w; ++j) t[j] = fmaxf(t[j], t[j + w]);
+        const float cm = t[0];
+        if (cm > -INFINITY) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) t[j] = __expf(x[j] - cm) + __expf(x[j + 16] - cm);
+#pragma unroll
+            for (int w = 8; w; w >>= 1)
+#pragma unroll
+                for (int j = 0; j < w; ++j) t[j] += t[j + w];
+            const float cs = t[0];
+            if (cm > mx) {
+                sm = sm * __expf(mx - cm) + cs;
+                mx = cm;
+            } else {
+                sm += cs * __expf(cm - mx);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t n = nb + j;
+            if (n >= N || !better(x[j], n, tv[TOPP - 1], ti[TOPP - 1])) continue;
+            tv[TOPP - 1] = x[j];
+            ti[TOPP - 1] = n;
+#pragma unroll
+            for (int p = TOPP - 1; p > 0; --p) {
+                if (better(tv[p], ti[p], tv[p - 1], ti[p - 1])) {
+                    const float tt = tv[p]; tv[p] = tv[p - 1]; tv[p - 1] = tt;
+                    const uint32_t u = ti[p]; ti[p] = ti[p - 1]; ti[p - 1] = u;
+                }
+            }
+        }
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, uint32_t M,
                 uint32_t N, uint32_t K, EpiArgs e)
 {
@@ -131,23 +207,28 @@ __global__ void __launch_bounds__(128, 1)
     uint8_t *sB = smem + STAGES * TILE_A;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * (TILE_A + TILE_B));
     uint64_t *empty = full + STAGES;
-    uint64_t *accb = empty + STAGES;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accb + 1);
+    uint64_t *acc_full = empty + STAGES;     // [2]: MMA -> epilogue
+    uint64_t *acc_empty = acc_full + 2;      // [2]: epilogue -> MMA
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const uint32_t nkb = (K + BK - 1) / BK;
+    const uint32_t n_tiles = (N + BN - 1) / BN, m_tiles = (M + BM - 1) / BM;
+    const uint32_t tiles = n_tiles * m_tiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
         fence_mbar_init();
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                     "r"((uint32_t)BN)
+                     "r"((uint32_t)(2 * BN))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -156,106 +237,87 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // producer: TMA tiles of A and B into the ring
-        for (uint32_t kb = 0; kb < nkb; ++kb) {
-            const uint32_t s = kb % STAGES, r = kb / STAGES;
-            if (!mbar_wait_bounded(&empty[s], (r & 1) ^ 1, e.err)) break;
-            mbar_arrive_expect_tx(&full[s], TILE_A + TILE_B);
-            tma_load_2d(sA + s * TILE_A, &tA, (int)(kb * BK), (int)m0, &full[s]);
-            tma_load_2d(sB + s * TILE_B, &tB, (int)(kb * BK), (int)n0, &full[s]);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(BM, BN);
-        bool ok = true;
-        for (uint32_t kb = 0; kb < nkb && ok; ++kb) {
-            const uint32_t s = kb % STAGES, r = kb / STAGES;
-            ok = mbar_wait_bounded(&full[s], r & 1, e.err);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t a0 = smem_addr(sA + s * TILE_A), b0 = smem_addr(sB + s * TILE_B);
-#pragma unroll
-            for (uint32_t k = 0; k < BK / 16; ++k)
-                mma_bf16(tmem, desc_sw128(a0 + k * 32), desc_sw128(b0 + k * 32), idesc, (kb | k) != 0);
-            mma_commit(&empty[s]);
-        }
-        mma_commit(accb);
-    }
-    __syncwarp();
-
-    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w+31
-    const bool ok = mbar_wait_bounded(accb, 0, e.err);
-    tc_fence_after();
-    const uint32_t row = warp * 32 + lane;
-    const uint32_t m = m0 + row;
-    float tv[TOPP];
-    uint32_t ti[TOPP];
-    float mx = -INFINITY, sm = 0.0f;
-    if (EPI == EPI_TOPP) {
-#pragma unroll
-        for (int p = 0; p < TOPP; ++p) { tv[p] = -INFINITY; ti[p] = 0xFFFFFFFFu; }
-    }
-    if (ok) {
-#pragma unroll 1
-        for (uint32_t c0 = 0; c0 < BN; c0 += 32) {
-            float v[32];
-            __syncwarp();
-            tmem_ld32(tmem + ((warp * 32u) << 16) + c0, v);
-            const uint32_t nb = n0 + c0;
-            if (m >= M) {
-                // rows past M: nothing to store
-            } else if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
-                float *out = e.c + (size_t)m * e.ldc + nb;
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (nb + j < N) out[j] = v[j] + (EPI == EPI_BIAS_F32 ? e.bias[nb + j] : 0.0f);
-            } else if (EPI == EPI_BIAS_RELU_BF16) {
-                __nv_bfloat16 *out = e.cb + (size_t)m * e.ldc + nb;
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (nb + j < N) out[j] = __float2bfloat16_rn(fmaxf(v[j] + e.bias[nb + j], 0.0f));
-            } else {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const uint32_t n = nb + j;
-                    if (n >= N) continue;
-                    const float x = v[j] + e.bias[n];
-                    if (x > mx) {
-                        sm = sm * __expf(mx - x) + 1.0f;
-                        mx = x;
-                    } else {
-                        sm += __expf(x - mx);
-                    }
-                    if (better(x, n, tv[TOPP - 1], ti[TOPP - 1])) {
-                        tv[TOPP - 1] = x;
-                        ti[TOPP - 1] = n;
-#pragma unroll
-                        for (int p = TOPP - 1; p > 0; --p) {
-                            if (better(tv[p], ti[p], tv[p - 1], ti[p - 1])) {
-                                const float t = tv[p]; tv[p] = tv[p - 1]; tv[p - 1] = t;
-                                const uint32_t u = ti[p]; ti[p] = ti[p - 1]; ti[p - 1] = u;
-                            }
-                        }
-                    }
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const uint32_t m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+                for (uint32_t kb = 0; kb < nkb; ++kb, ++it) {
+                    const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                    if (!(ok = mbar_wait_bounded(&empty[s], ph ^ 1, e.err))) break;
+                    mbar_arrive_expect_tx(&full[s], TILE_A + TILE_B);
+                    tma_load_2d(sA + s * TILE_A, &tA, (int)(kb * BK), (int)m0, &full[s]);
+                    tma_load_2d(sB + s * TILE_B, &tB, (int)(kb * BK), (int)n0, &full[s]);
                 }
             }
         }
-        if (EPI == EPI_TOPP && m < M) {
-            float *o = e.part + ((size_t)m * e.ntiles + blockIdx.x) * (2 * TOPP + 2);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            uint32_t it = 0, tc = 0;
+            bool ok = true;
+            for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tc) {
+                const uint32_t buf = tc & 1, use = tc >> 1;
+                if (!(ok = mbar_wait_bounded(&acc_empty[buf], (use & 1) ^ 1, e.err))) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + buf * BN;
+                for (uint32_t kb = 0; kb < nkb; ++kb, ++it) {
+                    const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
+                    if (!(ok = mbar_wait_bounded(&full[s], ph, e.err))) break;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_addr(sA + s * TILE_A), b0 = smem_addr(sB + s * TILE_B);
 #pragma unroll
-            for (int p = 0; p < TOPP; ++p) {
-                o[p] = tv[p];
-                o[TOPP + p] = __uint_as_float(ti[p]);
+                    for (uint32_t k = 0; k < BK / 16; ++k)
+                        mma_bf16(acc, desc_sw128(a0 + k * 32), desc_sw128(b0 + k * 32), idesc, (kb | k) != 0);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&acc_full[buf]);
             }
-            o[2 * TOPP] = mx;
-            o[2 * TOPP + 1] = sm;
+        }
+    } else {
+        // epilogue warps 2..5: warp w reads accumulator lanes 32 * (w % 4) ..
+        const uint32_t q = warp & 3;
+        uint32_t tc = 0;
+        for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
+            const uint32_t buf = tc & 1, use = tc >> 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[buf], use & 1, e.err));
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
+            const uint32_t m = m0 + q * 32 + lane;
+            float tv[TOPP];
+            uint32_t ti[TOPP];
+            float mx = -INFINITY, sm = 0.0f;
+#pragma unroll
+            for (int p = 0; p < TOPP; ++p) { tv[p] = -INFINITY; ti[p] = 0xFFFFFFFFu; }
+#pragma unroll 1
+            for (uint32_t c0 = 0; c0 < BN; c0 += 32) {
+                float v[32];
+                __syncwarp();
+                tmem_ld32(tmem + buf * BN + ((q * 32u) << 16) + c0, v);
+                epilogue_chunk<EPI>(v, m, M, n0 + c0, N, e, tv, ti, mx, sm);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            if (EPI == EPI_TOPP && m < M) {
+                float *o = e.part + ((size_t)m * e.ntiles + (t % n_tiles)) * (2 * TOPP + 2);
+#pragma unroll
+                for (int p = 0; p < TOPP; ++p) {
+                    o[p] = tv[p];
+                    o[TOPP + p] = __uint_as_float(ti[p]);
+                }
+                o[2 * TOPP] = mx;
+                o[2 * TOPP + 1] = sm;
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
+                     : "memory");
     }
 }
 
@@ -532,8 +594,11 @@ ann_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, uint32_t M, uint
         ANN_CUDA(cudaFuncSetAttribute(gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
         attr = true;
     }
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    gemm_kernel<EPI><<<grid, 128, GEMM_SMEM, st>>>(ta, tb, M, N, K, e);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+    gemm_kernel<EPI><<<std::min<uint32_t>(tiles, (uint32_t)sms), GEMM_THREADS, GEMM_SMEM, st>>>(ta, tb, M, N, K, e);
     ANN_CUDA(cudaGetLastError());
     return ANN_OK;
 }

@@ -479,13 +479,16 @@ struct WarpSearch {
     // kept). Score = matching sign bits; keep the top n_keep by (score desc,
     // slot asc): find the threshold score t by binary search with ballots,
     // keep scores above t and the first ties at t.
-    __device__ uint32_t dgs_keep(const View &v, uint32_t pi, uint32_t n_keep)
+    // NW = number of 32-slot words the degree spans (1, 2 or 4), so no
+    // ballot is spent on slots past the degree.
+    template <uint32_t NW>
+    __device__ uint32_t dgs_keep_nw(const View &v, uint32_t pi, uint32_t n_keep)
     {
         const uint32_t w = a.w, deg = v.deg;
         const uint32_t *pq = pqb() + pi * w;
-        int sc[kMaxDegWords];
+        int sc[NW];
 #pragma unroll
-        for (uint32_t r = 0; r < kMaxDegWords; ++r) {
+        for (uint32_t r = 0; r < NW; ++r) {
             const uint32_t j = lane + 32 * r;
             sc[r] = -2;  // beyond the degree: never kept
             if (j < deg) {
@@ -504,23 +507,30 @@ struct WarpSearch {
             const int mid = (lo + hi) >> 1;
             uint32_t c = 0;
 #pragma unroll
-            for (uint32_t r = 0; r < kMaxDegWords; ++r) c += __popc(__ballot_sync(0xffffffffu, sc[r] >= mid));
+            for (uint32_t r = 0; r < NW; ++r) c += __popc(__ballot_sync(0xffffffffu, sc[r] >= mid));
             if (c >= n_keep) lo = mid;
             else hi = mid;
         }
         uint32_t above = 0;
 #pragma unroll
-        for (uint32_t r = 0; r < kMaxDegWords; ++r) above += __popc(__ballot_sync(0xffffffffu, sc[r] > lo));
+        for (uint32_t r = 0; r < NW; ++r) above += __popc(__ballot_sync(0xffffffffu, sc[r] > lo));
         const uint32_t need = n_keep - above;
         uint32_t keep = 0, ties_before = 0;
 #pragma unroll
-        for (uint32_t r = 0; r < kMaxDegWords; ++r) {
+        for (uint32_t r = 0; r < NW; ++r) {
             const uint32_t tm = __ballot_sync(0xffffffffu, sc[r] == lo);
             const bool tie_kept = sc[r] == lo && ties_before + __popc(tm & lanemask_lt()) < need;
             if (sc[r] > lo || tie_kept) keep |= 1u << r;
             ties_before += __popc(tm);
         }
         return keep;
+    }
+
+    __device__ uint32_t dgs_keep(const View &v, uint32_t pi, uint32_t n_keep)
+    {
+        if (v.deg <= 32) return dgs_keep_nw<1>(v, pi, n_keep);
+        if (v.deg <= 64) return dgs_keep_nw<2>(v, pi, n_keep);
+        return dgs_keep_nw<kMaxDegWords>(v, pi, n_keep);
     }
 
     // Steps 3-4 repeated, with DGS and its cool-down (Section 3.3.2).
@@ -700,7 +710,7 @@ struct WarpSearch {
 };
 
 template <int ST>
-__global__ void __launch_bounds__(128) search_kernel(const Args a)
+__global__ void __launch_bounds__(128, 7) search_kernel(const Args a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -730,7 +740,7 @@ __global__ void __launch_bounds__(128) search_kernel(const Args a)
 // warp that finishes a request's last query raises its completion flag in
 // host-mapped memory after a system-scope fence.
 template <int ST>
-__global__ void __launch_bounds__(128) serve_kernel(const Args a, const ServeRing r)
+__global__ void __launch_bounds__(128, 7) serve_kernel(const Args a, const ServeRing r)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

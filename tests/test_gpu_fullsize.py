@@ -34,9 +34,14 @@ def gpu_search(ix, Q, **p):
 
 
 def check_sample(ds, storage, g_ids, g_d, idx, params, recall_min):
+    """Oracle search of the sampled queries, each with the RNG stream it had
+    in the full GPU batch (qid = qid_base + its row in the batch)."""
     oi = O.OracleIndex(ds.X, ds.G, storage, ds.S, ds.Gg)
     Qs = ds.Q[idx]
-    o_ids, o_d, _ = O.search(oi, Qs, **params)
+    base = params.get("qid_base", 0)
+    parts = [O.search(oi, Qs[i:i + 1], **dict(params, qid_base=base + int(r))) for i, r in enumerate(idx)]
+    o_ids = np.concatenate([p[0] for p in parts])
+    o_d = np.concatenate([p[1] for p in parts])
     assert np.array_equal(g_ids[idx], o_ids)
     assert np.array_equal(g_d[idx].view(np.uint32), o_d.view(np.uint32))
     k = params["k"]
@@ -131,8 +136,9 @@ def test_serving_20m_poisson():
     for rid in range(60):
         n = int(rng.integers(1, 4097))
         off = int(rng.integers(0, len(ds.Q) - n))
-        L = int(rng.choice([64, 256]))
-        prm = dict(k=int(rng.choice([10, 100])), itopk=L, max_iters=2 * L + 32, entry=1, dgs_discard=0.5,
+        k = int(rng.choice([10, 100]))
+        L = max(k, int(rng.choice([64, 256])))      # a queue holds at least the k results
+        prm = dict(k=k, itopk=L, max_iters=2 * L + 32, entry=1, dgs_discard=0.5,
                    ghost_max_iters=64, rerank=1, seed=5, qid_base=rid << 20)
         t += float(rng.exponential(0.002))
         trace.append((t, rid, ds.Q[off:off + n], prm))

@@ -105,7 +105,10 @@ def knn_partitioned(X: np.ndarray, K: int, n_parts: int, n_near: int = 2, device
         cn = _sqnorm(cent)
         cd = cn[:, None] + cn[None, :] - 2.0 * (cent @ cent.T)
         cd.fill_diagonal_(float("inf"))
-        near = torch.topk(cd, min(n_near, n_parts - 1), dim=1, largest=False).indices if n_parts > 1 \
+        # candidate partitions by centroid distance; a pool takes the n_near
+        # nearest and then more until it holds at least K + 1 points (tiny
+        # partitions of skewed cluster sizes would otherwise pad their lists)
+        near = torch.topk(cd, min(max(n_near, 32), n_parts - 1), dim=1, largest=False).indices if n_parts > 1 \
             else torch.zeros((1, 0), dtype=torch.int64, device=dev)
         xn = _sqnorm(Xt)
         out = torch.full((n, K), -1, dtype=torch.int64, device=dev)
@@ -116,7 +119,12 @@ def knn_partitioned(X: np.ndarray, K: int, n_parts: int, n_near: int = 2, device
             if a == b:
                 continue
             members = order[a:b]
-            pool = [members] + [order[starts_h[q]:starts_h[q + 1]] for q in near_h[p]]
+            pool, size = [members], b - a
+            for i, q in enumerate(near_h[p]):
+                if i >= n_near and size >= K + 1:
+                    break
+                pool.append(order[starts_h[q]:starts_h[q + 1]])
+                size += starts_h[q + 1] - starts_h[q]
             pool = torch.cat(pool)
             kk = min(K, pool.shape[0] - 1)
             P = Xt[pool]
