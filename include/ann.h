@@ -228,6 +228,15 @@ ann_status ann_mlp_train_epochs(ann_mlp *mlp, const float *x, const uint32_t *la
                                 uint64_t seed, float *epoch_loss, void *stream);
 /* Synchronise `stream` and report (then clear) the MLP's device error word. */
 ann_status ann_mlp_sync(ann_mlp *mlp, void *stream);
+/* Save the FP32 parameters to a file: the 8 bytes "ANNMLP01", the four sizes
+ * (in_dim, hidden1, hidden2, out_dim) as little-endian uint32, then W1, b1,
+ * W2, b2, W3, b3 as little-endian FP32 in the row-major layout above. The
+ * optimizer state is not saved. ANN_EIO if the file cannot be written. */
+ann_status ann_mlp_save(const ann_mlp *mlp, const char *path);
+/* Create an MLP on `device` with room for max_batch rows from a file written
+ * by ann_mlp_save (fresh optimizer state). ANN_EIO if the file cannot be read
+ * or is short, ANN_EINVAL if its magic or sizes are not valid. */
+ann_status ann_mlp_load(const char *path, int device, uint32_t max_batch, ann_mlp **out);
 
 /* ------------------------------------------------------------------------
  * Continuous-batching server (not in the paper). Requests (batches of any

@@ -28,6 +28,7 @@ EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_inde
            "ann_index_export", "ann_search", "ann_search_host", "ann_search_host_noalloc", "ann_sync",
            "ann_encode", "ann_dir_table", "ann_mlp_create", "ann_mlp_free", "ann_mlp_set_params", "ann_mlp_get",
            "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_train_epochs", "ann_mlp_predict", "ann_mlp_sync",
+           "ann_mlp_save", "ann_mlp_load",
            "ann_ghost_index_of", "ann_server_create", "ann_server_submit", "ann_server_poll",
            "ann_server_in_flight", "ann_server_destroy", "ann_last_error")
 
@@ -95,6 +96,8 @@ def lib() -> C.CDLL:
             L.ann_mlp_train_step.argtypes = [vp, vp, vp, u32, f32, f32, f32, f32, f32, vp, vp]
             L.ann_mlp_predict.argtypes = [vp, vp, u32, u32, f32, vp, vp, vp]
             L.ann_mlp_sync.argtypes = [vp, vp]
+            L.ann_mlp_save.argtypes = [vp, C.c_char_p]
+            L.ann_mlp_load.argtypes = [C.c_char_p, C.c_int, u32, C.POINTER(vp)]
             L.ann_mlp_train_epochs.argtypes = [vp, vp, vp, u32, u32, u32, f32, f32, f32, f32, f32, u64, vp, vp]
             L.ann_ghost_index_of.argtypes = [vp, vp, u32, vp, vp]
             L.ann_server_create.argtypes = [vp, C.POINTER(ServerConfig), vp, C.POINTER(vp)]
@@ -262,6 +265,20 @@ class MLP:
         _check(lib().ann_mlp_create(device, in_dim, hidden1, hidden2, out_dim, max_batch, C.byref(self._h)))
         self.dims = (in_dim, hidden1, hidden2, out_dim)
         self.max_batch = max_batch
+
+    @classmethod
+    def load(cls, path: str, max_batch: int, device: int = 0) -> "MLP":
+        """An MLP created from a file written by save()."""
+        self = cls.__new__(cls)
+        self._h = C.c_void_p()
+        _check(lib().ann_mlp_load(os.fsencode(path), device, max_batch, C.byref(self._h)))
+        hdr = np.fromfile(path, dtype=np.uint32, count=6)
+        self.dims = tuple(int(v) for v in hdr[2:6])
+        self.max_batch = max_batch
+        return self
+
+    def save(self, path: str):
+        _check(lib().ann_mlp_save(self._h, os.fsencode(path)))
 
     def close(self):
         if self._h:

@@ -1007,4 +1007,72 @@ ann_status ann_mlp_sync(ann_mlp *m, void *stream)
     return s;
 }
 
+
+// Parameter file: magic, four uint32 sizes, then W1 b1 W2 b2 W3 b3 (FP32);
+// both hosts this builds for are little-endian, so the bytes go out as they are.
+static const char kMlpMagic[8] = {'A', 'N', 'N', 'M', 'L', 'P', '0', '1'};
+
+ann_status ann_mlp_save(const ann_mlp *m, const char *path)
+{
+    if (!m || !path) { set_error("ann_mlp_save: NULL argument"); return ANN_EINVAL; }
+    const uint32_t dims[4] = {m->d, m->h1, m->h2, m->out};
+    std::vector<float> W[3], b[3];
+    const uint32_t rows[3] = {m->h1, m->h2, m->out}, cols[3] = {m->d, m->h1, m->h2};
+    for (int l = 0; l < 3; ++l) { W[l].resize((size_t)rows[l] * cols[l]); b[l].resize(rows[l]); }
+    ann_status s = ann_mlp_get(m, 0, W[0].data(), b[0].data(), W[1].data(), b[1].data(), W[2].data(), b[2].data());
+    if (s != ANN_OK) return s;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) { set_error("ann_mlp_save: cannot open %s", path); return ANN_EIO; }
+    bool ok = std::fwrite(kMlpMagic, 1, 8, f) == 8 && std::fwrite(dims, 4, 4, f) == 4;
+    for (int l = 0; l < 3 && ok; ++l)
+        ok = std::fwrite(W[l].data(), 4, W[l].size(), f) == W[l].size() &&
+             std::fwrite(b[l].data(), 4, b[l].size(), f) == b[l].size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) { set_error("ann_mlp_save: write to %s failed", path); return ANN_EIO; }
+    return ANN_OK;
+}
+
+ann_status ann_mlp_load(const char *path, int device, uint32_t max_batch, ann_mlp **out)
+{
+    if (!path || !out) { set_error("ann_mlp_load: NULL argument"); return ANN_EINVAL; }
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) { set_error("ann_mlp_load: cannot open %s", path); return ANN_EIO; }
+    char magic[8];
+    uint32_t dims[4];
+    if (std::fread(magic, 1, 8, f) != 8 || std::fread(dims, 4, 4, f) != 4) {
+        std::fclose(f);
+        set_error("ann_mlp_load: %s is too short", path);
+        return ANN_EIO;
+    }
+    if (std::memcmp(magic, kMlpMagic, 8) != 0) {
+        std::fclose(f);
+        set_error("ann_mlp_load: %s is not an MLP parameter file", path);
+        return ANN_EINVAL;
+    }
+    for (uint32_t v : dims)
+        if (!v || v % 8 || v > (1u << 24)) {
+            std::fclose(f);
+            set_error("ann_mlp_load: %s has invalid sizes", path);
+            return ANN_EINVAL;
+        }
+    const uint32_t rows[3] = {dims[1], dims[2], dims[3]}, cols[3] = {dims[0], dims[1], dims[2]};
+    std::vector<float> W[3], b[3];
+    bool ok = true;
+    for (int l = 0; l < 3 && ok; ++l) {
+        W[l].resize((size_t)rows[l] * cols[l]);
+        b[l].resize(rows[l]);
+        ok = std::fread(W[l].data(), 4, W[l].size(), f) == W[l].size() &&
+             std::fread(b[l].data(), 4, b[l].size(), f) == b[l].size();
+    }
+    std::fclose(f);
+    if (!ok) { set_error("ann_mlp_load: %s is too short", path); return ANN_EIO; }
+    ann_mlp *m = nullptr;
+    ann_status s = ann_mlp_create(device, dims[0], dims[1], dims[2], dims[3], max_batch, &m);
+    if (s == ANN_OK) s = ann_mlp_set_params(m, W[0].data(), b[0].data(), W[1].data(), b[1].data(), W[2].data(), b[2].data());
+    if (s != ANN_OK) { ann_mlp_free(m); return s; }
+    *out = m;
+    return ANN_OK;
+}
+
 }  // extern "C"

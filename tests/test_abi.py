@@ -48,3 +48,20 @@ def test_host_side_validation(L):
     assert e.value.status == 1
     assert L.ann_search(None, None, 0, None, None, 0, None, None, None, None) == 1
     assert L.ann_index_load(b"/nonexistent/file", 0, 0, 1, 1, C.byref(C.c_void_p())) == 4
+
+
+def test_mlp_file_errors_on_host(L, tmp_path):
+    """ann_mlp_load checks the file before it touches a device."""
+    h = C.c_void_p()
+    assert L.ann_mlp_load(b"/nonexistent/mlp.bin", 0, 8, C.byref(h)) == 4
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"NOTANMLP" + np.array([8, 8, 8, 8], np.uint32).tobytes())
+    assert L.ann_mlp_load(str(bad).encode(), 0, 8, C.byref(h)) == 1
+    short = tmp_path / "short.bin"
+    short.write_bytes(b"ANNMLP01" + np.array([8, 8, 8, 8], np.uint32).tobytes() + b"\0" * 40)
+    assert L.ann_mlp_load(str(short).encode(), 0, 8, C.byref(h)) == 4
+    odd = tmp_path / "odd.bin"
+    odd.write_bytes(b"ANNMLP01" + np.array([8, 12, 8, 8], np.uint32).tobytes())
+    assert L.ann_mlp_load(str(odd).encode(), 0, 8, C.byref(h)) == 1
+    assert not h.value
+    assert L.ann_mlp_save(None, b"x") == 1

@@ -174,3 +174,22 @@ def test_training_reduces_loss():
     acc = (seeds.cpu().numpy()[:, 0].view(np.uint32) == y).mean()
     assert acc > 0.9, acc
     g.close()
+
+
+def test_save_load_round_trip(tmp_path):
+    """A saved and reloaded network has bit-identical parameters and logits."""
+    import paper_2507_17094_gb300 as A
+    m = make_model(64, 128, 128, 256, seed=5)
+    g = gpu_mlp(m, 64)
+    path = str(tmp_path / "mlp.bin")
+    g.save(path)
+    h = A.MLP.load(path, max_batch=64)
+    assert h.dims == (64, 128, 128, 256)
+    for a, b in zip(g.get(0), h.get(0)):
+        assert np.array_equal(a, b)
+    X = torch.from_numpy(np.random.default_rng(6).standard_normal((40, 64)).astype(np.float32)).cuda()
+    za, zb = g.forward(X), h.forward(X)
+    torch.cuda.synchronize()
+    assert torch.equal(za, zb)
+    g.close()
+    h.close()
