@@ -228,10 +228,19 @@ ann_status ann_mlp_train_epochs(ann_mlp *mlp, const float *x, const uint32_t *la
                                 uint64_t seed, float *epoch_loss, void *stream);
 /* Synchronise `stream` and report (then clear) the MLP's device error word. */
 ann_status ann_mlp_sync(ann_mlp *mlp, void *stream);
+/* Per-dimension input standardisation, applied on the device to every query
+ * (forward, training, prediction) before its BF16 rounding:
+ * x' = (x - mean) * inv_std, each operation rounded in FP32. mean and inv_std
+ * are host arrays of in_dim finite floats; both NULL restores the identity
+ * (mean 0, inv_std 1, the state after ann_mlp_create). */
+ann_status ann_mlp_set_input_norm(ann_mlp *mlp, const float *mean, const float *inv_std);
+/* Host copies of the standardisation (in_dim floats each). */
+ann_status ann_mlp_get_input_norm(const ann_mlp *mlp, float *mean, float *inv_std);
 /* Save the FP32 parameters to a file: the 8 bytes "ANNMLP01", the four sizes
  * (in_dim, hidden1, hidden2, out_dim) as little-endian uint32, then W1, b1,
- * W2, b2, W3, b3 as little-endian FP32 in the row-major layout above. The
- * optimizer state is not saved. ANN_EIO if the file cannot be written. */
+ * W2, b2, W3, b3, mean, inv_std as little-endian FP32 in the row-major layout
+ * above. The optimizer state is not saved. ANN_EIO if the file cannot be
+ * written. */
 ann_status ann_mlp_save(const ann_mlp *mlp, const char *path);
 /* Create an MLP on `device` with room for max_batch rows from a file written
  * by ann_mlp_save (fresh optimizer state). ANN_EIO if the file cannot be read

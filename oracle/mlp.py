@@ -16,7 +16,7 @@ activation gradients) to BF16 before using them, and accumulates in FP64.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import Dict
+from typing import Dict, Optional
 
 import numpy as np
 
@@ -42,21 +42,38 @@ class MLP:
     b2: np.ndarray
     W3: np.ndarray
     b3: np.ndarray
+    # per-dimension input standardisation x' = (x - mean) * inv_std, applied
+    # in FP32 before the BF16 rounding of the queries (None = identity)
+    mean: Optional[np.ndarray] = None
+    inv_std: Optional[np.ndarray] = None
 
     def params(self) -> Dict[str, np.ndarray]:
         return {k: getattr(self, k) for k in LAYERS}
 
     def copy(self) -> "MLP":
-        return MLP(**{k: v.copy() for k, v in self.params().items()})
+        c = MLP(**{k: v.copy() for k, v in self.params().items()})
+        if self.mean is not None:
+            c.mean, c.inv_std = self.mean.copy(), self.inv_std.copy()
+        return c
 
 
 def _q(x, bf16):
     return bf16_round(x).astype(np.float64) if bf16 else np.asarray(x, dtype=np.float64)
 
 
+def standardise(m: MLP, X: np.ndarray) -> np.ndarray:
+    """(x - mean) * inv_std elementwise, each operation rounded to FP32."""
+    X = np.asarray(X, dtype=np.float32)
+    if m.mean is None:
+        return X
+    d = np.subtract(X, np.asarray(m.mean, dtype=np.float32), dtype=np.float32)
+    return np.multiply(d, np.asarray(m.inv_std, dtype=np.float32), dtype=np.float32)
+
+
 def forward(m: MLP, X: np.ndarray, bf16: bool = True) -> Dict[str, np.ndarray]:
-    """h1 = relu(X W1^T + b1), h2 = relu(h1 W2^T + b2), z = h2 W3^T + b3."""
-    Xq = _q(X, bf16)
+    """x' = standardise(x); h1 = relu(x' W1^T + b1), h2 = relu(h1 W2^T + b2),
+    z = h2 W3^T + b3."""
+    Xq = _q(standardise(m, X), bf16)
     a1 = Xq @ _q(m.W1, bf16).T + m.b1.astype(np.float64)
     h1 = np.maximum(a1, 0.0)
     h1q = _q(h1.astype(np.float32), bf16) if bf16 else h1

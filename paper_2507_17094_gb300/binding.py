@@ -28,7 +28,7 @@ EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_inde
            "ann_index_export", "ann_search", "ann_search_host", "ann_search_host_noalloc", "ann_sync",
            "ann_encode", "ann_dir_table", "ann_mlp_create", "ann_mlp_free", "ann_mlp_set_params", "ann_mlp_get",
            "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_train_epochs", "ann_mlp_predict", "ann_mlp_sync",
-           "ann_mlp_save", "ann_mlp_load",
+           "ann_mlp_save", "ann_mlp_load", "ann_mlp_set_input_norm", "ann_mlp_get_input_norm",
            "ann_ghost_index_of", "ann_server_create", "ann_server_submit", "ann_server_poll",
            "ann_server_in_flight", "ann_server_destroy", "ann_last_error")
 
@@ -97,6 +97,8 @@ def lib() -> C.CDLL:
             L.ann_mlp_predict.argtypes = [vp, vp, u32, u32, f32, vp, vp, vp]
             L.ann_mlp_sync.argtypes = [vp, vp]
             L.ann_mlp_save.argtypes = [vp, C.c_char_p]
+            L.ann_mlp_set_input_norm.argtypes = [vp, vp, vp]
+            L.ann_mlp_get_input_norm.argtypes = [vp, vp, vp]
             L.ann_mlp_load.argtypes = [C.c_char_p, C.c_int, u32, C.POINTER(vp)]
             L.ann_mlp_train_epochs.argtypes = [vp, vp, vp, u32, u32, u32, f32, f32, f32, f32, f32, u64, vp, vp]
             L.ann_ghost_index_of.argtypes = [vp, vp, u32, vp, vp]
@@ -306,6 +308,21 @@ class MLP:
         out = [np.empty(shp, dtype=np.float32) for shp in self._shapes()]
         _check(lib().ann_mlp_get(self._h, which, *[_np_ptr(a) for a in out]))
         return out
+
+    def set_input_norm(self, mean=None, inv_std=None):
+        """Standardise queries per dimension on the device: (x - mean) * inv_std."""
+        if mean is None:
+            _check(lib().ann_mlp_set_input_norm(self._h, None, None))
+            return
+        mu = np.ascontiguousarray(mean, dtype=np.float32).reshape(self.dims[0])
+        isd = np.ascontiguousarray(inv_std, dtype=np.float32).reshape(self.dims[0])
+        _check(lib().ann_mlp_set_input_norm(self._h, _np_ptr(mu), _np_ptr(isd)))
+
+    def get_input_norm(self):
+        mu = np.empty(self.dims[0], np.float32)
+        isd = np.empty(self.dims[0], np.float32)
+        _check(lib().ann_mlp_get_input_norm(self._h, _np_ptr(mu), _np_ptr(isd)))
+        return mu, isd
 
     def forward(self, x, stream=None):
         import torch

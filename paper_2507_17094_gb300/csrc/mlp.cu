@@ -328,6 +328,20 @@ __global__ void to_bf16_kernel(const float *__restrict__ x, __nv_bfloat16 *__res
         y[i] = __float2bfloat16_rn(x[i]);
 }
 
+// Queries (rows x d) to the first GEMM's BF16 operand, standardised per
+// dimension on the way: (x - mean) * inv_std, each step rounded in FP32
+// (mean 0 and inv_std 1, the defaults, leave x unchanged).
+__global__ void input_bf16_kernel(const float *__restrict__ x, const float *__restrict__ mean,
+                                  const float *__restrict__ inv_std, __nv_bfloat16 *__restrict__ y, size_t rows,
+                                  uint32_t d)
+{
+    const size_t n = rows * d;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t c = (uint32_t)(i % d);
+        y[i] = __float2bfloat16_rn(__fmul_rn(__fsub_rn(x[i], mean[c]), inv_std[c]));
+    }
+}
+
 // out (C x R) = in (R x C)^T, BF16, 32 x 32 tiles through shared memory
 __global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out,
                                       uint32_t R, uint32_t C)
@@ -529,6 +543,7 @@ struct ann_mlp {
     __nv_bfloat16 *dzb = nullptr, *dzT = nullptr, *da2b = nullptr, *da2T = nullptr, *da1T = nullptr;
     float *z = nullptr, *dh = nullptr, *dm = nullptr, *loss = nullptr, *part = nullptr;
     float *xbat = nullptr, *epoch_loss = nullptr;
+    float *mean = nullptr, *inv_std = nullptr;   // input standardisation (in_dim each)
     uint32_t *ybat = nullptr, *perm = nullptr;
     size_t perm_cap = 0;
     uint32_t train_cap = 0;
@@ -647,7 +662,7 @@ ann_status ensure_train_buffers(ann_mlp *m, uint32_t n)
 ann_status forward(ann_mlp *m, const float *x, uint32_t n, cudaStream_t st, int logits_epi, float *logits,
                    float *part, uint32_t ntiles)
 {
-    to_bf16_kernel<<<grid1d((size_t)n * m->d, m->num_sms), 256, 0, st>>>(x, m->xb, (size_t)n * m->d);
+    input_bf16_kernel<<<grid1d((size_t)n * m->d, m->num_sms), 256, 0, st>>>(x, m->mean, m->inv_std, m->xb, n, m->d);
     ANN_CUDA(cudaGetLastError());
     EpiArgs e{};
     e.err = m->d_error;
@@ -673,7 +688,8 @@ void mlp_free_all(ann_mlp *m)
         for (void *x : p) if (x) cudaFree(x);
     }
     void *q[] = {m->xb, m->xT, m->h1b, m->h1T, m->h2b, m->h2T, m->dzb, m->dzT, m->da2b, m->da2T, m->da1T,
-                 m->z, m->dh, m->dm, m->loss, m->part, m->d_error, m->xbat, m->ybat, m->perm, m->epoch_loss};
+                 m->z, m->dh, m->dm, m->loss, m->part, m->d_error, m->xbat, m->ybat, m->perm, m->epoch_loss,
+                 m->mean, m->inv_std};
     for (void *x : q) if (x) cudaFree(x);
 }
 
@@ -722,6 +738,12 @@ ann_status ann_mlp_create(int device, uint32_t in_dim, uint32_t hidden1, uint32_
     al((void **)&m->loss, 64);
     al((void **)&m->d_error, 64);
     al((void **)&m->epoch_loss, 4096 * 4);
+    al((void **)&m->mean, (size_t)in_dim * 4);
+    al((void **)&m->inv_std, (size_t)in_dim * 4);
+    if (e == cudaSuccess) {
+        const std::vector<float> ones(in_dim, 1.0f);
+        e = cudaMemcpy(m->inv_std, ones.data(), (size_t)in_dim * 4, cudaMemcpyHostToDevice);
+    }
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) {
         mlp_free_all(m);
@@ -794,6 +816,44 @@ ann_status ann_mlp_get(const ann_mlp *m, int which, float *W1, float *b1, float 
     }
     if (prev >= 0) cudaSetDevice(prev);
     return s;
+}
+
+// Per-dimension input standardisation (host arrays of in_dim floats; both
+// NULL restores the identity: mean 0, inv_std 1).
+ann_status ann_mlp_set_input_norm(ann_mlp *m, const float *mean, const float *inv_std)
+{
+    if (!m || (!mean) != (!inv_std)) { set_error("ann_mlp_set_input_norm: bad arguments"); return ANN_EINVAL; }
+    std::vector<float> mu(m->d, 0.0f), is(m->d, 1.0f);
+    if (mean) {
+        for (uint32_t i = 0; i < m->d; ++i) {
+            if (!std::isfinite(mean[i]) || !std::isfinite(inv_std[i])) {
+                set_error("ann_mlp_set_input_norm: non-finite value at %u", i);
+                return ANN_EINVAL;
+            }
+            mu[i] = mean[i];
+            is[i] = inv_std[i];
+        }
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    cudaError_t e = cudaMemcpy(m->mean, mu.data(), (size_t)m->d * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->inv_std, is.data(), (size_t)m->d * 4, cudaMemcpyHostToDevice);
+    if (prev >= 0) cudaSetDevice(prev);
+    return e == cudaSuccess ? ANN_OK : cuda_fail(e, "ann_mlp_set_input_norm");
+}
+
+// Host copies of the input standardisation (in_dim floats each).
+ann_status ann_mlp_get_input_norm(const ann_mlp *m, float *mean, float *inv_std)
+{
+    if (!m || !mean || !inv_std) { set_error("ann_mlp_get_input_norm: NULL argument"); return ANN_EINVAL; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(m->device);
+    cudaError_t e = cudaMemcpy(mean, m->mean, (size_t)m->d * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(inv_std, m->inv_std, (size_t)m->d * 4, cudaMemcpyDeviceToHost);
+    if (prev >= 0) cudaSetDevice(prev);
+    return e == cudaSuccess ? ANN_OK : cuda_fail(e, "ann_mlp_get_input_norm");
 }
 
 // Logits z = MLP(x) (device x: n x in_dim FP32; device logits: n x out_dim).
@@ -1008,7 +1068,8 @@ ann_status ann_mlp_sync(ann_mlp *m, void *stream)
 }
 
 
-// Parameter file: magic, four uint32 sizes, then W1 b1 W2 b2 W3 b3 (FP32);
+// Parameter file: magic, four uint32 sizes, then W1 b1 W2 b2 W3 b3 and the
+// input standardisation (mean, inv_std) as FP32;
 // both hosts this builds for are little-endian, so the bytes go out as they are.
 static const char kMlpMagic[8] = {'A', 'N', 'N', 'M', 'L', 'P', '0', '1'};
 
@@ -1020,6 +1081,8 @@ ann_status ann_mlp_save(const ann_mlp *m, const char *path)
     const uint32_t rows[3] = {m->h1, m->h2, m->out}, cols[3] = {m->d, m->h1, m->h2};
     for (int l = 0; l < 3; ++l) { W[l].resize((size_t)rows[l] * cols[l]); b[l].resize(rows[l]); }
     ann_status s = ann_mlp_get(m, 0, W[0].data(), b[0].data(), W[1].data(), b[1].data(), W[2].data(), b[2].data());
+    std::vector<float> mu(m->d), is(m->d);
+    if (s == ANN_OK) s = ann_mlp_get_input_norm(m, mu.data(), is.data());
     if (s != ANN_OK) return s;
     FILE *f = std::fopen(path, "wb");
     if (!f) { set_error("ann_mlp_save: cannot open %s", path); return ANN_EIO; }
@@ -1027,6 +1090,7 @@ ann_status ann_mlp_save(const ann_mlp *m, const char *path)
     for (int l = 0; l < 3 && ok; ++l)
         ok = std::fwrite(W[l].data(), 4, W[l].size(), f) == W[l].size() &&
              std::fwrite(b[l].data(), 4, b[l].size(), f) == b[l].size();
+    ok = ok && std::fwrite(mu.data(), 4, m->d, f) == m->d && std::fwrite(is.data(), 4, m->d, f) == m->d;
     ok = (std::fclose(f) == 0) && ok;
     if (!ok) { set_error("ann_mlp_save: write to %s failed", path); return ANN_EIO; }
     return ANN_OK;
@@ -1065,11 +1129,14 @@ ann_status ann_mlp_load(const char *path, int device, uint32_t max_batch, ann_ml
         ok = std::fread(W[l].data(), 4, W[l].size(), f) == W[l].size() &&
              std::fread(b[l].data(), 4, b[l].size(), f) == b[l].size();
     }
+    std::vector<float> mu(dims[0]), is(dims[0]);
+    ok = ok && std::fread(mu.data(), 4, dims[0], f) == dims[0] && std::fread(is.data(), 4, dims[0], f) == dims[0];
     std::fclose(f);
     if (!ok) { set_error("ann_mlp_load: %s is too short", path); return ANN_EIO; }
     ann_mlp *m = nullptr;
     ann_status s = ann_mlp_create(device, dims[0], dims[1], dims[2], dims[3], max_batch, &m);
     if (s == ANN_OK) s = ann_mlp_set_params(m, W[0].data(), b[0].data(), W[1].data(), b[1].data(), W[2].data(), b[2].data());
+    if (s == ANN_OK) s = ann_mlp_set_input_norm(m, mu.data(), is.data());
     if (s != ANN_OK) { ann_mlp_free(m); return s; }
     *out = m;
     return ANN_OK;

@@ -46,7 +46,17 @@ class LearnedEntry:
         self.tau = 0.0
         self.losses = None
 
-    def fit(self, train_queries, labels, epochs: int = 5, batch: int = 1024, lr: float = 1e-3, seed: int = 0):
+    def fit(self, train_queries, labels, epochs: int = 5, batch: int = 1024, lr: float = 1e-3, seed: int = 0,
+            standardise: bool = True):
+        """Train on (query, label) pairs. With `standardise`, the network first
+        takes each query dimension to zero mean and unit variance over the
+        training queries (the library applies it on the device)."""
+        if standardise:
+            x = train_queries.detach().cpu().numpy().astype(np.float64)
+            mean = x.mean(axis=0)
+            std = x.std(axis=0)
+            self.mlp.set_input_norm(mean.astype(np.float32),
+                                    (1.0 / np.maximum(std, 1e-6 * max(float(std.max()), 1e-30))).astype(np.float32))
         self.losses = self.mlp.train_epochs(train_queries, labels, batch=batch, epochs=epochs, lr=lr, seed=seed)
         return self.losses
 

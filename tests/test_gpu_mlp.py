@@ -181,11 +181,13 @@ def test_save_load_round_trip(tmp_path):
     import paper_2507_17094_gb300 as A
     m = make_model(64, 128, 128, 256, seed=5)
     g = gpu_mlp(m, 64)
+    rng = np.random.default_rng(7)
+    g.set_input_norm(rng.uniform(-1, 1, 64), rng.uniform(0.5, 2, 64))
     path = str(tmp_path / "mlp.bin")
     g.save(path)
     h = A.MLP.load(path, max_batch=64)
     assert h.dims == (64, 128, 128, 256)
-    for a, b in zip(g.get(0), h.get(0)):
+    for a, b in zip(g.get(0) + list(g.get_input_norm()), h.get(0) + list(h.get_input_norm())):
         assert np.array_equal(a, b)
     X = torch.from_numpy(np.random.default_rng(6).standard_normal((40, 64)).astype(np.float32)).cuda()
     za, zb = g.forward(X), h.forward(X)
@@ -193,3 +195,24 @@ def test_save_load_round_trip(tmp_path):
     assert torch.equal(za, zb)
     g.close()
     h.close()
+
+
+def test_forward_with_input_standardisation():
+    """Queries of magnitude ~50 standardised on the device match the oracle's
+    FP32 standardisation followed by the same BF16 network."""
+    d, h1, h2, out, n = 256, 512, 512, 1024, 200
+    m = make_model(d, h1, h2, out, seed=8)
+    rng = np.random.default_rng(9)
+    m.mean = rng.uniform(20, 80, d).astype(np.float32)
+    m.inv_std = (1.0 / rng.uniform(4, 12, d)).astype(np.float32)
+    X = (m.mean + rng.standard_normal((n, d)) / m.inv_std).astype(np.float32)
+    g = gpu_mlp(m, 256)
+    g.set_input_norm(m.mean, m.inv_std)
+    z = g.forward(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    g.sync()
+    f = M.forward(m, X)
+    scale = np.abs(f["h2q"]) @ np.abs(M.bf16_round(m.W3).astype(np.float64)).T + np.abs(m.b3)
+    err = np.abs(z.cpu().numpy().astype(np.float64) - f["z"])
+    assert (err <= 2.0 ** -7 * scale + 1e-5).all(), float((err / (scale + 1e-12)).max())
+    g.close()

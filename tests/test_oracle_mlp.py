@@ -94,3 +94,33 @@ def test_top_p_and_fallback_probability():
     assert np.array_equal(np.take_along_axis(z, ids.astype(np.int64), 1), vals.numpy())
     assert ids[0, 0] == 5 and ids[0, 1] == 9
     np.testing.assert_allclose(pmax, torch.softmax(torch.tensor(z), 1).max(1).values.numpy(), rtol=1e-12)
+
+
+def test_standardisation_folds_into_the_first_layer():
+    """(x - mean) * inv_std followed by layer 1 is the affine map with
+    columns of W1 scaled by inv_std and b1 shifted by -W1' mean: the two
+    forms agree up to FP32 rounding of the standardised inputs."""
+    rng = np.random.default_rng(11)
+    d, h1, h2, out = 12, 16, 16, 20
+    m = M.MLP(rng.standard_normal((h1, d)).astype(np.float32), rng.standard_normal(h1).astype(np.float32),
+              rng.standard_normal((h2, h1)).astype(np.float32), rng.standard_normal(h2).astype(np.float32),
+              rng.standard_normal((out, h2)).astype(np.float32), rng.standard_normal(out).astype(np.float32))
+    mean = rng.uniform(20, 80, d).astype(np.float32)
+    inv_std = (1.0 / rng.uniform(2, 10, d)).astype(np.float32)
+    X = (mean + rng.standard_normal((30, d)) / inv_std).astype(np.float32)
+    mn = m.copy()
+    mn.mean, mn.inv_std = mean, inv_std
+    W1f = (m.W1.astype(np.float64) * inv_std.astype(np.float64)[None, :])
+    mf = m.copy()
+    mf.W1 = W1f
+    mf.b1 = m.b1.astype(np.float64) - W1f @ mean.astype(np.float64)
+    z_norm = M.forward(mn, X, bf16=False)["z"]
+    Xd = X.astype(np.float64)
+    a1 = Xd @ mf.W1.T + mf.b1
+    h = np.maximum(a1, 0) @ m.W2.astype(np.float64).T + m.b2
+    z_fold = np.maximum(h, 0) @ m.W3.astype(np.float64).T + m.b3
+    np.testing.assert_allclose(z_norm, z_fold, rtol=1e-4, atol=1e-4 * np.abs(z_fold).max())
+    # identity standardisation changes nothing, bit for bit
+    mi = m.copy()
+    mi.mean, mi.inv_std = np.zeros(d, np.float32), np.ones(d, np.float32)
+    assert np.array_equal(M.forward(mi, X)["z"], M.forward(m, X)["z"])
