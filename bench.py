@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "QPS at recall@10>=0.95 on 1 GB300: plain FP32 vs FP16/FP8+learned entry"
 UNIT = "queries/s"
 RECALL_TARGET = 0.95
-SWEEP = (32, 64, 128, 256)
+SWEEP = (16, 32, 64, 128, 256)
 KERNEL_SOURCES = ("paper_2507_17094_gb300/csrc/search.cu", "paper_2507_17094_gb300/csrc/ann_internal.cuh")
 
 
@@ -171,27 +171,37 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ forms
+# Operating point of the method on the 1M x 96 workload (measured sweep over
+# the ghost-stage length 24-64, the DGS discard ratio 0.5-0.75 and the
+# iteration cap itopk + 16 or 2 itopk + 32, at itopk 32): 48 ghost
+# iterations, discard 0.7, cap itopk + 16 is the fastest setting whose
+# recall@10 stays at or above 0.95.
+GHOST_ITERS = 48
+DGS_DISCARD = 0.7
+
+
 def forms_for(spec):
     """Search configurations compared (each swept over itopk)."""
-    base = dict(k=10, search_width=1, dgs_cooldown=0.3, ghost_max_iters=64)
+    base = dict(k=10, search_width=1, dgs_cooldown=0.3, ghost_max_iters=GHOST_ITERS)
     return {
         # the paper's method: ghost staging + DGS, FP32 storage (headline)
-        "paper_fp32": dict(storage=0, entry=1, dgs_discard=0.5, rerank=0, **base),
+        "paper_fp32": dict(storage=0, entry=1, dgs_discard=DGS_DISCARD, rerank=0, **base),
         # the method without its two techniques (CAGRA-style random entry)
         "plain_fp32": dict(storage=0, entry=0, dgs_discard=0.0, rerank=0, **base),
         # low-precision storage with FP32 rerank of the final queue
-        "f16_rerank": dict(storage=1, entry=1, dgs_discard=0.5, rerank=1, **base),
-        "e4m3_rerank": dict(storage=2, entry=1, dgs_discard=0.5, rerank=1, **base),
+        "f16_rerank": dict(storage=1, entry=1, dgs_discard=DGS_DISCARD, rerank=1, **base),
+        "e4m3_rerank": dict(storage=2, entry=1, dgs_discard=DGS_DISCARD, rerank=1, **base),
         # low precision + learned entry: the MLP's top-8 ghost nodes seed a
         # 4-iteration ghost stage (fallback to ghost staging below tau)
-        "f16_learned": dict(storage=1, entry=2, dgs_discard=0.5, rerank=1, ghost_max_iters_given=4, **base),
-        "e4m3_learned": dict(storage=2, entry=2, dgs_discard=0.5, rerank=1, ghost_max_iters_given=4, **base),
+        "f16_learned": dict(storage=1, entry=2, dgs_discard=DGS_DISCARD, rerank=1, ghost_max_iters_given=4, **base),
+        "e4m3_learned": dict(storage=2, entry=2, dgs_discard=DGS_DISCARD, rerank=1, ghost_max_iters_given=4,
+                             **base),
     }
 
 
 def params_for(form: dict, L: int, seed: int) -> dict:
     p = {k: v for k, v in form.items() if k != "storage"}
-    p.update(itopk=L, max_iters=2 * L // form["search_width"] + 32, seed=seed)
+    p.update(itopk=L, max_iters=L // form["search_width"] + 16, seed=seed)
     return p
 
 
@@ -449,13 +459,35 @@ def run_ours(args):
             print(f"[bench] serving: {serving}", file=sys.stderr, flush=True)
 
     # ------------------------------------------------------------ e2e (host buffers)
-    Qh = torch.from_numpy(ds.Q).pin_memory().numpy()
+    # every step copies the queries in from pinned host memory and the
+    # results out: through ann_search_host for the plain forms; for learned
+    # forms the queries go to the device, the MLP picks the seeds there and
+    # the search reads them, and the results come back
+    Qpin = torch.from_numpy(ds.Q).pin_memory()
+    Qh = Qpin.numpy()
     e2e_steps = max(3, min(args.steps, 50))
-    ix.search_host(Qh, **p)
+    if form["entry"] == 2:
+        le = entries[form["storage"]]
+        res_ids = torch.empty((nq, 10), dtype=torch.int32).pin_memory()
+        res_d = torch.empty((nq, 10), dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            Qd.copy_(Qpin, non_blocking=True)
+            seeds, _ = le.seeds(Qd, stream=stream)
+            i_, d_, _ = ix.search(Qd, given=seeds, stream=stream, out=out, **p)
+            res_ids.copy_(i_, non_blocking=True)
+            res_d.copy_(d_, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        e2e_api = "LearnedEntry.seeds + Index.search (ann_mlp_predict + ann_search), pinned host copies"
+    else:
+        def e2e_step():
+            ix.search_host(Qh, **p)
+        e2e_api = "ann_search_host (pinned host buffers)"
+    e2e_step()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ix.search_host(Qh, **p)
+        e2e_step()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e_value = sum_over_ranks(float(nq * e2e_steps), dist, dev) / e2e_s
 
@@ -487,14 +519,16 @@ def run_ours(args):
                 "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
                 "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
-                "kernel": "search_kernel<F32>"}
+                "kernel": f"search_kernel<{('F32', 'F16', 'E4M3')[form['storage']]}>"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Gaussian mixture; no dataset files)",
         "config": {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "nq": nq,
-                   "k": 10, "itopk": L, "search_width": 1, "max_iters": p["max_iters"], "entry": "ghost",
-                   "ghost_n": spec.ghost_n, "dgs_discard": 0.5, "dgs_cooldown": 0.3, "storage": "f32",
+                   "form": headline, "k": 10, "itopk": L, "search_width": 1, "max_iters": p["max_iters"],
+                   "entry": ("random", "ghost", "learned")[form["entry"]], "ghost_n": spec.ghost_n,
+                   "ghost_max_iters": form["ghost_max_iters"], "dgs_discard": form["dgs_discard"],
+                   "dgs_cooldown": form["dgs_cooldown"], "storage": ("f32", "f16", "e4m3")[form["storage"]],
                    "recall_at_10": head_recall, "recall_target": RECALL_TARGET,
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "parallelism": f"replicas x{world}"},
@@ -503,7 +537,7 @@ def run_ours(args):
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nq * spec.d * 4),
                 "d2h_bytes_per_step": int(nq * 10 * 8), "steps": e2e_steps,
-                "api": "ann_search_host (pinned host buffers)"},
+                "api": e2e_api},
         "gpu_launches": args.steps,
         "cpu_baseline": cpu_baseline,
         "serving": serving,
@@ -567,8 +601,10 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
             "config": {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree,
-                       "nq": sample, "k": 10, "itopk": chosen, "search_width": 1, "max_iters": p["max_iters"],
-                       "entry": "ghost", "dgs_discard": 0.5, "storage": "f32", "recall_at_10": rec_at},
+                       "nq": sample, "form": "paper_fp32", "k": 10, "itopk": chosen, "search_width": 1,
+                       "max_iters": p["max_iters"], "entry": "ghost", "ghost_n": spec.ghost_n,
+                       "ghost_max_iters": form["ghost_max_iters"], "dgs_discard": form["dgs_discard"],
+                       "dgs_cooldown": form["dgs_cooldown"], "storage": "f32", "recall_at_10": rec_at},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{sample} queries per step of the {spec.nq}-query workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -18,6 +18,17 @@
 // error word and gives up instead of spinning forever.
 #define ANN_WAIT_LIMIT_CYCLES (2000000000ll)
 
+// Per-warp visited tables in global memory, one table of 2^bits uint32
+// entries per resident-warp slot, plus each slot's current generation.
+// An entry is (generation << idbits) | id; entries of older generations count
+// as empty, so starting a new query's set is one increment, and the table is
+// zeroed only when the generation counter wraps.
+struct ann_visited_pool {
+    uint32_t *tab = nullptr;     // slots x 2^bits
+    uint32_t *gen = nullptr;     // slots
+    uint32_t slots = 0, bits = 0, idbits = 0;
+};
+
 struct ann_index {
     int device = 0;
     int storage = ANN_F32;
@@ -42,6 +53,10 @@ struct ann_index {
     size_t ws_bytes = 0;
     int num_sms = 0;
     size_t smem_optin = 0;
+    ann_visited_pool visited;          // visited tables of ann_search launches
+    cudaEvent_t busy = nullptr;        // completes when this index's last search does
+    cudaStream_t busy_stream = nullptr;
+    bool busy_set = false;
 };
 
 namespace ann {
@@ -84,15 +99,27 @@ struct ServeRing {
     uint32_t cap, kmax, per_warp;
 };
 
+// Visited tables for `slots` warps over ids < n (n < 2^31), 2^bits entries
+// each; zeroed. visited_pool_free releases them.
+ann_status visited_pool_alloc(ann_visited_pool &vp, uint32_t slots, uint32_t bits, uint64_t n);
+void visited_pool_free(ann_visited_pool &vp);
+// Warp slots that one launch of the search or serve kernel can occupy.
+uint32_t max_warp_slots(const ann_index *ix);
+constexpr uint32_t kVisitedBits = 12;   // 4,096 entries (16 KB) per warp
+
 // Validate `p` against the index and derive the per-query parameters.
 ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint32_t n_given, QParams *out);
 
 // A serve-kernel launch plan sized for the largest parameters `maxp`
 // (opaque; free with serve_plan_free).
-ann_status serve_plan(ann_index *ix, const ann_search_params *maxp, uint32_t n_given_max, void **plan);
+// The plan owns visited tables for `n_streams` concurrent launches.
+ann_status serve_plan(ann_index *ix, const ann_search_params *maxp, uint32_t n_given_max, uint32_t n_streams,
+                      void **plan);
 void serve_plan_free(void *plan);
-// Launch a serve kernel with capacity for at least `queries` queries.
-ann_status serve_launch(void *plan, const ServeRing &ring, uint32_t queries, cudaStream_t stream);
+// Launch a serve kernel with capacity for at least `queries` queries on
+// `stream`, the plan's concurrent-launch slot `stream_index`.
+ann_status serve_launch(void *plan, const ServeRing &ring, uint32_t queries, cudaStream_t stream,
+                        uint32_t stream_index);
 
 // The search launch (search.cu) with caller-chosen device scratch: the work
 // counter (zeroed on `stream` before the launch) and the error word.

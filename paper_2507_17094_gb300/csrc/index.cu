@@ -17,6 +17,36 @@
 
 namespace ann {
 
+ann_status visited_pool_alloc(ann_visited_pool &vp, uint32_t slots, uint32_t bits, uint64_t n)
+{
+    uint32_t idbits = 1;
+    while (idbits < 31 && (1ull << idbits) < n) ++idbits;
+    vp.slots = slots;
+    vp.bits = bits;
+    vp.idbits = idbits;
+    const size_t tab_bytes = ((size_t)slots << bits) * sizeof(uint32_t);
+    cudaError_t e = cudaMalloc(&vp.tab, tab_bytes);
+    if (e == cudaSuccess) e = cudaMemset(vp.tab, 0, tab_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&vp.gen, (size_t)slots * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(vp.gen, 0, (size_t)slots * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        visited_pool_free(vp);
+        return cuda_fail(e, "visited tables");
+    }
+    return ANN_OK;
+}
+
+void visited_pool_free(ann_visited_pool &vp)
+{
+    if (vp.tab) cudaFree(vp.tab);
+    if (vp.gen) cudaFree(vp.gen);
+    vp = ann_visited_pool{};
+}
+
+// The search and serve kernels run 4 warps per block and at most 7 blocks
+// per SM (their launch bounds).
+uint32_t max_warp_slots(const ann_index *ix) { return (uint32_t)ix->num_sms * 7u * 4u; }
+
 static thread_local char g_err[512] = "";
 
 void set_error(const char *fmt, ...)
@@ -271,10 +301,15 @@ ann_status ann_index_free(ann_index *ix)
 {
     if (!ix) return ANN_OK;
     DeviceGuard g(ix->device);
+    if (ix->busy) {
+        cudaEventSynchronize(ix->busy);
+        cudaEventDestroy(ix->busy);
+    }
     void *ptrs[] = {ix->codes, ix->scales, ix->graph, ix->dir, ix->ghost_ids, ix->ghost_codes,
                     ix->ghost_scales, ix->ghost_graph, ix->d_counter, ix->d_error, ix->ws};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    visited_pool_free(ix->visited);
     if (ix->x32 && (void *)ix->x32 != ix->codes) cudaFree(ix->x32);
     delete ix;
     return ANN_OK;
@@ -291,9 +326,9 @@ ann_status ann_index_create(int device, ann_storage storage, uint64_t n, uint32_
         set_error("ann_index_create: unknown storage %d", (int)storage);
         return ANN_EINVAL;
     }
-    if (!vectors || !graph || n == 0 || n >= ANN_INVALID_ID || dim == 0 || dim > ANN_MAX_DIM || degree == 0 ||
+    if (!vectors || !graph || n == 0 || n >= (1ull << 31) || dim == 0 || dim > ANN_MAX_DIM || degree == 0 ||
         degree > ANN_MAX_DEGREE) {
-        set_error("ann_index_create: need n in [1, 2^32-1), dim in [1, %u], degree in [1, %u]", ANN_MAX_DIM,
+        set_error("ann_index_create: need n in [1, 2^31), dim in [1, %u], degree in [1, %u]", ANN_MAX_DIM,
                   ANN_MAX_DEGREE);
         return ANN_EINVAL;
     }
@@ -352,6 +387,9 @@ ann_status ann_index_create(int device, ann_storage storage, uint64_t n, uint32_
     ANN_TRY(cudaMalloc(&ix->d_counter, 64));
     ANN_TRY(cudaMalloc(&ix->d_error, 64));
     ANN_TRY(cudaMemset(ix->d_error, 0, 64));
+    ANN_TRY(cudaEventCreateWithFlags(&ix->busy, cudaEventDisableTiming));
+    if (ann_status vs = visited_pool_alloc(ix->visited, max_warp_slots(ix), kVisitedBits, n); vs != ANN_OK)
+        return fail(vs);
 
     // vectors: upload in chunks of FP32 rows, encode into the padded layout
     {

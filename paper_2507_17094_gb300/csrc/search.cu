@@ -5,10 +5,12 @@
 //   - persistent CTAs of 4 warps; each warp owns one query at a time and pulls
 //     the next query index from a device counter, so long and short searches
 //     balance across the 152 SMs;
-//   - per warp, a small shared-memory region (about 14 KB for itopk 64) holds
-//     the query, the priority queue, the candidate list, the parents'
-//     adjacency / direction / vector rows, 16 staged rows and the visited
-//     table, so 16 warps share an SM and hide each other's memory latency;
+//   - per warp, a small shared-memory region (about 9.5 KB for itopk 32 on
+//     96-d FP32) holds the query, the priority queue, the candidate list, the
+//     parents' adjacency / direction / vector rows and 16 staged rows, so 24
+//     warps share an SM and hide each other's memory latency;
+//   - the visited set of each warp is a 4,096-entry table in global memory
+//     (L2-resident, 16 KB per warp), probed with one atomicMax per lane;
 //   - every random global read (adjacency rows, direction rows, vector rows,
 //     FP32 rerank rows) is a 1-D TMA bulk copy into shared memory completing
 //     on the warp's mbarrier: one instruction per row, all rows of a round in
@@ -26,12 +28,20 @@
 //     candidates plus its insertion point in the queue, and only queue
 //     entries behind the first insertion point move.
 //
-// Visited set: the table is exact between resets. It is cleared (and refilled
-// with the queue's ids) only when it would pass half full. Forgetting a node
-// that is no longer in the queue cannot change the result: its key is larger
-// than the queue's current l-th key (which only decreases), so re-evaluating
-// it rejects it again. Results therefore equal those of an exact visited set;
-// only the work counters can grow (counted in hash_resets).
+// Visited set: open addressing with linear probing over entries
+// (generation << idbits) | id. Entries of older generations are empty, so a
+// new query (or the switch from the ghost to the base graph) only increments
+// the warp's generation. Insertion is atomicMax along the probe sequence: an
+// entry only ever grows within a generation, a smaller current entry is
+// displaced and carried on to the next slot, so every id sits behind a run of
+// larger current entries from its home slot and a lookup finds it; the first
+// slot whose entry is smaller than the id (or empty) proves it absent.
+// The table is exact between resets. It is reset (and refilled with the
+// queue's ids) only when it would pass half full. Forgetting a node that is no
+// longer in the queue cannot change the result: its key is larger than the
+// queue's current l-th key (which only decreases), so re-evaluating it rejects
+// it again. Results therefore equal those of an exact visited set; only the
+// work counters can grow (counted in hash_resets).
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -58,7 +68,7 @@ struct View {
 };
 
 struct Layout {  // byte offsets inside one warp's shared-memory region
-    uint32_t q, bd, bi, bs, cd, ci, cs, adj, dir, prow, pqb, par, stage, hash, bar, qp, total;
+    uint32_t q, bd, bi, bs, cd, ci, cs, adj, dir, prow, pqb, par, stage, bar, qp, total;
 };
 
 struct Args {
@@ -76,7 +86,11 @@ struct Args {
     uint32_t *counter;
     int *err;
     Layout lay;
-    uint32_t cap_cand, hash_bits, stage_rows, stage_stride, prow_bytes;
+    uint32_t cap_cand, stage_rows, stage_stride, prow_bytes;
+    // visited tables: slot_base + warp slot selects one table of 2^vbits
+    // entries; generations run 1..vgmax
+    uint32_t *vtab, *vgen;
+    uint32_t vbits, vstride_bits, idbits, vgmax, slot_base;
 };
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
@@ -189,8 +203,13 @@ struct WarpSearch {
     bool failed = false;
     uint64_t qid = 0;
     ann_query_stats st;
+    uint32_t *vt;        // this warp's visited table
+    uint32_t *vgen_at;   // its generation word
+    uint32_t vg;         // current generation
 
-    __device__ WarpSearch(const Args &args, uint8_t *b) : a(args), base(b), lane(threadIdx.x & 31) {}
+    __device__ WarpSearch(const Args &args, uint8_t *b, uint32_t slot)
+        : a(args), base(b), lane(threadIdx.x & 31), vt(args.vtab + ((size_t)slot << args.vstride_bits)),
+          vgen_at(args.vgen + slot), vg(__ldcg(args.vgen + slot)) {}
 
     // shared-memory arrays of this warp
     __device__ __forceinline__ float *q() const { return reinterpret_cast<float *>(base + a.lay.q); }
@@ -206,30 +225,46 @@ struct WarpSearch {
     __device__ __forceinline__ uint32_t *pqb() const { return reinterpret_cast<uint32_t *>(base + a.lay.pqb); }
     __device__ __forceinline__ uint32_t *par() const { return reinterpret_cast<uint32_t *>(base + a.lay.par); }
     __device__ __forceinline__ uint8_t *stage() const { return base + a.lay.stage; }
-    __device__ __forceinline__ uint32_t *hash() const { return reinterpret_cast<uint32_t *>(base + a.lay.hash); }
     __device__ __forceinline__ uint64_t *bar() const { return reinterpret_cast<uint64_t *>(base + a.lay.bar); }
 
     // ---------------------------------------------------------- visited set
-    __device__ bool hash_insert(uint32_t v)
+    __device__ __forceinline__ uint32_t hash_home(uint32_t v) const { return (v * 2654435761u) >> (32 - a.vbits); }
+
+    // The rest of a test-and-insert whose first probe (at slot s, entry cur
+    // = this generation's tag | id) returned old: true if the id was new.
+    __device__ bool hash_finish(uint32_t s, uint32_t cur, uint32_t old)
     {
-        uint32_t *h = hash();
-        const uint32_t mask = (1u << a.hash_bits) - 1;
-        uint32_t s = (v * 2654435761u) >> (32 - a.hash_bits);
+        const uint32_t tag = vg << a.idbits;
+        const uint32_t mask = (1u << a.vbits) - 1;
         for (uint32_t probe = 0; probe <= mask; ++probe) {
-            const uint32_t old = atomicCAS(&h[s], kEmpty, v);
-            if (old == kEmpty) return true;
-            if (old == v) return false;
+            if (old == cur) return false;         // only the id itself can be found: entries are unique
+            if (old < tag) return true;           // an empty slot took cur
+            if (old < cur) cur = old;             // cur took the slot; carry the displaced entry on
             s = (s + 1) & mask;
+            old = atomicMax(vt + s, cur);
         }
         return true;  // unreachable: the table is never more than half full
     }
 
+    // Test-and-insert: true if v was not in the set (and is now).
+    __device__ bool hash_insert(uint32_t v)
+    {
+        const uint32_t s = hash_home(v), cur = (vg << a.idbits) | v;
+        return hash_finish(s, cur, atomicMax(vt + s, cur));
+    }
+
+    // Start an empty set: the next generation (zeroing the table when the
+    // generation counter wraps).
     __device__ void hash_clear()
     {
-        uint32_t *h = hash();
-        const uint32_t H = 1u << a.hash_bits;
-        for (uint32_t i = lane; i < H; i += 32) h[i] = kEmpty;
+        if (++vg > a.vgmax) {
+            const uint32_t H = 1u << a.vbits;
+            for (uint32_t i = lane; i < H; i += 32) vt[i] = 0;
+            __threadfence();
+            vg = 1;
+        }
         __syncwarp();
+        if (lane == 0) *vgen_at = vg;
         hash_count = 0;
     }
 
@@ -246,7 +281,7 @@ struct WarpSearch {
 
     __device__ __forceinline__ void hash_make_room(uint32_t incoming)
     {
-        if (hash_count + incoming > (1u << (a.hash_bits - 1))) hash_reset();
+        if (hash_count + incoming > (1u << (a.vbits - 1))) hash_reset();
     }
 
     // ------------------------------------------------ bulk copies + waiting
@@ -383,6 +418,46 @@ struct WarpSearch {
         }
         cnt = min(lcap, cnt + nc);
         __syncwarp();
+    }
+
+    // Collect the kept neighbours of parent pi in slots lane + 32 (r0 + r),
+    // r < NW (bit r0 + r of km), that are new to the visited set. The first
+    // probes of a lane's NW slots are issued before any result is examined,
+    // so their latencies overlap. Returns the warp's new candidate count.
+    template <uint32_t NW>
+    __device__ uint32_t collect_row_nw(const View &v, uint32_t pi, uint32_t km, uint32_t r0, uint32_t nc)
+    {
+        uint32_t nb[NW], hs[NW], cur[NW], old[NW];
+        bool ok[NW];
+#pragma unroll
+        for (uint32_t r = 0; r < NW; ++r) {
+            const uint32_t j = lane + 32 * (r0 + r);
+            nb[r] = j < v.deg ? adj()[pi * v.deg_pad + j] : ANN_INVALID_ID;
+            ok[r] = nb[r] != ANN_INVALID_ID && ((km >> (r0 + r)) & 1u);
+        }
+#pragma unroll
+        for (uint32_t r = 0; r < NW; ++r) {
+            if (ok[r]) {
+                hs[r] = hash_home(nb[r]);
+                cur[r] = (vg << a.idbits) | nb[r];
+                old[r] = atomicMax(vt + hs[r], cur[r]);
+            }
+        }
+#pragma unroll
+        for (uint32_t r = 0; r < NW; ++r) {
+            const bool isnew = ok[r] && hash_finish(hs[r], cur[r], old[r]);
+            const uint32_t m = __ballot_sync(0xffffffffu, isnew);
+            if (isnew) ci()[nc + __popc(m & lanemask_lt())] = nb[r];
+            nc += __popc(m);
+        }
+        return nc;
+    }
+
+    __device__ uint32_t collect_row(const View &v, uint32_t pi, uint32_t km, uint32_t nc)
+    {
+        if (v.deg <= 32) return collect_row_nw<1>(v, pi, km, 0, nc);
+        for (uint32_t r0 = 0; r0 * 32 < v.deg; r0 += 2) nc = collect_row_nw<2>(v, pi, km, r0, nc);
+        return nc;
     }
 
     // Collect a lane's id into the candidate list if it is new to the
@@ -598,15 +673,7 @@ struct WarpSearch {
             }
             hash_make_room(np * deg);
             uint32_t nc = 0;
-            for (uint32_t pi = 0; pi < np; ++pi) {
-                const uint32_t km = dgs_now ? keep[pi] : 0xffffffffu;
-                for (uint32_t r = 0; r * 32 < deg; ++r) {
-                    const uint32_t j = lane + 32 * r;
-                    uint32_t nb = ANN_INVALID_ID;
-                    if (j < deg) nb = adj()[pi * v.deg_pad + j];
-                    nc = collect(j < deg && nb != ANN_INVALID_ID && ((km >> r) & 1u), nb, nc);
-                }
-            }
+            for (uint32_t pi = 0; pi < np; ++pi) nc = collect_row(v, pi, dgs_now ? keep[pi] : 0xffffffffu, nc);
             __syncwarp();
             hash_count += nc;
             if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
@@ -714,7 +781,7 @@ __global__ void __launch_bounds__(128, 7) search_kernel(const Args a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSearch<ST> ws(a, smem + (size_t)warp * a.lay.total);
+    WarpSearch<ST> ws(a, smem + (size_t)warp * a.lay.total, a.slot_base + blockIdx.x * (blockDim.x >> 5) + warp);
     if (lane == 0) mbar_init(ws.bar(), 1);
     fence_mbar_init();
     __syncwarp();
@@ -745,7 +812,7 @@ __global__ void __launch_bounds__(128, 7) serve_kernel(const Args a, const Serve
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *base = smem + (size_t)warp * a.lay.total;
-    WarpSearch<ST> ws(a, base);
+    WarpSearch<ST> ws(a, base, a.slot_base + blockIdx.x * (blockDim.x >> 5) + warp);
     QParams *qp = reinterpret_cast<QParams *>(base + a.lay.qp);
     if (lane == 0) mbar_init(ws.bar(), 1);
     fence_mbar_init();
@@ -790,8 +857,7 @@ __global__ void __launch_bounds__(128, 7) serve_kernel(const Args a, const Serve
 uint32_t align16(uint32_t x) { return (x + 15) & ~15u; }
 
 Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, uint32_t W, uint32_t adj_words,
-                   uint32_t dir_words, uint32_t prow_bytes, uint32_t stage_rows, uint32_t stage_stride,
-                   uint32_t hash_bits)
+                   uint32_t dir_words, uint32_t prow_bytes, uint32_t stage_rows, uint32_t stage_stride)
 {
     Layout L{};
     uint32_t o = 0;
@@ -813,18 +879,10 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
     L.pqb = take(W * w * 4);
     L.par = take(W * 4);
     L.stage = take(stage_rows * stage_stride);
-    L.hash = take((1u << hash_bits) * 4);
     L.bar = take(16);
     L.qp = take(96);
     L.total = align16(o);
     return L;
-}
-
-uint32_t bits_for(uint32_t x)
-{
-    uint32_t b = 0;
-    while ((1u << b) < x) ++b;
-    return b;
 }
 
 template <int ST>
@@ -948,35 +1006,29 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     const uint32_t stage_bytes = std::max(ix->row_bytes, q.rerank ? a.row32_bytes : 0u);
     a.stage_stride = smem_row_stride(stage_bytes);
     a.stage_rows = (uint32_t)std::min(32, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
-    // visited table: at least twice (queue + one iteration's candidates);
-    // beyond that as large as still fits the target number of warps per SM
-    // (28 by default, measured best of 16-32 on the 1M x 96 workload; up to
-    // 4096 entries), so resets stay rare
-    const uint32_t need = 2 * (cap_buf + cap_cand);
-    const uint32_t hb_min = std::max(8u, bits_for(need));
-    uint32_t hb = hb_min;
-    const int target_warps = std::min(32, std::max(4, env_int("ANN_WARPS_PER_SM", 28)));
-    const size_t sm_bytes = ix->smem_optin + 1024;                   // shared memory of one SM
-    const size_t warp_budget = (sm_bytes - (size_t)(target_warps / 4) * 1024) / target_warps;
-    while (hb < 12) {
-        const Layout t = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W, adj_words, dir_words, a.prow_bytes,
-                                     a.stage_rows, a.stage_stride, hb + 1);
-        if (t.total > warp_budget) break;
-        ++hb;
+    // visited tables: the queue plus one iteration's candidates must fit in
+    // half a table (the reset threshold)
+    if (cap_buf + cap_cand > (1u << (kVisitedBits - 1))) {
+        set_error("ann_search: queue (%u) + candidates (%u) exceed the visited table", cap_buf, cap_cand);
+        return ANN_EINVAL;
     }
-    if (const int v = env_int("ANN_HASH_BITS", 0); v > 0 && (uint32_t)v >= hb_min) hb = (uint32_t)v;
+    a.vtab = ix->visited.tab;
+    a.vgen = ix->visited.gen;
+    a.vstride_bits = ix->visited.bits;
+    a.vbits = ix->visited.bits;   // 4,096 entries: measured faster than 2,048 or 1,024 (L2-resident either way)
+    a.idbits = ix->visited.idbits;
+    a.vgmax = (uint32_t)((1ull << (32 - ix->visited.idbits)) - 1);
+    a.slot_base = 0;
     warps = 4;
     Layout lay{};
     for (;;) {
         lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W, adj_words, dir_words, a.prow_bytes,
-                          a.stage_rows, a.stage_stride, hb);
+                          a.stage_rows, a.stage_stride);
         if ((size_t)lay.total * warps <= ix->smem_optin) break;
         if (warps > 1) { warps /= 2; continue; }
-        if (hb > hb_min) { --hb; continue; }
         set_error("ann_search: per-query state (%u bytes) exceeds shared memory", lay.total);
         return ANN_EINVAL;
     }
-    a.hash_bits = hb;
     a.lay = lay;
     smem = (size_t)lay.total * warps;
     switch (ix->storage) {
@@ -995,6 +1047,8 @@ struct ServePlanImpl {
     Args a;
     int warps, nb, num_sms, storage;
     size_t smem;
+    ann_visited_pool visited;     // the plan's own tables: n_streams launches at once
+    uint32_t slots_per_launch;
 };
 
 template <int ST>
@@ -1037,6 +1091,9 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
     a.err = err;
     const uint64_t want = ((uint64_t)nq + warps - 1) / warps;
     const int blocks = (int)std::min<uint64_t>(want, (uint64_t)nb * ix->num_sms);
+    // one search of this index at a time: its visited tables (and work
+    // counter) are shared, so a launch on another stream waits for the last
+    if (ix->busy_set && ix->busy_stream != stream) ANN_CUDA(cudaStreamWaitEvent(stream, ix->busy, 0));
     ANN_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream));
     cudaError_t e;
     switch (ix->storage) {
@@ -1045,17 +1102,27 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
     default: e = launch<ANN_E4M3>(a, warps, blocks, smem, stream); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "search_kernel launch");
+    ANN_CUDA(cudaEventRecord(ix->busy, stream));
+    ix->busy_stream = stream;
+    ix->busy_set = true;
     return ANN_OK;
 }
 
-ann_status serve_plan(ann_index *ix, const ann_search_params *maxp, uint32_t n_given_max, void **plan)
+ann_status serve_plan(ann_index *ix, const ann_search_params *maxp, uint32_t n_given_max, uint32_t n_streams,
+                      void **plan)
 {
     QParams q;
     ann_status s = derive_qparams(ix, maxp, n_given_max, &q);
     if (s != ANN_OK) return s;
     ServePlanImpl *pl = new ServePlanImpl();
     s = plan_args(ix, q, pl->a, pl->warps, pl->smem, pl->nb);
+    if (s == ANN_OK) {
+        pl->slots_per_launch = (uint32_t)(pl->nb * ix->num_sms * pl->warps);
+        s = visited_pool_alloc(pl->visited, pl->slots_per_launch * std::max(1u, n_streams), kVisitedBits, ix->n);
+    }
     if (s != ANN_OK) { delete pl; return s; }
+    pl->a.vtab = pl->visited.tab;
+    pl->a.vgen = pl->visited.gen;
     pl->a.counter = ix->d_counter;
     pl->a.err = ix->d_error;
     pl->num_sms = ix->num_sms;
@@ -1064,11 +1131,19 @@ ann_status serve_plan(ann_index *ix, const ann_search_params *maxp, uint32_t n_g
     return ANN_OK;
 }
 
-void serve_plan_free(void *plan) { delete static_cast<ServePlanImpl *>(plan); }
-
-ann_status serve_launch(void *plan, const ServeRing &ring, uint32_t queries, cudaStream_t stream)
+void serve_plan_free(void *plan)
 {
-    const ServePlanImpl &pl = *static_cast<const ServePlanImpl *>(plan);
+    ServePlanImpl *pl = static_cast<ServePlanImpl *>(plan);
+    if (!pl) return;
+    visited_pool_free(pl->visited);
+    delete pl;
+}
+
+ann_status serve_launch(void *plan, const ServeRing &ring, uint32_t queries, cudaStream_t stream,
+                        uint32_t stream_index)
+{
+    ServePlanImpl &pl = *static_cast<ServePlanImpl *>(plan);
+    pl.a.slot_base = stream_index * pl.slots_per_launch;
     const uint64_t per_block = (uint64_t)pl.warps * ring.per_warp;
     const uint64_t want = ((uint64_t)queries + per_block - 1) / per_block;
     const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)pl.nb * pl.num_sms));

@@ -144,7 +144,8 @@ ann_status ann_server_create(ann_index *ix, const ann_server_config *cfg, ann_ml
     s->kmax = mp.k;
     s->per_warp = cfg->queries_per_warp ? cfg->queries_per_warp : 4;
     s->maxp = mp;
-    ann_status st = serve_plan(ix, &mp, s->P ? s->P : 1, &s->plan);
+    const uint32_t ns = cfg->streams ? cfg->streams : 4;
+    ann_status st = serve_plan(ix, &mp, s->P ? s->P : 1, ns, &s->plan);
     cudaError_t e = cudaSuccess;
     auto al = [&](void **p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
     if (st == ANN_OK) {
@@ -163,7 +164,6 @@ ann_status ann_server_create(ann_index *ix, const ann_server_config *cfg, ann_ml
         int lo = 0, hi = 0;
         if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->ingest, cudaStreamNonBlocking, hi);
-        const uint32_t ns = cfg->streams ? cfg->streams : 4;
         for (uint32_t i = 0; i < ns && e == cudaSuccess; ++i) {
             cudaStream_t c;
             e = cudaStreamCreateWithPriority(&c, cudaStreamNonBlocking, lo);
@@ -248,7 +248,8 @@ ann_status ann_server_submit(ann_server *s, uint64_t req_id, const float *querie
         if (e == cudaSuccess) e = cudaEventRecord(s->ev[ri], in);
     }
     if (st == ANN_OK && e == cudaSuccess) {
-        cudaStream_t c = s->compute[s->next_stream++ % s->compute.size()];
+        const uint32_t si = (uint32_t)(s->next_stream++ % s->compute.size());
+        cudaStream_t c = s->compute[si];
         e = cudaStreamWaitEvent(c, s->ev[ri], 0);
         if (e == cudaSuccess) {
             ServeRing r{};
@@ -265,7 +266,7 @@ ann_status ann_server_submit(ann_server *s, uint64_t req_id, const float *querie
             r.cap = s->cap;
             r.kmax = s->kmax;
             r.per_warp = s->per_warp;
-            st = serve_launch(s->plan, r, nq, c);
+            st = serve_launch(s->plan, r, nq, c, si);
         }
     }
     if (st == ANN_OK && e != cudaSuccess) st = cuda_fail(e, "ann_server_submit");
