@@ -8,8 +8,8 @@
  *
  * Everything here is written to be read against the paper, not to be fast:
  * plain loops, qsort for every sort, a bitmap for the visited set, FP32
- * distances summed in index order with one fused multiply-add per element,
- * and FP64 for the exact ground truth.
+ * distances with one fused multiply-add per element into four interleaved
+ * partial sums (dist_f32), and FP64 for the exact ground truth.
  *
  * Parts and the passages they follow:
  *   - exact kNN ground truth ............ Section 2.1, Eq. 1 (squared L2)
@@ -319,12 +319,14 @@ static int entry_cmp(const void *a, const void *b)
     return (x->id < y->id) ? -1 : (x->id > y->id);
 }
 
-/* Eq. 2, squared: FP32, elements in index order, one fma per element. */
+/* Eq. 2, squared, in FP32. The paper fixes no summation order; this one
+ * keeps four partial sums, element i going to sum i mod 4 (one fma each, in
+ * index order), and returns (s0 + s1) + (s2 + s3). */
 static float dist_f32(const float *q, const float *x, uint32_t d)
 {
-    float acc = 0.0f;
-    for (uint32_t i = 0; i < d; ++i) { float df = q[i] - x[i]; acc = fmaf(df, df, acc); }
-    return acc;
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (uint32_t i = 0; i < d; ++i) { float df = q[i] - x[i]; s[i & 3] = fmaf(df, df, s[i & 3]); }
+    return (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 static int bit_get(const uint8_t *bm, uint64_t i) { return (bm[i >> 3] >> (i & 7)) & 1; }

@@ -15,9 +15,9 @@
 //     FP32 rerank rows) is a 1-D TMA bulk copy into shared memory completing
 //     on the warp's mbarrier: one instruction per row, all rows of a round in
 //     flight together;
-//   - distances are computed lane-per-row from shared memory, elements in
-//     index order with one fused multiply-add each, so they equal the FP32
-//     reference definition bit for bit;
+//   - distances are computed lane-per-row from shared memory, one fused
+//     multiply-add per element into four interleaved partial sums, the same
+//     FP32 operations as the reference definition, so they agree bit for bit;
 //   - DGS needs the query's sign bits relative to each parent; they are
 //     recomputed from the parent's row, which arrives in the same bulk-copy
 //     round as its adjacency and direction rows (one ballot per 32 dims);
@@ -120,25 +120,34 @@ __device__ __forceinline__ void step(float qv, float xv, float &acc)
     acc = __fmaf_rn(df, df, acc);
 }
 
-// Squared L2 between a staged row and the query (both in shared memory),
-// elements in index order.
+// Stored value of element i (decoded to FP32).
+template <int ST>
+__device__ __forceinline__ float stored_elem(const uint8_t *row, uint32_t i, float scale)
+{
+    if (ST == ANN_F32) return reinterpret_cast<const float *>(row)[i];
+    if (ST == ANN_F16) return __fmul_rn(scale, __half2float(reinterpret_cast<const __half *>(row)[i]));
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[i], __NV_E4M3);
+    return __fmul_rn(scale, __half2float(__half(h)));
+}
+
+// Squared L2 between a staged row and the query (both in shared memory):
+// element i is fused into partial sum i mod 4 (in index order) and the result
+// is (s0 + s1) + (s2 + s3), so the dependent FMA chain is d/4 long.
 template <int ST>
 __device__ __forceinline__ float row_dist(const uint8_t *row, const float *q, float scale, uint32_t d)
 {
-    float acc = 0.0f;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    uint32_t i = 0;
     if (ST == ANN_F32) {
-        uint32_t i = 0;
         for (; i + 4 <= d; i += 4) {
             const float4 x = *reinterpret_cast<const float4 *>(row + (size_t)i * 4);
             const float4 y = *reinterpret_cast<const float4 *>(q + i);
-            step(y.x, x.x, acc);
-            step(y.y, x.y, acc);
-            step(y.z, x.z, acc);
-            step(y.w, x.w, acc);
+            step(y.x, x.x, s0);
+            step(y.y, x.y, s1);
+            step(y.z, x.z, s2);
+            step(y.w, x.w, s3);
         }
-        for (; i < d; ++i) step(q[i], reinterpret_cast<const float *>(row)[i], acc);
     } else if (ST == ANN_F16) {
-        uint32_t i = 0;
         for (; i + 8 <= d; i += 8) {
             const uint4 raw = *reinterpret_cast<const uint4 *>(row + (size_t)i * 2);
             const float4 y0 = *reinterpret_cast<const float4 *>(q + i);
@@ -147,19 +156,16 @@ __device__ __forceinline__ float row_dist(const uint8_t *row, const float *q, fl
             const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
             const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
             const float2 f3 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
-            step(y0.x, __fmul_rn(scale, f0.x), acc);
-            step(y0.y, __fmul_rn(scale, f0.y), acc);
-            step(y0.z, __fmul_rn(scale, f1.x), acc);
-            step(y0.w, __fmul_rn(scale, f1.y), acc);
-            step(y1.x, __fmul_rn(scale, f2.x), acc);
-            step(y1.y, __fmul_rn(scale, f2.y), acc);
-            step(y1.z, __fmul_rn(scale, f3.x), acc);
-            step(y1.w, __fmul_rn(scale, f3.y), acc);
+            step(y0.x, __fmul_rn(scale, f0.x), s0);
+            step(y0.y, __fmul_rn(scale, f0.y), s1);
+            step(y0.z, __fmul_rn(scale, f1.x), s2);
+            step(y0.w, __fmul_rn(scale, f1.y), s3);
+            step(y1.x, __fmul_rn(scale, f2.x), s0);
+            step(y1.y, __fmul_rn(scale, f2.y), s1);
+            step(y1.z, __fmul_rn(scale, f3.x), s2);
+            step(y1.w, __fmul_rn(scale, f3.y), s3);
         }
-        for (; i < d; ++i)
-            step(q[i], __fmul_rn(scale, __half2float(reinterpret_cast<const __half *>(row)[i])), acc);
     } else {
-        uint32_t i = 0;
         for (; i + 16 <= d; i += 16) {
             const uint4 raw = *reinterpret_cast<const uint4 *>(row + i);
             const uint32_t wds[4] = {raw.x, raw.y, raw.z, raw.w};
@@ -170,29 +176,23 @@ __device__ __forceinline__ float row_dist(const uint8_t *row, const float *q, fl
                 const float2 a = __half22float2(__half2(lo));
                 const float2 b = __half22float2(__half2(hi));
                 const float4 y = *reinterpret_cast<const float4 *>(q + i + 4 * e);
-                step(y.x, __fmul_rn(scale, a.x), acc);
-                step(y.y, __fmul_rn(scale, a.y), acc);
-                step(y.z, __fmul_rn(scale, b.x), acc);
-                step(y.w, __fmul_rn(scale, b.y), acc);
+                step(y.x, __fmul_rn(scale, a.x), s0);
+                step(y.y, __fmul_rn(scale, a.y), s1);
+                step(y.z, __fmul_rn(scale, b.x), s2);
+                step(y.w, __fmul_rn(scale, b.y), s3);
             }
         }
-        for (; i < d; ++i) {
-            const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[i], __NV_E4M3);
-            step(q[i], __fmul_rn(scale, __half2float(__half(h))), acc);
-        }
     }
-    return acc;
+    // tail (d not a multiple of the vector width); i is a multiple of 4 here
+    for (; i < d; i += 4) {
+        step(q[i], stored_elem<ST>(row, i, scale), s0);
+        if (i + 1 < d) step(q[i + 1], stored_elem<ST>(row, i + 1, scale), s1);
+        if (i + 2 < d) step(q[i + 2], stored_elem<ST>(row, i + 2, scale), s2);
+        if (i + 3 < d) step(q[i + 3], stored_elem<ST>(row, i + 3, scale), s3);
+    }
+    return __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3));
 }
 
-// Stored value of element i (for the parent's sign bits).
-template <int ST>
-__device__ __forceinline__ float stored_elem(const uint8_t *row, uint32_t i, float scale)
-{
-    if (ST == ANN_F32) return reinterpret_cast<const float *>(row)[i];
-    if (ST == ANN_F16) return __fmul_rn(scale, __half2float(reinterpret_cast<const __half *>(row)[i]));
-    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)row[i], __NV_E4M3);
-    return __fmul_rn(scale, __half2float(__half(h)));
-}
 
 template <int ST>
 struct WarpSearch {

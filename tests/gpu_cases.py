@@ -12,8 +12,9 @@ import numpy as np
 import oracle as O
 from workloads import CONFIGS, build_graph, ghost_sample, make_queries
 
-# Distances are FP32 on both sides, summed in index order with one fused
-# multiply-add per element, so the expected agreement is exact. The bar the
+# Distances are FP32 on both sides, one fused multiply-add per element into
+# four interleaved partial sums combined pairwise, so the expected agreement
+# is exact. The bar the
 # method sets is looser: ids equal except at distance ties within 1e-5
 # relative, distances within 1e-5 relative.
 DIST_RTOL = 1e-5
