@@ -124,37 +124,101 @@ __device__ __forceinline__ bool better(float va, uint32_t ia, float vb, uint32_t
 }
 
 // ------------------------------------------------------------------ GEMM
-// Persistent and warp-specialised: one CTA per SM walks the output tiles
-// (tile = blockIdx.x + i * gridDim.x, row-block-major so neighbouring CTAs
-// share A tiles in L2). Warp 0 streams A/B tiles with TMA into the stage ring,
-// warp 1 issues the MMAs into one of two tensor-memory accumulators, warps
-// 2-5 run the epilogue of the previous tile from the other accumulator, so
+// Persistent and warp-specialised: CTA b walks the contiguous tile range
+// [b * per, (b + 1) * per) in row-block-major order (per = ceil(tiles /
+// grid)), so a CTA stays on one row block for many consecutive column tiles.
+// Warp 0 streams A/B tiles with TMA into the stage ring, warp 1 issues the
+// MMAs into one of two tensor-memory accumulators, warps 2-9 run the
+// epilogue of the previous tile from the other accumulator (two warps per
+// 32-lane quarter of the accumulator, one per half of the columns), so
 // loads, MMAs and epilogues of consecutive tiles overlap.
-constexpr int GEMM_THREADS = 192;
+constexpr int EPI_WARPS = 8;
+constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 
+// Per-thread state of the fused top-P epilogue: the TOPP best (logit,
+// column) pairs and the online-softmax (max, sum) of the columns seen.
+struct TopP {
+    float tv[TOPP];
+    uint32_t ti[TOPP];
+    float mx, sm;
+    __device__ void reset()
+    {
+#pragma unroll
+        for (int p = 0; p < TOPP; ++p) { tv[p] = -INFINITY; ti[p] = 0xFFFFFFFFu; }
+        mx = -INFINITY;
+        sm = 0.0f;
+    }
+};
+
+// One 32-column chunk of a row (accumulator values v) for columns nb..nb+31.
+// Rows m >= M take part in the warp's collectives with no effect.
 template <int EPI>
 __device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m, uint32_t M, uint32_t nb, uint32_t N,
-                                               const EpiArgs &e, float (&tv)[TOPP], uint32_t (&ti)[TOPP], float &mx,
-                                               float &sm)
+                                               const EpiArgs &e, TopP &tp)
 {
-    if (m >= M) return;
+    const bool full = nb + 32 <= N;
+    float bias[32];
+    if (EPI != EPI_F32) {
+        if (full) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                const float4 b4 = __ldg(reinterpret_cast<const float4 *>(e.bias + nb + j));
+                bias[j] = b4.x; bias[j + 1] = b4.y; bias[j + 2] = b4.z; bias[j + 3] = b4.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) bias[j] = nb + j < N ? __ldg(e.bias + nb + j) : 0.0f;
+        }
+    }
     if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
+        if (m >= M) return;
         float *out = e.c + (size_t)m * e.ldc + nb;
+        if (full && (e.ldc % 4) == 0) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (nb + j < N) out[j] = v[j] + (EPI == EPI_BIAS_F32 ? e.bias[nb + j] : 0.0f);
+            for (int j = 0; j < 32; j += 4) {
+                float4 o;
+                o.x = v[j] + (EPI == EPI_BIAS_F32 ? bias[j] : 0.0f);
+                o.y = v[j + 1] + (EPI == EPI_BIAS_F32 ? bias[j + 1] : 0.0f);
+                o.z = v[j + 2] + (EPI == EPI_BIAS_F32 ? bias[j + 2] : 0.0f);
+                o.w = v[j + 3] + (EPI == EPI_BIAS_F32 ? bias[j + 3] : 0.0f);
+                *reinterpret_cast<float4 *>(out + j) = o;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (nb + j < N) out[j] = v[j] + (EPI == EPI_BIAS_F32 ? bias[j] : 0.0f);
+        }
     } else if (EPI == EPI_BIAS_RELU_BF16) {
+        if (m >= M) return;
         __nv_bfloat16 *out = e.cb + (size_t)m * e.ldc + nb;
+        if (full && (e.ldc % 8) == 0) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (nb + j < N) out[j] = __float2bfloat16_rn(fmaxf(v[j] + e.bias[nb + j], 0.0f));
+            for (int j = 0; j < 32; j += 8) {
+                uint4 o;
+                __nv_bfloat162 h[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    h[k] = __floats2bfloat162_rn(fmaxf(v[j + 2 * k] + bias[j + 2 * k], 0.0f),
+                                                 fmaxf(v[j + 2 * k + 1] + bias[j + 2 * k + 1], 0.0f));
+                o.x = *reinterpret_cast<uint32_t *>(&h[0]);
+                o.y = *reinterpret_cast<uint32_t *>(&h[1]);
+                o.z = *reinterpret_cast<uint32_t *>(&h[2]);
+                o.w = *reinterpret_cast<uint32_t *>(&h[3]);
+                *reinterpret_cast<uint4 *>(out + j) = o;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (nb + j < N) out[j] = __float2bfloat16_rn(fmaxf(v[j] + bias[j], 0.0f));
+        }
     } else {
-        // logits of the chunk, their max and exp-sum by trees (no serial
-        // chain), one online-softmax combine, then top-P insertion behind a
-        // threshold test
+        // logits of the chunk; their max and exp-sum by trees, one
+        // online-softmax combine; insertion into the top-P only where some
+        // lane of the warp has a logit above its current P-th (columns
+        // arrive in increasing order, so a tie never enters)
         float x[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) x[j] = (nb + j < N) ? v[j] + e.bias[nb + j] : -INFINITY;
+        for (int j = 0; j < 32; ++j) x[j] = (m < M && nb + j < N) ? v[j] + bias[j] : -INFINITY;
         float t[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) t[j] = fmaxf(x[j], x[j + 16]);
@@ -171,28 +235,43 @@ __device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m,
 #pragma unroll
                 for (int j = 0; j < w; ++j) t[j] += t[j + w];
             const float cs = t[0];
-            if (cm > mx) {
-                sm = sm * __expf(mx - cm) + cs;
-                mx = cm;
+            if (cm > tp.mx) {
+                tp.sm = tp.sm * __expf(tp.mx - cm) + cs;
+                tp.mx = cm;
             } else {
-                sm += cs * __expf(cm - mx);
+                tp.sm += cs * __expf(cm - tp.mx);
             }
         }
+        if (__any_sync(0xffffffffu, cm > tp.tv[TOPP - 1])) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const uint32_t n = nb + j;
-            if (n >= N || !better(x[j], n, tv[TOPP - 1], ti[TOPP - 1])) continue;
-            tv[TOPP - 1] = x[j];
-            ti[TOPP - 1] = n;
+            for (int j = 0; j < 32; ++j) {
+                if (!(x[j] > tp.tv[TOPP - 1])) continue;
+                tp.tv[TOPP - 1] = x[j];
+                tp.ti[TOPP - 1] = nb + j;
 #pragma unroll
-            for (int p = TOPP - 1; p > 0; --p) {
-                if (better(tv[p], ti[p], tv[p - 1], ti[p - 1])) {
-                    const float tt = tv[p]; tv[p] = tv[p - 1]; tv[p - 1] = tt;
-                    const uint32_t u = ti[p]; ti[p] = ti[p - 1]; ti[p - 1] = u;
+                for (int p = TOPP - 1; p > 0; --p) {
+                    if (better(tp.tv[p], tp.ti[p], tp.tv[p - 1], tp.ti[p - 1])) {
+                        const float tt = tp.tv[p]; tp.tv[p] = tp.tv[p - 1]; tp.tv[p - 1] = tt;
+                        const uint32_t u = tp.ti[p]; tp.ti[p] = tp.ti[p - 1]; tp.ti[p - 1] = u;
+                    }
                 }
             }
         }
     }
+}
+
+// Top-P partial record of (row m, CTA segment slot): TOPP logits, TOPP
+// columns, max, exp-sum.
+__device__ __forceinline__ void topp_flush(const EpiArgs &e, const TopP &tp, uint32_t m, uint32_t slot)
+{
+    float *o = e.part + ((size_t)m * e.ntiles + slot) * (2 * TOPP + 2);
+#pragma unroll
+    for (int p = 0; p < TOPP; ++p) {
+        o[p] = tp.tv[p];
+        o[TOPP + p] = __uint_as_float(tp.ti[p]);
+    }
+    o[2 * TOPP] = tp.mx;
+    o[2 * TOPP + 1] = tp.sm;
 }
 
 template <int EPI>
@@ -214,6 +293,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const uint32_t nkb = (K + BK - 1) / BK;
     const uint32_t n_tiles = (N + BN - 1) / BN, m_tiles = (M + BM - 1) / BM;
     const uint32_t tiles = n_tiles * m_tiles;
+    const uint32_t per = (tiles + gridDim.x - 1) / gridDim.x;
+    const uint32_t t_begin = min(tiles, blockIdx.x * per), t_end = min(tiles, t_begin + per);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -222,7 +303,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);
+            mbar_init(&acc_empty[b], EPI_WARPS);
         }
         fence_mbar_init();
     }
@@ -241,7 +322,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            for (uint32_t t = t_begin; t < t_end && ok; ++t) {
                 const uint32_t m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
                 for (uint32_t kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
@@ -257,7 +338,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             constexpr uint32_t idesc = idesc_bf16(BM, BN);
             uint32_t it = 0, tc = 0;
             bool ok = true;
-            for (uint32_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tc) {
+            for (uint32_t t = t_begin; t < t_end && ok; ++t, ++tc) {
                 const uint32_t buf = tc & 1, use = tc >> 1;
                 if (!(ok = mbar_wait_bounded(&acc_empty[buf], (use & 1) ^ 1, e.err))) break;
                 tc_fence_after();
@@ -276,41 +357,42 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             }
         }
     } else {
-        // epilogue warps 2..5: warp w reads accumulator lanes 32 * (w % 4) ..
-        const uint32_t q = warp & 3;
-        uint32_t tc = 0;
-        for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x, ++tc) {
+        // epilogue warps 2..9: warp w reads accumulator lanes 32 * (w % 4) ..
+        // + 31 (its quarter) and columns 64 * h .. + 63 of each tile
+        const uint32_t q = warp & 3, h = (warp - 2) >> 2;
+        uint32_t tc = 0, cur_m = 0xFFFFFFFFu;
+        TopP tp;
+        tp.reset();
+        for (uint32_t t = t_begin; t < t_end; ++t, ++tc) {
             const uint32_t buf = tc & 1, use = tc >> 1;
             const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[buf], use & 1, e.err));
             if (!ok) break;
             tc_fence_after();
-            const uint32_t m0 = (t / n_tiles) * BM, n0 = (t % n_tiles) * BN;
-            const uint32_t m = m0 + q * 32 + lane;
-            float tv[TOPP];
-            uint32_t ti[TOPP];
-            float mx = -INFINITY, sm = 0.0f;
-#pragma unroll
-            for (int p = 0; p < TOPP; ++p) { tv[p] = -INFINITY; ti[p] = 0xFFFFFFFFu; }
+            const uint32_t mb = t / n_tiles, n0 = (t % n_tiles) * BN;
+            const uint32_t m = mb * BM + q * 32 + lane;
+            if (EPI == EPI_TOPP && mb != cur_m) {
+                // a new row block: the previous one's partial is complete
+                if (cur_m != 0xFFFFFFFFu) {
+                    const uint32_t pm = cur_m * BM + q * 32 + lane;
+                    if (pm < M) topp_flush(e, tp, pm, (blockIdx.x - (cur_m * n_tiles) / per) * 2 + h);
+                }
+                tp.reset();
+                cur_m = mb;
+            }
 #pragma unroll 1
-            for (uint32_t c0 = 0; c0 < BN; c0 += 32) {
+            for (uint32_t c0 = h * (BN / 2); c0 < (h + 1) * (BN / 2); c0 += 32) {
                 float v[32];
                 __syncwarp();
                 tmem_ld32(tmem + buf * BN + ((q * 32u) << 16) + c0, v);
-                epilogue_chunk<EPI>(v, m, M, n0 + c0, N, e, tv, ti, mx, sm);
+                epilogue_chunk<EPI>(v, m, M, n0 + c0, N, e, tp);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
-            if (EPI == EPI_TOPP && m < M) {
-                float *o = e.part + ((size_t)m * e.ntiles + (t % n_tiles)) * (2 * TOPP + 2);
-#pragma unroll
-                for (int p = 0; p < TOPP; ++p) {
-                    o[p] = tv[p];
-                    o[TOPP + p] = __uint_as_float(ti[p]);
-                }
-                o[2 * TOPP] = mx;
-                o[2 * TOPP + 1] = sm;
-            }
+        }
+        if (EPI == EPI_TOPP && cur_m != 0xFFFFFFFFu) {
+            const uint32_t pm = cur_m * BM + q * 32 + lane;
+            if (pm < M) topp_flush(e, tp, pm, (blockIdx.x - (cur_m * n_tiles) / per) * 2 + h);
         }
     }
     tc_fence_before();
@@ -591,6 +673,25 @@ ann_status make_map(CUtensorMap *map, const void *ptr, uint32_t rows, uint32_t K
     return ANN_OK;
 }
 
+// One persistent CTA per SM (fewer if there are fewer tiles).
+uint32_t gemm_grid(uint32_t M, uint32_t N, uint32_t sms)
+{
+    const uint32_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+    return std::max(1u, std::min(tiles, sms));
+}
+
+// Top-P partial slots per row: two column halves times the largest number
+// of CTAs whose contiguous tile ranges meet one row block.
+uint32_t topp_slots(uint32_t M, uint32_t N, uint32_t sms)
+{
+    const uint32_t n_tiles = (N + BN - 1) / BN, m_tiles = (M + BM - 1) / BM;
+    const uint32_t tiles = n_tiles * m_tiles, per = (tiles + gemm_grid(M, N, sms) - 1) / gemm_grid(M, N, sms);
+    uint32_t smax = 1;
+    for (uint32_t mb = 0; mb < m_tiles; ++mb)
+        smax = std::max(smax, ((mb + 1) * n_tiles - 1) / per - (mb * n_tiles) / per + 1);
+    return 2 * smax;
+}
+
 template <int EPI>
 ann_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, uint32_t M, uint32_t N, uint32_t K, EpiArgs e,
                 cudaStream_t st)
@@ -612,8 +713,7 @@ ann_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, uint32_t M, uint
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint32_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-    gemm_kernel<EPI><<<std::min<uint32_t>(tiles, (uint32_t)sms), GEMM_THREADS, GEMM_SMEM, st>>>(ta, tb, M, N, K, e);
+    gemm_kernel<EPI><<<gemm_grid(M, N, (uint32_t)sms), GEMM_THREADS, GEMM_SMEM, st>>>(ta, tb, M, N, K, e);
     ANN_CUDA(cudaGetLastError());
     return ANN_OK;
 }
@@ -963,9 +1063,9 @@ ann_status ann_mlp_predict(ann_mlp *m, const float *x, uint32_t n, uint32_t P, f
     cudaSetDevice(m->device);
     cudaStream_t st = (cudaStream_t)stream;
     ann_status s = ANN_OK;
-    const uint32_t ntiles = (m->out + BN - 1) / BN;
     for (uint32_t r0 = 0; r0 < n && s == ANN_OK; r0 += m->maxb) {
         const uint32_t rows = std::min(m->maxb, n - r0);
+        const uint32_t ntiles = topp_slots(rows, m->out, (uint32_t)m->num_sms);
         const size_t need = (size_t)rows * ntiles * (2 * TOPP + 2) * 4;
         if (need > m->part_cap) {
             if (m->part) cudaFree(m->part);
@@ -975,7 +1075,10 @@ ann_status ann_mlp_predict(ann_mlp *m, const float *x, uint32_t n, uint32_t P, f
             if (e != cudaSuccess) { s = cuda_fail(e, "ann_mlp_predict"); break; }
             m->part_cap = need;
         }
-        s = forward(m, x + (size_t)r0 * m->d, rows, st, EPI_TOPP, nullptr, m->part, ntiles);
+        // slots no CTA writes read as empty (ids 0xFFFFFFFF, exp-sum NaN)
+        if (cudaError_t me = cudaMemsetAsync(m->part, 0xFF, need, st); me != cudaSuccess)
+            s = cuda_fail(me, "ann_mlp_predict");
+        if (s == ANN_OK) s = forward(m, x + (size_t)r0 * m->d, rows, st, EPI_TOPP, nullptr, m->part, ntiles);
         if (s == ANN_OK) {
             topp_merge_kernel<<<(rows + 3) / 4, 128, 0, st>>>(m->part, rows, ntiles, P, tau, seeds + (size_t)r0 * P,
                                                                pmax ? pmax + r0 : nullptr);
