@@ -23,16 +23,14 @@ def ghost_labels(index: Index, queries, seed: int, ghost_itopk: int = 64, ghost_
     return index.ghost_index_of(ids[:, 0].contiguous(), stream=stream)
 
 
-def choose_tau(pmax: np.ndarray, hit: np.ndarray, target: float = 0.97) -> float:
-    """Smallest confidence threshold above which the predicted seeds contain
-    the label for at least `target` of the validation queries (0 if all do)."""
-    order = np.argsort(-pmax)
-    hits = np.cumsum(hit[order]) / np.arange(1, len(order) + 1)
-    ok = np.nonzero(hits >= target)[0]
-    if len(ok) == 0:
-        return float(pmax.max()) + 1.0
-    last = ok.max()
-    return 0.0 if last == len(order) - 1 else float(pmax[order][last])
+def choose_tau(pmax: np.ndarray, fallback: float = 0.05) -> float:
+    """Confidence threshold: the `fallback` quantile of the validation
+    queries' top softmax probabilities, so that fraction of in-distribution
+    queries (and any query the network is less sure of) falls back to plain
+    ghost staging."""
+    if len(pmax) == 0 or fallback <= 0.0:
+        return 0.0
+    return float(np.quantile(np.asarray(pmax, dtype=np.float64), min(fallback, 1.0), method="lower"))
 
 
 class LearnedEntry:
@@ -60,10 +58,12 @@ class LearnedEntry:
         self.losses = self.mlp.train_epochs(train_queries, labels, batch=batch, epochs=epochs, lr=lr, seed=seed)
         return self.losses
 
-    def calibrate(self, val_queries, val_labels, target: float = 0.97):
+    def calibrate(self, val_queries, val_labels, fallback: float = 0.05):
+        """Set tau from a validation split (see choose_tau); returns tau and
+        the fraction of validation queries whose label is among the P seeds."""
         seeds, pmax = self.mlp.predict(val_queries, P=self.P, tau=0.0)
         hit = (seeds == val_labels[:, None]).any(dim=1).cpu().numpy()
-        self.tau = choose_tau(pmax.cpu().numpy(), hit, target)
+        self.tau = choose_tau(pmax.cpu().numpy(), fallback)
         return self.tau, float(hit.mean())
 
     def seeds(self, queries, stream=None):
