@@ -71,6 +71,10 @@ struct Layout {  // byte offsets inside one warp's shared-memory region
     uint32_t q, bd, bi, bs, cd, ci, cs, adj, dir, prow, pqb, par, stage, bar, qp, total;
 };
 
+// Ghost sets up to this many nodes get an exact shared-memory bitmap as the
+// ghost stage's visited set (2 KB per warp at most).
+constexpr uint32_t kGhostBitmapMax = 16384;
+
 struct Args {
     View base, ghost;
     const uint32_t *ghost_ids;
@@ -91,6 +95,7 @@ struct Args {
     // entries; generations run 1..vgmax
     uint32_t *vtab, *vgen;
     uint32_t vbits, vstride_bits, idbits, vgmax, slot_base;
+    uint32_t gbm_words;   // > 0: the ghost stage's visited set is a bitmap of this many words
 };
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
@@ -130,69 +135,58 @@ __device__ __forceinline__ float stored_elem(const uint8_t *row, uint32_t i, flo
     return __fmul_rn(scale, __half2float(__half(h)));
 }
 
-// Squared L2 between a staged row and the query (both in shared memory):
-// element i is fused into partial sum i mod 4 (in index order) and the result
-// is (s0 + s1) + (s2 + s3), so the dependent FMA chain is d/4 long.
+// Half of the squared L2 between a staged row and the query (both in
+// shared memory). The distance keeps four partial sums, element i (in index
+// order) fused into sum i mod 4, and is (s0 + s1) + (s2 + s3); half h of the
+// lane pair of a row computes s_{2h} + s_{2h+1}, so one more add of the two
+// halves gives the distance and each lane does half the elements.
 template <int ST>
-__device__ __forceinline__ float row_dist(const uint8_t *row, const float *q, float scale, uint32_t d)
+__device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *q, float scale, uint32_t d,
+                                               uint32_t h)
 {
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    float sa = 0.0f, sb = 0.0f;  // s_{2h}, s_{2h+1}
     uint32_t i = 0;
     if (ST == ANN_F32) {
         for (; i + 4 <= d; i += 4) {
-            const float4 x = *reinterpret_cast<const float4 *>(row + (size_t)i * 4);
-            const float4 y = *reinterpret_cast<const float4 *>(q + i);
-            step(y.x, x.x, s0);
-            step(y.y, x.y, s1);
-            step(y.z, x.z, s2);
-            step(y.w, x.w, s3);
+            const float2 x = *reinterpret_cast<const float2 *>(row + (size_t)(i + 2 * h) * 4);
+            const float2 y = *reinterpret_cast<const float2 *>(q + i + 2 * h);
+            step(y.x, x.x, sa);
+            step(y.y, x.y, sb);
         }
     } else if (ST == ANN_F16) {
         for (; i + 8 <= d; i += 8) {
-            const uint4 raw = *reinterpret_cast<const uint4 *>(row + (size_t)i * 2);
-            const float4 y0 = *reinterpret_cast<const float4 *>(q + i);
-            const float4 y1 = *reinterpret_cast<const float4 *>(q + i + 4);
-            const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
-            const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
-            const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.z));
-            const float2 f3 = __half22float2(*reinterpret_cast<const __half2 *>(&raw.w));
-            step(y0.x, __fmul_rn(scale, f0.x), s0);
-            step(y0.y, __fmul_rn(scale, f0.y), s1);
-            step(y0.z, __fmul_rn(scale, f1.x), s2);
-            step(y0.w, __fmul_rn(scale, f1.y), s3);
-            step(y1.x, __fmul_rn(scale, f2.x), s0);
-            step(y1.y, __fmul_rn(scale, f2.y), s1);
-            step(y1.z, __fmul_rn(scale, f3.x), s2);
-            step(y1.w, __fmul_rn(scale, f3.y), s3);
+#pragma unroll
+            for (uint32_t g = 0; g < 2; ++g) {
+                const uint32_t e = i + 4 * g + 2 * h;
+                const __half2 hv = *reinterpret_cast<const __half2 *>(row + (size_t)e * 2);
+                const float2 f = __half22float2(hv);
+                const float2 y = *reinterpret_cast<const float2 *>(q + e);
+                step(y.x, __fmul_rn(scale, f.x), sa);
+                step(y.y, __fmul_rn(scale, f.y), sb);
+            }
         }
     } else {
         for (; i + 16 <= d; i += 16) {
             const uint4 raw = *reinterpret_cast<const uint4 *>(row + i);
             const uint32_t wds[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wds[e] & 0xffffu), __NV_E4M3);
-                const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(wds[e] >> 16), __NV_E4M3);
-                const float2 a = __half22float2(__half2(lo));
-                const float2 b = __half22float2(__half2(hi));
-                const float4 y = *reinterpret_cast<const float4 *>(q + i + 4 * e);
-                step(y.x, __fmul_rn(scale, a.x), s0);
-                step(y.y, __fmul_rn(scale, a.y), s1);
-                step(y.z, __fmul_rn(scale, b.x), s2);
-                step(y.w, __fmul_rn(scale, b.y), s3);
+            for (uint32_t g = 0; g < 4; ++g) {
+                const __half2_raw pr =
+                    __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((wds[g] >> (16 * h)) & 0xffffu), __NV_E4M3);
+                const float2 f = __half22float2(__half2(pr));
+                const float2 y = *reinterpret_cast<const float2 *>(q + i + 4 * g + 2 * h);
+                step(y.x, __fmul_rn(scale, f.x), sa);
+                step(y.y, __fmul_rn(scale, f.y), sb);
             }
         }
     }
     // tail (d not a multiple of the vector width); i is a multiple of 4 here
     for (; i < d; i += 4) {
-        step(q[i], stored_elem<ST>(row, i, scale), s0);
-        if (i + 1 < d) step(q[i + 1], stored_elem<ST>(row, i + 1, scale), s1);
-        if (i + 2 < d) step(q[i + 2], stored_elem<ST>(row, i + 2, scale), s2);
-        if (i + 3 < d) step(q[i + 3], stored_elem<ST>(row, i + 3, scale), s3);
+        if (i + 2 * h < d) step(q[i + 2 * h], stored_elem<ST>(row, i + 2 * h, scale), sa);
+        if (i + 2 * h + 1 < d) step(q[i + 2 * h + 1], stored_elem<ST>(row, i + 2 * h + 1, scale), sb);
     }
-    return __fadd_rn(__fadd_rn(s0, s1), __fadd_rn(s2, s3));
+    return __fadd_rn(sa, sb);
 }
-
 
 template <int ST>
 struct WarpSearch {
@@ -206,6 +200,7 @@ struct WarpSearch {
     uint32_t *vt;        // this warp's visited table
     uint32_t *vgen_at;   // its generation word
     uint32_t vg;         // current generation
+    bool gbm = false;    // the visited set is the ghost bitmap (ghost stage, small ghost sets)
 
     __device__ WarpSearch(const Args &args, uint8_t *b, uint32_t slot)
         : a(args), base(b), lane(threadIdx.x & 31), vt(args.vtab + ((size_t)slot << args.vstride_bits)),
@@ -246,9 +241,15 @@ struct WarpSearch {
         return true;  // unreachable: the table is never more than half full
     }
 
+    __device__ __forceinline__ uint32_t *gbits() const { return reinterpret_cast<uint32_t *>(base + a.lay.dir); }
+
     // Test-and-insert: true if v was not in the set (and is now).
     __device__ bool hash_insert(uint32_t v)
     {
+        if (gbm) {
+            const uint32_t bit = 1u << (v & 31);
+            return (atomicOr(gbits() + (v >> 5), bit) & bit) == 0;
+        }
         const uint32_t s = hash_home(v), cur = (vg << a.idbits) | v;
         return hash_finish(s, cur, atomicMax(vt + s, cur));
     }
@@ -257,6 +258,12 @@ struct WarpSearch {
     // generation counter wraps).
     __device__ void hash_clear()
     {
+        if (gbm) {
+            for (uint32_t i = lane; i < a.gbm_words; i += 32) gbits()[i] = 0;
+            __syncwarp();
+            hash_count = 0;
+            return;
+        }
         if (++vg > a.vgmax) {
             const uint32_t H = 1u << a.vbits;
             for (uint32_t i = lane; i < H; i += 32) vt[i] = 0;
@@ -281,7 +288,7 @@ struct WarpSearch {
 
     __device__ __forceinline__ void hash_make_room(uint32_t incoming)
     {
-        if (hash_count + incoming > (1u << (a.vbits - 1))) hash_reset();
+        if (!gbm && hash_count + incoming > (1u << (a.vbits - 1))) hash_reset();
     }
 
     // ------------------------------------------------ bulk copies + waiting
@@ -300,8 +307,8 @@ struct WarpSearch {
     }
 
     // ----------------------------------------------------- evaluate rows
-    // Distances of rows ids[0, n) of `codes` into out[0, n), stage_rows rows
-    // per bulk-copy round.
+    // Distances of rows ids[0, n) of `codes` into out[0, n), stage_rows
+    // (<= 16) rows per bulk-copy round; lanes 2r and 2r + 1 compute row r.
     template <int RST>
     __device__ bool evaluate(const uint8_t *codes, const float *scales, uint32_t row_bytes, const uint32_t *ids,
                              uint32_t n, float *out)
@@ -321,7 +328,12 @@ struct WarpSearch {
                 if (RST != ANN_F32) scale = __ldg(scales + v);
             }
             if (!wait_copies()) return false;
-            if (lane < rows) out[b0 + lane] = row_dist<RST>(stage() + lane * a.stage_stride, q(), scale, a.d);
+            const uint32_t r = lane >> 1;
+            const float rs = __shfl_sync(0xffffffffu, scale, r);
+            float part = 0.0f;
+            if (r < rows) part = row_dist_half<RST>(stage() + r * a.stage_stride, q(), rs, a.d, lane & 1);
+            const float other = __shfl_xor_sync(0xffffffffu, part, 1);
+            if (r < rows && (lane & 1) == 0) out[b0 + r] = __fadd_rn(part, other);
             __syncwarp();
         }
         return true;
@@ -455,6 +467,14 @@ struct WarpSearch {
 
     __device__ uint32_t collect_row(const View &v, uint32_t pi, uint32_t km, uint32_t nc)
     {
+        if (gbm) {
+            for (uint32_t r = 0; r * 32 < v.deg; ++r) {
+                const uint32_t j = lane + 32 * r;
+                const uint32_t nb = j < v.deg ? adj()[pi * v.deg_pad + j] : ANN_INVALID_ID;
+                nc = collect(nb != ANN_INVALID_ID && ((km >> r) & 1u), nb, nc);
+            }
+            return nc;
+        }
         if (v.deg <= 32) return collect_row_nw<1>(v, pi, km, 0, nc);
         for (uint32_t r0 = 0; r0 * 32 < v.deg; r0 += 2) nc = collect_row_nw<2>(v, pi, km, r0, nc);
         return nc;
@@ -698,6 +718,7 @@ struct WarpSearch {
         // uses, and L1 is not kept coherent with those copies
         for (uint32_t i = lane; i < dpad; i += 32) q()[i] = i < a.d ? __ldcg(qg + i) : 0.0f;
         __syncwarp();
+        gbm = qp.entry != ANN_ENTRY_RANDOM && a.gbm_words > 0;
         hash_clear();
         bool ok = true;
         if (qp.entry == ANN_ENTRY_RANDOM) {
@@ -729,6 +750,7 @@ struct WarpSearch {
                 }
                 __syncwarp();
                 cnt = g;
+                gbm = false;   // the base stage's visited set is the global table
                 hash_clear();
                 for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi()[i]);
                 __syncwarp();
@@ -857,7 +879,8 @@ __global__ void __launch_bounds__(128, 7) serve_kernel(const Args a, const Serve
 uint32_t align16(uint32_t x) { return (x + 15) & ~15u; }
 
 Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, uint32_t W, uint32_t adj_words,
-                   uint32_t dir_words, uint32_t prow_bytes, uint32_t stage_rows, uint32_t stage_stride)
+                   uint32_t dir_words, uint32_t prow_bytes, uint32_t stage_rows, uint32_t stage_stride,
+                   uint32_t gbm_words, bool serve)
 {
     Layout L{};
     uint32_t o = 0;
@@ -874,13 +897,16 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
     L.ci = take(cap_cand * 4);
     L.cs = take(cap_cand * 4);
     L.adj = take(adj_words * 4);
-    L.dir = take(dir_words * 4);
-    L.prow = take(dir_words ? W * prow_bytes : 0);
+    // the base stage's direction and parent rows share their space with the
+    // ghost stage's visited bitmap (the two stages never overlap)
+    const uint32_t dir_part = align16(dir_words * 4) + align16(dir_words ? W * prow_bytes : 0);
+    L.dir = take(std::max(dir_part, gbm_words * 4));
+    L.prow = L.dir + align16(dir_words * 4);
     L.pqb = take(W * w * 4);
     L.par = take(W * 4);
     L.stage = take(stage_rows * stage_stride);
     L.bar = take(16);
-    L.qp = take(96);
+    L.qp = take(serve ? 96 : 0);
     L.total = align16(o);
     return L;
 }
@@ -981,7 +1007,7 @@ namespace planning {
 
 // Kernel arguments and launch shape for parameters q (the largest a launch
 // must serve): shared-memory layout per warp, warps per block, blocks per SM.
-ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_t &smem, int &nb)
+ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_t &smem, int &nb, bool serve)
 {
     const uint32_t deg = ix->degree;
     a.base = View{(const uint8_t *)ix->codes, ix->scales, ix->row_bytes, ix->graph, deg, ix->deg_pad,
@@ -1005,7 +1031,7 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     a.prow_bytes = ix->row_bytes;
     const uint32_t stage_bytes = std::max(ix->row_bytes, q.rerank ? a.row32_bytes : 0u);
     a.stage_stride = smem_row_stride(stage_bytes);
-    a.stage_rows = (uint32_t)std::min(32, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
+    a.stage_rows = (uint32_t)std::min(16, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
     // visited tables: the queue plus one iteration's candidates must fit in
     // half a table (the reset threshold)
     if (cap_buf + cap_cand > (1u << (kVisitedBits - 1))) {
@@ -1019,11 +1045,12 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     a.idbits = ix->visited.idbits;
     a.vgmax = (uint32_t)((1ull << (32 - ix->visited.idbits)) - 1);
     a.slot_base = 0;
+    a.gbm_words = (q.entry != ANN_ENTRY_RANDOM && ix->n_ghost <= kGhostBitmapMax) ? (ix->n_ghost + 31) / 32 : 0;
     warps = 4;
     Layout lay{};
     for (;;) {
         lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W, adj_words, dir_words, a.prow_bytes,
-                          a.stage_rows, a.stage_stride);
+                          a.stage_rows, a.stage_stride, a.gbm_words, serve);
         if ((size_t)lay.total * warps <= ix->smem_optin) break;
         if (warps > 1) { warps /= 2; continue; }
         set_error("ann_search: per-query state (%u bytes) exceeds shared memory", lay.total);
@@ -1079,7 +1106,7 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
     Args a{};
     int warps = 0, nb = 0;
     size_t smem = 0;
-    s = plan_args(ix, q, a, warps, smem, nb);
+    s = plan_args(ix, q, a, warps, smem, nb, false);
     if (s != ANN_OK) return s;
     a.queries = queries;
     a.nq = nq;
@@ -1115,7 +1142,7 @@ ann_status serve_plan(ann_index *ix, const ann_search_params *maxp, uint32_t n_g
     ann_status s = derive_qparams(ix, maxp, n_given_max, &q);
     if (s != ANN_OK) return s;
     ServePlanImpl *pl = new ServePlanImpl();
-    s = plan_args(ix, q, pl->a, pl->warps, pl->smem, pl->nb);
+    s = plan_args(ix, q, pl->a, pl->warps, pl->smem, pl->nb, true);
     if (s == ANN_OK) {
         pl->slots_per_launch = (uint32_t)(pl->nb * ix->num_sms * pl->warps);
         s = visited_pool_alloc(pl->visited, pl->slots_per_launch * std::max(1u, n_streams), kVisitedBits, ix->n);
