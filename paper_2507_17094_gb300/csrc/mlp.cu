@@ -35,7 +35,13 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
 constexpr int TILE_A = BM * BK * 2;
 constexpr int TILE_B = BN * BK * 2;
-constexpr int GEMM_SMEM = STAGES * (TILE_A + TILE_B) + 1024 + 256;
+constexpr int GEMM_STAGE_BYTES = STAGES * (TILE_A + TILE_B);
+// top-P epilogue: each of the 8 x 32 epilogue threads parks a 32-logit chunk
+// here (stride 33 floats: conflict-free) while it inserts the chunk's
+// candidates one per step
+constexpr int XS_STRIDE = 33;
+constexpr int GEMM_XS_BYTES = 8 * 32 * XS_STRIDE * 4;
+constexpr int GEMM_SMEM = GEMM_STAGE_BYTES + 256 + GEMM_XS_BYTES + 1024;
 constexpr int TOPP = 8;   // top-P of the fused inference epilogue
 
 enum { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_RELU_BF16 = 2, EPI_TOPP = 3 };
@@ -118,6 +124,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// 2^x by the hardware approximation (MUFU): the softmax sum only decides the
+// confidence fallback, relative error ~2^-22 is ample.
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ bool better(float va, uint32_t ia, float vb, uint32_t ib)
 {
     return va > vb || (va == vb && ia < ib);
@@ -154,7 +169,7 @@ struct TopP {
 // Rows m >= M take part in the warp's collectives with no effect.
 template <int EPI>
 __device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m, uint32_t M, uint32_t nb, uint32_t N,
-                                               const EpiArgs &e, TopP &tp)
+                                               const EpiArgs &e, TopP &tp, float *xs)
 {
     const bool full = nb + 32 <= N;
     float bias[32];
@@ -213,9 +228,10 @@ __device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m,
         }
     } else {
         // logits of the chunk; their max and exp-sum by trees, one
-        // online-softmax combine; insertion into the top-P only where some
-        // lane of the warp has a logit above its current P-th (columns
-        // arrive in increasing order, so a tie never enters)
+        // online-softmax combine; then the logits above the thread's current
+        // P-th enter its top-P one per step (columns arrive in increasing
+        // order, so a tie never enters), all lanes inserting together
+        constexpr float kLog2e = 1.4426950408889634f;
         float x[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) x[j] = (m < M && nb + j < N) ? v[j] + bias[j] : -INFINITY;
@@ -228,34 +244,50 @@ __device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m,
             for (int j = 0; j < w; ++j) t[j] = fmaxf(t[j], t[j + w]);
         const float cm = t[0];
         if (cm > -INFINITY) {
+            const float off = -cm * kLog2e;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) t[j] = __expf(x[j] - cm) + __expf(x[j + 16] - cm);
+            for (int j = 0; j < 16; ++j) t[j] = ex2_approx(fmaf(x[j], kLog2e, off)) + ex2_approx(fmaf(x[j + 16], kLog2e, off));
 #pragma unroll
             for (int w = 8; w; w >>= 1)
 #pragma unroll
                 for (int j = 0; j < w; ++j) t[j] += t[j + w];
             const float cs = t[0];
             if (cm > tp.mx) {
-                tp.sm = tp.sm * __expf(tp.mx - cm) + cs;
+                tp.sm = tp.sm * ex2_approx((tp.mx - cm) * kLog2e) + cs;
                 tp.mx = cm;
             } else {
-                tp.sm += cs * __expf(cm - tp.mx);
+                tp.sm += cs * ex2_approx((cm - tp.mx) * kLog2e);
             }
         }
-        if (__any_sync(0xffffffffu, cm > tp.tv[TOPP - 1])) {
+        uint32_t pend = 0;
+        const float th = tp.tv[TOPP - 1];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (!(x[j] > tp.tv[TOPP - 1])) continue;
-                tp.tv[TOPP - 1] = x[j];
-                tp.ti[TOPP - 1] = nb + j;
+        for (int j = 0; j < 32; ++j) pend |= (x[j] > th ? 1u : 0u) << j;
+        if (__any_sync(0xffffffffu, pend != 0)) {
+            if (pend) {
 #pragma unroll
-                for (int p = TOPP - 1; p > 0; --p) {
-                    if (better(tp.tv[p], tp.ti[p], tp.tv[p - 1], tp.ti[p - 1])) {
-                        const float tt = tp.tv[p]; tp.tv[p] = tp.tv[p - 1]; tp.tv[p - 1] = tt;
-                        const uint32_t u = tp.ti[p]; tp.ti[p] = tp.ti[p - 1]; tp.ti[p - 1] = u;
+                for (int j = 0; j < 32; ++j) xs[j] = x[j];
+            }
+            __syncwarp();
+            while (__any_sync(0xffffffffu, pend != 0)) {
+                if (pend) {
+                    const uint32_t j = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    const float xv = xs[j];
+                    if (xv > tp.tv[TOPP - 1]) {
+                        tp.tv[TOPP - 1] = xv;
+                        tp.ti[TOPP - 1] = nb + j;
+#pragma unroll
+                        for (int p = TOPP - 1; p > 0; --p) {
+                            if (better(tp.tv[p], tp.ti[p], tp.tv[p - 1], tp.ti[p - 1])) {
+                                const float tt = tp.tv[p]; tp.tv[p] = tp.tv[p - 1]; tp.tv[p - 1] = tt;
+                                const uint32_t u = tp.ti[p]; tp.ti[p] = tp.ti[p - 1]; tp.ti[p - 1] = u;
+                            }
+                        }
                     }
                 }
             }
+            __syncwarp();
         }
     }
 }
@@ -284,11 +316,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     uint8_t *smem = smem_raw + pad;
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * TILE_A;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * (TILE_A + TILE_B));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + GEMM_STAGE_BYTES);
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;     // [2]: MMA -> epilogue
     uint64_t *acc_empty = acc_full + 2;      // [2]: epilogue -> MMA
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    float *xs_all = reinterpret_cast<float *>(smem + GEMM_STAGE_BYTES + 256);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t nkb = (K + BK - 1) / BK;
     const uint32_t n_tiles = (N + BN - 1) / BN, m_tiles = (M + BM - 1) / BM;
@@ -384,7 +417,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 float v[32];
                 __syncwarp();
                 tmem_ld32(tmem + buf * BN + ((q * 32u) << 16) + c0, v);
-                epilogue_chunk<EPI>(v, m, M, n0 + c0, N, e, tp);
+                epilogue_chunk<EPI>(v, m, M, n0 + c0, N, e, tp, xs_all + (threadIdx.x - 64) * XS_STRIDE);
             }
             tc_fence_before();
             __syncwarp();
