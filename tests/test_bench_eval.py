@@ -1,0 +1,28 @@
+"""The benchmark's own FP64 ground truth and recall agree with the oracle's
+(the benchmark runs the oracle only in its CPU-baseline leg)."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+torch = pytest.importorskip("torch")
+
+
+def test_truth_knn_and_recall_match_the_oracle():
+    import bench
+    rng = np.random.default_rng(5)
+    X = rng.integers(0, 6, (3000, 12)).astype(np.float32)       # many exact ties
+    Q = rng.integers(0, 6, (40, 12)).astype(np.float32)
+    ids, d = bench.truth_knn(X, Q, 10, "cpu")
+    o_ids, o_d = O.knn_f64(X, Q, 10)
+    assert np.array_equal(d, o_d)
+    assert np.array_equal(ids, o_ids)
+    # recall of a perturbed answer set, both definitions
+    ann = o_ids.copy()
+    ann[::3, 4:] = rng.integers(0, 3000, ann[::3, 4:].shape).astype(np.uint32)
+    ann[1, 9] = 0xFFFFFFFF
+    ann[2, 8] = ann[2, 7]
+    want = O.recall_at_k(ann, o_ids, o_d, X, Q, 10)[0]
+    got = bench.recall_at(ann.view(np.int32), d, X, Q, 10)
+    assert abs(got - want) < 1e-12
+    assert np.array_equal(bench.pair_dist(X, Q, ann[:, :5]), O.pair_dist_f64(X, Q, ann[:, :5]))
