@@ -103,17 +103,17 @@ def kernel_hash() -> str:
 
 def ncu_traffic(workload: str, form: str):
     """DRAM bytes per launch of the search kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
+    summary (a line 'traffic <workload> <form>: <bytes> bytes per launch,
+    kernel source <hash>'), if it was taken on the current kernel source."""
+    import re
+    p = os.path.join(ROOT, "profiles", "search_kernel_scale-1M-96d.md")
     if not os.path.exists(p):
         return None
-    try:
-        d = json.load(open(p))
-        e = d.get(workload, {}).get(form)
-        if e and e.get("kernel_hash") == kernel_hash():
-            return e
-    except (ValueError, OSError):
-        return None
+    pat = re.compile(r"traffic (\S+) (\S+): (\d+) bytes per launch, kernel source ([0-9a-f]+)")
+    for line in open(p):
+        m = pat.search(line)
+        if m and m.group(1) == workload and m.group(2) == form and m.group(4) == kernel_hash():
+            return {"dram_bytes_per_launch": int(m.group(3))}
     return None
 
 
