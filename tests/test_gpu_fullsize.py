@@ -33,6 +33,19 @@ def gpu_search(ix, Q, **p):
     return ids.cpu().numpy().view(np.uint32), dists.cpu().numpy(), A.stats_to_numpy(st)
 
 
+def qps(fn, nq, reps=5):
+    """Queries per second of fn() (one batch of nq queries), CUDA events."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return nq * reps / (e0.elapsed_time(e1) / 1e3)
+
+
 def check_sample(ds, storage, g_ids, g_d, idx, params, recall_min):
     """Oracle search of the sampled queries, each with the RNG stream it had
     in the full GPU batch (qid = qid_base + its row in the batch)."""
@@ -85,7 +98,10 @@ def test_precision_10m(storage, k, itopk):
     g_ids, g_d, st = gpu_search(ix, ds.Q, **p)
     assert (st["status"] == 0).all()
     rec = check_sample(ds, storage, g_ids, g_d, sample_rows(len(ds.Q), 150, 2), p, 0.8)
-    print(f"workload 3 storage {storage} k {k} itopk {itopk}: recall {rec:.3f}")
+    Qd = torch.from_numpy(ds.Q).cuda()
+    rate = qps(lambda: ix.search(Qd, **p), len(ds.Q))
+    print(f"workload 3 storage {storage} k {k} itopk {itopk}: recall {rec:.3f}, {rate / 1e6:.3f}M QPS, "
+          f"rows {st['vec_rows'].mean():.0f}, rerank rows {st['rerank_rows'].mean():.0f}")
     ix.close()
 
 
@@ -116,9 +132,16 @@ def test_learned_entry_5m():
         torch.cuda.synchronize()
         stn = A.stats_to_numpy(st)
         rec = O.recall_at_k(ids.cpu().numpy().view(np.uint32)[idx], gt, gd, ds.X, ds.Q[idx], 10)[0]
-        out[name] = (rec, stn["ghost_vec_rows"].mean())
-    print(f"workload 4: ghost staging recall {out['ghost'][0]:.3f} ghost rows {out['ghost'][1]:.0f}; "
-          f"learned recall {out['learned'][0]:.3f} ghost rows {out['learned'][1]:.0f}; tau {tau:.3g}, val hit {hit:.3f}")
+        if name == "ghost":
+            rate = qps(lambda: ix.search(Q, **common, **extra), len(ds.Q))
+        else:
+            rate = qps(lambda: ix.search(Q, given=le.seeds(Q)[0], **common, ghost_max_iters_given=4, entry=2),
+                       len(ds.Q))
+        out[name] = (rec, stn["ghost_vec_rows"].mean(), rate)
+    print(f"workload 4: ghost staging recall {out['ghost'][0]:.3f} ghost rows {out['ghost'][1]:.0f} "
+          f"{out['ghost'][2] / 1e6:.3f}M QPS; learned recall {out['learned'][0]:.3f} ghost rows "
+          f"{out['learned'][1]:.0f} {out['learned'][2] / 1e6:.3f}M QPS (predict included); tau {tau:.3g}, "
+          f"val hit {hit:.3f}, fallback {float((seeds[:, 0] == -1).float().mean()):.3f}")
     assert out["learned"][1] < out["ghost"][1]
     assert out["learned"][0] >= out["ghost"][0] - 0.02
     le.close()
