@@ -173,3 +173,29 @@ def test_empty_batch_and_errors():
         gi.search(torch.zeros((1, 128), device="cuda"), itopk=1024)
     with pytest.raises(A.AnnError):
         gi.search(torch.zeros((1, 128), device="cuda"), rerank=1, entry=2)   # given seeds missing
+
+
+def test_searches_on_two_streams_of_one_index():
+    """Searches of one index launched on different streams share its visited
+    tables and work counter; the library orders them, so each result equals
+    the same search run alone."""
+    c = tiny_case()
+    gi = c.gpu_index(O.F32)
+    Q = torch.from_numpy(c.Q).cuda()
+    p1 = dict(seed=11, entry=1, dgs_discard=0.5, itopk=64, max_iters=64)
+    p2 = dict(seed=12, entry=0, itopk=32, max_iters=40)
+    a1, d1, _ = gi.search(Q, **p1)
+    a2, d2, _ = gi.search(Q, **p2)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for _ in range(4):
+        with torch.cuda.stream(s1):
+            outs.append((1, gi.search(Q, stream=s1, **p1)))
+        with torch.cuda.stream(s2):
+            outs.append((2, gi.search(Q, stream=s2, **p2)))
+    torch.cuda.synchronize()
+    gi.sync()
+    for which, (ids, dists, _) in outs:
+        want = (a1, d1) if which == 1 else (a2, d2)
+        assert torch.equal(ids, want[0]) and torch.equal(dists, want[1])
