@@ -18,15 +18,12 @@
 // error word and gives up instead of spinning forever.
 #define ANN_WAIT_LIMIT_CYCLES (2000000000ll)
 
-// Per-warp visited tables in global memory, one table of 2^bits uint32
-// entries per resident-warp slot, plus each slot's current generation.
-// An entry is (generation << idbits) | id; entries of older generations count
-// as empty, so starting a new query's set is one increment, and the table is
-// zeroed only when the generation counter wraps.
+// Per-warp visited tables in global memory: one table of 2^bits uint32
+// entries (id + 1, 0 = empty) per resident-warp slot; a warp zeroes its table
+// at the start of each query.
 struct ann_visited_pool {
     uint32_t *tab = nullptr;     // slots x 2^bits
-    uint32_t *gen = nullptr;     // slots
-    uint32_t slots = 0, bits = 0, idbits = 0;
+    uint32_t slots = 0, bits = 0;
 };
 
 struct ann_index {
@@ -99,9 +96,9 @@ struct ServeRing {
     uint32_t cap, kmax, per_warp;
 };
 
-// Visited tables for `slots` warps over ids < n (n < 2^31), 2^bits entries
-// each; zeroed. visited_pool_free releases them.
-ann_status visited_pool_alloc(ann_visited_pool &vp, uint32_t slots, uint32_t bits, uint64_t n);
+// Visited tables for `slots` warps, 2^bits entries each; zeroed.
+// visited_pool_free releases them.
+ann_status visited_pool_alloc(ann_visited_pool &vp, uint32_t slots, uint32_t bits);
 void visited_pool_free(ann_visited_pool &vp);
 // Warp slots that one launch of the search or serve kernel can occupy.
 uint32_t max_warp_slots(const ann_index *ix);

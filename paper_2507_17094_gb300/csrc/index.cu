@@ -17,18 +17,13 @@
 
 namespace ann {
 
-ann_status visited_pool_alloc(ann_visited_pool &vp, uint32_t slots, uint32_t bits, uint64_t n)
+ann_status visited_pool_alloc(ann_visited_pool &vp, uint32_t slots, uint32_t bits)
 {
-    uint32_t idbits = 1;
-    while (idbits < 31 && (1ull << idbits) < n) ++idbits;
     vp.slots = slots;
     vp.bits = bits;
-    vp.idbits = idbits;
     const size_t tab_bytes = ((size_t)slots << bits) * sizeof(uint32_t);
     cudaError_t e = cudaMalloc(&vp.tab, tab_bytes);
     if (e == cudaSuccess) e = cudaMemset(vp.tab, 0, tab_bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&vp.gen, (size_t)slots * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(vp.gen, 0, (size_t)slots * sizeof(uint32_t));
     if (e != cudaSuccess) {
         visited_pool_free(vp);
         return cuda_fail(e, "visited tables");
@@ -39,12 +34,12 @@ ann_status visited_pool_alloc(ann_visited_pool &vp, uint32_t slots, uint32_t bit
 void visited_pool_free(ann_visited_pool &vp)
 {
     if (vp.tab) cudaFree(vp.tab);
-    if (vp.gen) cudaFree(vp.gen);
     vp = ann_visited_pool{};
 }
 
-// The search and serve kernels run 4 warps per block and at most 7 blocks
-// per SM (their launch bounds).
+// Visited-table slots of an index: 28 warps per SM, more than the search
+// kernel's register budget lets run (6 blocks of 4 warps); a launch is also
+// capped so that its resident warps never outnumber the slots.
 uint32_t max_warp_slots(const ann_index *ix) { return (uint32_t)ix->num_sms * 7u * 4u; }
 
 static thread_local char g_err[512] = "";
@@ -388,7 +383,7 @@ ann_status ann_index_create(int device, ann_storage storage, uint64_t n, uint32_
     ANN_TRY(cudaMalloc(&ix->d_error, 64));
     ANN_TRY(cudaMemset(ix->d_error, 0, 64));
     ANN_TRY(cudaEventCreateWithFlags(&ix->busy, cudaEventDisableTiming));
-    if (ann_status vs = visited_pool_alloc(ix->visited, max_warp_slots(ix), kVisitedBits, n); vs != ANN_OK)
+    if (ann_status vs = visited_pool_alloc(ix->visited, max_warp_slots(ix), kVisitedBits); vs != ANN_OK)
         return fail(vs);
 
     // vectors: upload in chunks of FP32 rows, encode into the padded layout

@@ -28,15 +28,13 @@
 //     candidates plus its insertion point in the queue, and only queue
 //     entries behind the first insertion point move.
 //
-// Visited set: open addressing with linear probing over entries
-// (generation << idbits) | id. Entries of older generations are empty, so a
-// new query (or the switch from the ghost to the base graph) only increments
-// the warp's generation. Insertion is atomicMax along the probe sequence: an
-// entry only ever grows within a generation, a smaller current entry is
-// displaced and carried on to the next slot, so every id sits behind a run of
-// larger current entries from its home slot and a lookup finds it; the first
-// slot whose entry is smaller than the id (or empty) proves it absent.
-// The table is exact between resets. It is reset (and refilled with the
+// Visited set: open addressing with linear probing over entries id + 1 (0 =
+// empty) in the warp's table in global memory, zeroed at the start of each
+// query (and at the switch from the ghost to the base graph). A lane claims
+// an empty slot with atomicCAS; slots only ever change from empty to an id,
+// so a probe run never moves and a lookup that reaches an empty slot has
+// proved the id absent (concurrent lanes inserting the same id: one CAS wins,
+// the other then finds it). The table is exact between resets. It is reset (and refilled with the
 // queue's ids) only when it would pass half full. Forgetting a node that is no
 // longer in the queue cannot change the result: its key is larger than the
 // queue's current l-th key (which only decreases), so re-evaluating it rejects
@@ -92,9 +90,9 @@ struct Args {
     Layout lay;
     uint32_t cap_cand, stage_rows, stage_stride, prow_bytes;
     // visited tables: slot_base + warp slot selects one table of 2^vbits
-    // entries; generations run 1..vgmax
-    uint32_t *vtab, *vgen;
-    uint32_t vbits, vstride_bits, idbits, vgmax, slot_base;
+    // entries (tables 2^vstride_bits entries apart)
+    uint32_t *vtab;
+    uint32_t vbits, vstride_bits, slot_base;
     uint32_t gbm_words;   // > 0: the ghost stage's visited set is a bitmap of this many words
 };
 
@@ -198,13 +196,10 @@ struct WarpSearch {
     uint64_t qid = 0;
     ann_query_stats st;
     uint32_t *vt;        // this warp's visited table
-    uint32_t *vgen_at;   // its generation word
-    uint32_t vg;         // current generation
     bool gbm = false;    // the visited set is the ghost bitmap (ghost stage, small ghost sets)
 
     __device__ WarpSearch(const Args &args, uint8_t *b, uint32_t slot)
-        : a(args), base(b), lane(threadIdx.x & 31), vt(args.vtab + ((size_t)slot << args.vstride_bits)),
-          vgen_at(args.vgen + slot), vg(__ldcg(args.vgen + slot)) {}
+        : a(args), base(b), lane(threadIdx.x & 31), vt(args.vtab + ((size_t)slot << args.vstride_bits)) {}
 
     // shared-memory arrays of this warp
     __device__ __forceinline__ float *q() const { return reinterpret_cast<float *>(base + a.lay.q); }
@@ -223,25 +218,22 @@ struct WarpSearch {
     __device__ __forceinline__ uint64_t *bar() const { return reinterpret_cast<uint64_t *>(base + a.lay.bar); }
 
     // ---------------------------------------------------------- visited set
+    __device__ __forceinline__ uint32_t *gbits() const { return reinterpret_cast<uint32_t *>(base + a.lay.dir); }
     __device__ __forceinline__ uint32_t hash_home(uint32_t v) const { return (v * 2654435761u) >> (32 - a.vbits); }
 
-    // The rest of a test-and-insert whose first probe (at slot s, entry cur
-    // = this generation's tag | id) returned old: true if the id was new.
-    __device__ bool hash_finish(uint32_t s, uint32_t cur, uint32_t old)
+    // The rest of a test-and-insert of entry want (id + 1) whose first probe,
+    // a CAS of slot s from empty, returned old: true if the id was new.
+    __device__ bool hash_finish(uint32_t s, uint32_t want, uint32_t old)
     {
-        const uint32_t tag = vg << a.idbits;
         const uint32_t mask = (1u << a.vbits) - 1;
         for (uint32_t probe = 0; probe <= mask; ++probe) {
-            if (old == cur) return false;         // only the id itself can be found: entries are unique
-            if (old < tag) return true;           // an empty slot took cur
-            if (old < cur) cur = old;             // cur took the slot; carry the displaced entry on
+            if (old == 0) return true;        // claimed an empty slot
+            if (old == want) return false;    // found it
             s = (s + 1) & mask;
-            old = atomicMax(vt + s, cur);
+            old = atomicCAS(vt + s, 0u, want);
         }
         return true;  // unreachable: the table is never more than half full
     }
-
-    __device__ __forceinline__ uint32_t *gbits() const { return reinterpret_cast<uint32_t *>(base + a.lay.dir); }
 
     // Test-and-insert: true if v was not in the set (and is now).
     __device__ bool hash_insert(uint32_t v)
@@ -250,12 +242,11 @@ struct WarpSearch {
             const uint32_t bit = 1u << (v & 31);
             return (atomicOr(gbits() + (v >> 5), bit) & bit) == 0;
         }
-        const uint32_t s = hash_home(v), cur = (vg << a.idbits) | v;
-        return hash_finish(s, cur, atomicMax(vt + s, cur));
+        const uint32_t s = hash_home(v);
+        return hash_finish(s, v + 1, atomicCAS(vt + s, 0u, v + 1));
     }
 
-    // Start an empty set: the next generation (zeroing the table when the
-    // generation counter wraps).
+    // Start an empty set: zero the bitmap or the warp's table.
     __device__ void hash_clear()
     {
         if (gbm) {
@@ -264,14 +255,11 @@ struct WarpSearch {
             hash_count = 0;
             return;
         }
-        if (++vg > a.vgmax) {
-            const uint32_t H = 1u << a.vbits;
-            for (uint32_t i = lane; i < H; i += 32) vt[i] = 0;
-            __threadfence();
-            vg = 1;
-        }
-        __syncwarp();
-        if (lane == 0) *vgen_at = vg;
+        const uint32_t H = 1u << a.vbits;
+        uint4 *t4 = reinterpret_cast<uint4 *>(vt);
+        for (uint32_t i = lane; i < H / 4; i += 32) t4[i] = make_uint4(0, 0, 0, 0);
+        __threadfence_block();
+        __syncwarp();   // the lanes' zeroing precedes any lane's probes
         hash_count = 0;
     }
 
@@ -451,8 +439,8 @@ struct WarpSearch {
         for (uint32_t r = 0; r < NW; ++r) {
             if (ok[r]) {
                 hs[r] = hash_home(nb[r]);
-                cur[r] = (vg << a.idbits) | nb[r];
-                old[r] = atomicMax(vt + hs[r], cur[r]);
+                cur[r] = nb[r] + 1;
+                old[r] = atomicCAS(vt + hs[r], 0u, cur[r]);
             }
         }
 #pragma unroll
@@ -491,11 +479,13 @@ struct WarpSearch {
     }
 
     // ------------------------------------------------------------- seeding
-    // Random seeds j = 0..m-1 (Step 2), deduplicated without redraw: node j
-    // is splitmix64(key ^ (qid << 32) ^ j) mod n, key = splitmix64(seed ^ tag).
+    // Seeds (Step 2): given nodes (ids, the learned entry's ghost nodes;
+    // invalid or out-of-range ids skipped) or, with ids NULL, m random nodes
+    // deduplicated without redraw: node j is splitmix64(key ^ (qid << 32) ^ j)
+    // mod n, key = splitmix64(seed ^ tag).
     template <int RST>
-    __device__ bool seed_random(const View &v, uint32_t m, uint64_t seed, uint64_t tag, uint32_t lcap,
-                                uint32_t &rows)
+    __device__ bool seed(const View &v, const uint32_t *ids, uint32_t m, uint64_t seed, uint64_t tag, uint32_t lcap,
+                         uint32_t &rows)
     {
         const uint64_t key = splitmix64(seed ^ tag);
         for (uint32_t j0 = 0; j0 < m; j0 += a.cap_cand) {
@@ -503,30 +493,10 @@ struct WarpSearch {
             hash_make_room(chunk);
             uint32_t nc = 0;
             for (uint32_t b = 0; b < chunk; b += 32) {
-                const bool valid = b + lane < chunk;
-                uint32_t id = 0;
-                if (valid) id = (uint32_t)(splitmix64(key ^ (qid << 32) ^ (uint64_t)(j0 + b + lane)) % v.n);
-                nc = collect(valid, id, nc);
-            }
-            __syncwarp();
-            hash_count += nc;
-            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
-            rows += nc;
-            merge(nc, lcap);
-        }
-        return true;
-    }
-
-    // Given ghost seeds (learned entry). Invalid or out-of-range ids are skipped.
-    template <int RST>
-    __device__ bool seed_given(const View &v, const uint32_t *ids, uint32_t m, uint32_t lcap, uint32_t &rows)
-    {
-        for (uint32_t j0 = 0; j0 < m; j0 += a.cap_cand) {
-            const uint32_t chunk = min(a.cap_cand, m - j0);
-            hash_make_room(chunk);
-            uint32_t nc = 0;
-            for (uint32_t b = 0; b < chunk; b += 32) {
-                const uint32_t id = (b + lane < chunk) ? __ldcg(ids + j0 + b + lane) : kEmpty;
+                const uint32_t j = j0 + b + lane;
+                uint32_t id = kEmpty;
+                if (b + lane < chunk)
+                    id = ids ? __ldcg(ids + j) : (uint32_t)(splitmix64(key ^ (qid << 32) ^ (uint64_t)j) % v.n);
                 nc = collect(id < v.n, id, nc);
             }
             __syncwarp();
@@ -577,38 +547,61 @@ struct WarpSearch {
     // NW = number of 32-slot words the degree spans (1, 2 or 4), so no
     // ballot is spent on slots past the degree.
     template <uint32_t NW>
-    __device__ uint32_t dgs_keep_nw(const View &v, uint32_t pi, uint32_t n_keep)
+    __device__ uint32_t dgs_keep_nw(const View &v, uint32_t pi, uint32_t n_keep, float ps)
     {
         const uint32_t w = a.w, deg = v.deg;
-        const uint32_t *pq = pqb() + pi * w;
+        const uint8_t *pr = prow() + pi * a.prow_bytes;
+        // mismatching sign bits per slot, 8 words of the query's sign bits
+        // relative to the parent ([q > x_parent], one ballot per 32
+        // dimensions) at a time, kept in registers
+        int diff[NW];
+        bool live[NW];
+        const uint32_t *db[NW];
+#pragma unroll
+        for (uint32_t r = 0; r < NW; ++r) {
+            const uint32_t j = lane + 32 * r;
+            live[r] = j < deg && adj()[pi * v.deg_pad + min(j, deg - 1)] != ANN_INVALID_ID;
+            db[r] = dirs() + (pi * v.deg_pad + min(j, deg - 1)) * w;
+            diff[r] = 0;
+        }
+        for (uint32_t t0 = 0; t0 < w; t0 += 8) {
+            uint32_t qw[8];
+#pragma unroll
+            for (uint32_t x = 0; x < 8; ++x) {
+                const uint32_t i = 32 * (t0 + x) + lane;
+                const bool bit = i < a.d && q()[min(i, a.d - 1)] > stored_elem<ST>(pr, min(i, a.d - 1), ps);
+                qw[x] = __ballot_sync(0xffffffffu, bit);
+            }
+#pragma unroll
+            for (uint32_t r = 0; r < NW; ++r)
+#pragma unroll
+                for (uint32_t x = 0; x < 8; ++x)
+                    if (t0 + x < w) diff[r] += __popc(qw[x] ^ db[r][t0 + x]);
+        }
         int sc[NW];
 #pragma unroll
         for (uint32_t r = 0; r < NW; ++r) {
             const uint32_t j = lane + 32 * r;
-            sc[r] = -2;  // beyond the degree: never kept
-            if (j < deg) {
-                const uint32_t nb = adj()[pi * v.deg_pad + j];
-                sc[r] = -1;
-                if (nb != ANN_INVALID_ID) {
-                    const uint32_t *db = dirs() + (pi * v.deg_pad + j) * w;
-                    int diff = 0;
-                    for (uint32_t x = 0; x < w; ++x) diff += __popc(pq[x] ^ db[x]);
-                    sc[r] = (int)a.d - diff;
-                }
-            }
+            sc[r] = j >= deg ? -2 : (live[r] ? (int)a.d - diff[r] : -1);  // -2: never kept
         }
-        int lo = -1, hi = (int)a.d + 1;  // count(score >= lo) >= n_keep > count(score >= hi)
+        // count(score >= lo) >= n_keep > count(score >= hi); hi starts one
+        // above the best score (warp reductions count across lanes)
+        int best = sc[0];
+#pragma unroll
+        for (uint32_t r = 1; r < NW; ++r) best = max(best, sc[r]);
+        int lo = -1, hi = (int)__reduce_max_sync(0xffffffffu, (uint32_t)(best + 2)) - 1;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             uint32_t c = 0;
 #pragma unroll
-            for (uint32_t r = 0; r < NW; ++r) c += __popc(__ballot_sync(0xffffffffu, sc[r] >= mid));
-            if (c >= n_keep) lo = mid;
+            for (uint32_t r = 0; r < NW; ++r) c += sc[r] >= mid ? 1u : 0u;
+            if (__reduce_add_sync(0xffffffffu, c) >= n_keep) lo = mid;
             else hi = mid;
         }
         uint32_t above = 0;
 #pragma unroll
-        for (uint32_t r = 0; r < NW; ++r) above += __popc(__ballot_sync(0xffffffffu, sc[r] > lo));
+        for (uint32_t r = 0; r < NW; ++r) above += sc[r] > lo ? 1u : 0u;
+        above = __reduce_add_sync(0xffffffffu, above);
         const uint32_t need = n_keep - above;
         uint32_t keep = 0, ties_before = 0;
 #pragma unroll
@@ -621,11 +614,11 @@ struct WarpSearch {
         return keep;
     }
 
-    __device__ uint32_t dgs_keep(const View &v, uint32_t pi, uint32_t n_keep)
+    __device__ uint32_t dgs_keep(const View &v, uint32_t pi, uint32_t n_keep, float ps)
     {
-        if (v.deg <= 32) return dgs_keep_nw<1>(v, pi, n_keep);
-        if (v.deg <= 64) return dgs_keep_nw<2>(v, pi, n_keep);
-        return dgs_keep_nw<kMaxDegWords>(v, pi, n_keep);
+        if (v.deg <= 32) return dgs_keep_nw<1>(v, pi, n_keep, ps);
+        if (v.deg <= 64) return dgs_keep_nw<2>(v, pi, n_keep, ps);
+        return dgs_keep_nw<kMaxDegWords>(v, pi, n_keep, ps);
     }
 
     // Steps 3-4 repeated, with DGS and its cool-down (Section 3.3.2).
@@ -674,26 +667,14 @@ struct WarpSearch {
             }
             if (!wait_copies()) return false;
             c_parents += np;
-            uint32_t keep[ANN_MAX_WIDTH];
-            if (dgs_now) {
-                c_dgs += np;
-                // the query's sign bits relative to each parent: [q > x_parent]
-                for (uint32_t pi = 0; pi < np; ++pi) {
-                    const float ps = __shfl_sync(0xffffffffu, pscale, pi);
-                    const uint8_t *pr = prow() + pi * a.prow_bytes;
-                    for (uint32_t t = 0; t < w; ++t) {
-                        const uint32_t i = 32 * t + lane;
-                        const bool bit = i < a.d && q()[i] > stored_elem<RST>(pr, i, ps);
-                        const uint32_t word = __ballot_sync(0xffffffffu, bit);
-                        if (lane == 0) pqb()[pi * w + t] = word;
-                    }
-                }
-                __syncwarp();
-                for (uint32_t pi = 0; pi < np; ++pi) keep[pi] = dgs_keep(v, pi, n_keep);
-            }
+            if (dgs_now) c_dgs += np;
             hash_make_room(np * deg);
             uint32_t nc = 0;
-            for (uint32_t pi = 0; pi < np; ++pi) nc = collect_row(v, pi, dgs_now ? keep[pi] : 0xffffffffu, nc);
+            for (uint32_t pi = 0; pi < np; ++pi) {
+                uint32_t km = 0xffffffffu;
+                if (dgs_now) km = dgs_keep(v, pi, n_keep, __shfl_sync(0xffffffffu, pscale, pi));
+                nc = collect_row(v, pi, km, nc);
+            }
             __syncwarp();
             hash_count += nc;
             if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
@@ -718,29 +699,20 @@ struct WarpSearch {
         // uses, and L1 is not kept coherent with those copies
         for (uint32_t i = lane; i < dpad; i += 32) q()[i] = i < a.d ? __ldcg(qg + i) : 0.0f;
         __syncwarp();
-        gbm = qp.entry != ANN_ENTRY_RANDOM && a.gbm_words > 0;
+        const bool ghost = qp.entry != ANN_ENTRY_RANDOM;
+        gbm = ghost && a.gbm_words > 0;
         hash_clear();
+        const uint32_t *given = nullptr;
+        if (qp.entry == ANN_ENTRY_GIVEN_GHOST && given_row && given_row[0] != ANN_INVALID_ID)
+            given = given_row;   // else: fall back to random ghost seeds
+        // stage 0: the ghost stage (Section 3.2.2) on the ghost graph; stage
+        // 1: the search on the base graph. One loop body serves both.
         bool ok = true;
-        if (qp.entry == ANN_ENTRY_RANDOM) {
-            ok = seed_random<ST>(a.base, qp.m, qp.seed, 0, qp.L, st.vec_rows);
-        } else {
-            const uint32_t *given = nullptr;
-            if (qp.entry == ANN_ENTRY_GIVEN_GHOST && given_row) {
-                given = given_row;
-                if (given[0] == ANN_INVALID_ID) given = nullptr;  // fall back to random ghost seeds
-            }
-            uint32_t Tg = qp.Tg;
-            if (given) {
-                Tg = qp.Tg_given;
-                ok = seed_given<ST>(a.ghost, given, qp.n_given, qp.Lg, st.ghost_vec_rows);
-            } else {
-                ok = seed_random<ST>(a.ghost, a.ghost.deg, qp.seed, kGhostTag, qp.Lg, st.ghost_vec_rows);
-            }
-            uint32_t no_dgs = 0;
-            if (ok)
-                ok = iterate<ST>(a.ghost, qp.Lg, 1, Tg, a.ghost.deg, 0, 0, st.ghost_iters, st.ghost_parents, no_dgs,
-                                 st.ghost_vec_rows);
-            if (ok) {
+        for (uint32_t stage = ghost ? 0u : 1u; stage < 2 && ok; ++stage) {
+            const View v = stage ? a.base : a.ghost;
+            const uint32_t lcap = stage ? qp.L : qp.Lg;
+            uint32_t rows = 0, iters = 0, parents = 0, dgs_parents = 0;
+            if (stage == 1 && ghost) {
                 // transition: the top g ghost results become the base queue;
                 // ghost ids are ascending, so the (dist, id) order carries over
                 const uint32_t g = min(min(qp.g, cnt), qp.L);
@@ -755,11 +727,26 @@ struct WarpSearch {
                 for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi()[i]);
                 __syncwarp();
                 hash_count = cnt;
+            } else {
+                const bool use_given = stage == 0 && given;
+                ok = seed<ST>(v, use_given ? given : nullptr, use_given ? qp.n_given : (stage ? qp.m : v.deg),
+                              qp.seed, stage ? 0 : kGhostTag, lcap, rows);
+            }
+            if (ok)
+                ok = iterate<ST>(v, lcap, stage ? qp.W : 1, stage ? qp.T : (given ? qp.Tg_given : qp.Tg),
+                                 stage ? qp.n_keep : v.deg, stage ? qp.it_cool : 0, stage ? qp.reexpand : 0, iters,
+                                 parents, dgs_parents, rows);
+            if (stage) {
+                st.iters = iters;
+                st.parents = parents;
+                st.dgs_parents = dgs_parents;
+                st.vec_rows = rows;
+            } else {
+                st.ghost_iters = iters;
+                st.ghost_parents = parents;
+                st.ghost_vec_rows = rows;
             }
         }
-        if (ok)
-            ok = iterate<ST>(a.base, qp.L, qp.W, qp.T, qp.n_keep, qp.it_cool, qp.reexpand, st.iters, st.parents,
-                             st.dgs_parents, st.vec_rows);
         if (ok && qp.rerank) {
             // FP32 distances of the whole queue on the originals, then the top k
             ok = evaluate<ANN_F32>(a.x32, nullptr, a.row32_bytes, bi(), cnt, bd());
@@ -799,7 +786,7 @@ struct WarpSearch {
 };
 
 template <int ST>
-__global__ void __launch_bounds__(128, 7) search_kernel(const Args a)
+__global__ void __launch_bounds__(128, 6) search_kernel(const Args a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -829,7 +816,7 @@ __global__ void __launch_bounds__(128, 7) search_kernel(const Args a)
 // warp that finishes a request's last query raises its completion flag in
 // host-mapped memory after a system-scope fence.
 template <int ST>
-__global__ void __launch_bounds__(128, 7) serve_kernel(const Args a, const ServeRing r)
+__global__ void __launch_bounds__(128, 6) serve_kernel(const Args a, const ServeRing r)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1039,11 +1026,8 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
         return ANN_EINVAL;
     }
     a.vtab = ix->visited.tab;
-    a.vgen = ix->visited.gen;
     a.vstride_bits = ix->visited.bits;
     a.vbits = ix->visited.bits;   // 4,096 entries: measured faster than 2,048 or 1,024 (L2-resident either way)
-    a.idbits = ix->visited.idbits;
-    a.vgmax = (uint32_t)((1ull << (32 - ix->visited.idbits)) - 1);
     a.slot_base = 0;
     a.gbm_words = (q.entry != ANN_ENTRY_RANDOM && ix->n_ghost <= kGhostBitmapMax) ? (ix->n_ghost + 31) / 32 : 0;
     warps = 4;
@@ -1117,7 +1101,9 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
     a.counter = counter;
     a.err = err;
     const uint64_t want = ((uint64_t)nq + warps - 1) / warps;
-    const int blocks = (int)std::min<uint64_t>(want, (uint64_t)nb * ix->num_sms);
+    // every resident warp needs its own visited table
+    const uint64_t cap = std::min<uint64_t>((uint64_t)nb * ix->num_sms, ix->visited.slots / (uint32_t)warps);
+    const int blocks = (int)std::min<uint64_t>(want, cap);
     // one search of this index at a time: its visited tables (and work
     // counter) are shared, so a launch on another stream waits for the last
     if (ix->busy_set && ix->busy_stream != stream) ANN_CUDA(cudaStreamWaitEvent(stream, ix->busy, 0));
@@ -1145,11 +1131,10 @@ ann_status serve_plan(ann_index *ix, const ann_search_params *maxp, uint32_t n_g
     s = plan_args(ix, q, pl->a, pl->warps, pl->smem, pl->nb, true);
     if (s == ANN_OK) {
         pl->slots_per_launch = (uint32_t)(pl->nb * ix->num_sms * pl->warps);
-        s = visited_pool_alloc(pl->visited, pl->slots_per_launch * std::max(1u, n_streams), kVisitedBits, ix->n);
+        s = visited_pool_alloc(pl->visited, pl->slots_per_launch * std::max(1u, n_streams), kVisitedBits);
     }
     if (s != ANN_OK) { delete pl; return s; }
     pl->a.vtab = pl->visited.tab;
-    pl->a.vgen = pl->visited.gen;
     pl->a.counter = ix->d_counter;
     pl->a.err = ix->d_error;
     pl->num_sms = ix->num_sms;

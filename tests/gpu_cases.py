@@ -117,3 +117,21 @@ def int_case(n=4000, d=128, deg=16, nq=64, seed=9):
     S = ghost_sample(n, n // 50, s.seeds["ghost"])
     Gg = build_graph(X[S], 8, 16, "exact", n_bridge=0)
     return Case(X, G, Q, S, Gg)
+
+
+@functools.lru_cache(maxsize=None)
+def hub_case(n=6000, d=32, deg=32, nq=96, seed=13):
+    """A graph built to crowd the visited table: every adjacency row starts
+    with the same four hub nodes and repeats neighbours (slot j + 16 copies
+    slot j for j < 8), so lanes of one warp insert equal ids at once and
+    long probe runs form; long searches fill the table towards its reset
+    threshold."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Q = rng.standard_normal((nq, d)).astype(np.float32)
+    G = build_graph(X, deg, 2 * deg, "exact", n_bridge=2).copy()
+    G[:, :4] = np.array([1, 2, 3, 5], dtype=np.uint32)
+    G[:, 16:24] = G[:, 0:8]
+    S = ghost_sample(n, n // 20, seed + 1)
+    Gg = build_graph(X[S], 8, 16, "exact", n_bridge=0)
+    return Case(X, G, Q, S, Gg)

@@ -199,3 +199,15 @@ def test_searches_on_two_streams_of_one_index():
     for which, (ids, dists, _) in outs:
         want = (a1, d1) if which == 1 else (a2, d2)
         assert torch.equal(ids, want[0]) and torch.equal(dists, want[1])
+
+
+@pytest.mark.parametrize("params", [dict(itopk=256, max_iters=400, search_width=4),
+                                    dict(itopk=512, k=50, max_iters=800, search_width=8, entry=1),
+                                    dict(itopk=64, max_iters=200, search_width=2, dgs_discard=0.5)])
+def test_visited_set_under_collisions(params):
+    """Equal ids inserted by several lanes at once, long probe runs and a
+    table filled towards its reset threshold: results still match the
+    oracle's exact visited set."""
+    from gpu_cases import hub_case
+    g, o = hub_case().run(O.F32, seed=5, **params)
+    assert_parity(g, o)
