@@ -171,6 +171,14 @@ ann_status ann_ghost_index_of(const ann_index *index, const uint32_t *ids, uint3
  * word: ANN_OK, or ANN_ETIMEOUT if a bounded device wait ran out. */
 ann_status ann_sync(ann_index *index, void *stream);
 
+/* Check the device-failure path (not in the paper): one warp waits about
+ * 1 ms on a barrier that nothing completes, the bounded wait runs out and
+ * records a timeout in the index's device error word, and ann_sync reports
+ * it (then clears it). Returns ANN_OK when all of that happened, ANN_EDEVICE
+ * if the timeout was not reported, or the CUDA error. Synchronises the
+ * device; the index stays usable. */
+ann_status ann_selftest_timeout(ann_index *index);
+
 /* Preprocessing primitives on caller-owned device memory (Section 3.3.2 (a)
  * and the low-precision codec), used by ann_index_create.
  * ann_encode: x (n x dim FP32) -> codes (n x dim FP16 or E4M3, dense rows) +

@@ -29,6 +29,7 @@ EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_inde
            "ann_encode", "ann_dir_table", "ann_mlp_create", "ann_mlp_free", "ann_mlp_set_params", "ann_mlp_get",
            "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_train_epochs", "ann_mlp_predict", "ann_mlp_sync",
            "ann_mlp_save", "ann_mlp_load", "ann_mlp_set_input_norm", "ann_mlp_get_input_norm",
+           "ann_selftest_timeout",
            "ann_ghost_index_of", "ann_server_create", "ann_server_submit", "ann_server_poll",
            "ann_server_in_flight", "ann_server_destroy", "ann_last_error")
 
@@ -87,6 +88,7 @@ def lib() -> C.CDLL:
             L.ann_search_host.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp]
             L.ann_search_host_noalloc.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, vp, vp]
             L.ann_sync.argtypes = [vp, vp]
+            L.ann_selftest_timeout.argtypes = [vp]
             f32 = C.c_float
             L.ann_mlp_create.argtypes = [C.c_int, u32, u32, u32, u32, u32, C.POINTER(vp)]
             L.ann_mlp_free.argtypes = [vp]
@@ -249,6 +251,10 @@ class Index:
 
     def sync(self, stream=None):
         _check(lib().ann_sync(self._h, _stream_ptr(stream)))
+
+    def selftest_timeout(self):
+        """Run the device-failure self-test (see include/ann.h); raises on failure."""
+        _check(lib().ann_selftest_timeout(self._h))
 
     def ghost_index_of(self, ids, stream=None):
         """Ghost index of each node id (CUDA int32 tensor); INVALID if not a ghost."""

@@ -186,14 +186,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for phase `parity` of `bar` to complete, at most ANN_WAIT_LIMIT_CYCLES.
+// Wait for phase `parity` of `bar` to complete, at most `limit` cycles.
 // Returns false (and records a timeout in *err) if it did not.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
+                                                  long long limit = ANN_WAIT_LIMIT_CYCLES)
 {
     if (mbar_try_wait(bar, parity)) return true;
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > ANN_WAIT_LIMIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             atomicExch(err, ANN_DEV_TIMEOUT);
             return false;
         }

@@ -532,6 +532,31 @@ ann_status ann_ghost_index_of(const ann_index *ix, const uint32_t *ids, uint32_t
     return ANN_OK;
 }
 
+// One warp waits, at most `cycles`, for a phase of an mbarrier that no copy
+// and no thread completes: the bounded wait must run out and record
+// ANN_DEV_TIMEOUT in *err, and the kernel then returns normally.
+__global__ void timeout_probe_kernel(int *err, long long cycles)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    fence_mbar_init();
+    __syncwarp();
+    (void)__all_sync(0xffffffffu, mbar_wait_bounded(&bar, 0, err, cycles));
+}
+
+ann_status ann_selftest_timeout(ann_index *ix)
+{
+    if (!ix) { set_error("ann_selftest_timeout: NULL index"); return ANN_EINVAL; }
+    DeviceGuard g(ix->device);
+    ANN_CUDA(cudaDeviceSynchronize());
+    timeout_probe_kernel<<<1, 32>>>(ix->d_error, 2000000ll);   // about 1 ms at 2 GHz
+    ANN_CUDA(cudaGetLastError());
+    const ann_status s = ann_sync(ix, nullptr);
+    if (s == ANN_ETIMEOUT) return ANN_OK;
+    if (s == ANN_OK) set_error("ann_selftest_timeout: the expired wait was not reported");
+    return s == ANN_OK ? ANN_EDEVICE : s;
+}
+
 ann_status ann_sync(ann_index *ix, void *stream)
 {
     if (!ix) { set_error("ann_sync: NULL index"); return ANN_EINVAL; }

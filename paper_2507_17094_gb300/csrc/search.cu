@@ -66,7 +66,7 @@ struct View {
 };
 
 struct Layout {  // byte offsets inside one warp's shared-memory region
-    uint32_t q, bd, bi, bs, cd, ci, cs, adj, dir, prow, pqb, par, stage, bar, qp, total;
+    uint32_t q, bd, bi, bs, cd, ci, cs, adj, dir, prow, par, stage, bar, qp, total;
 };
 
 // Ghost sets up to this many nodes get an exact shared-memory bitmap as the
@@ -212,7 +212,6 @@ struct WarpSearch {
     __device__ __forceinline__ uint32_t *adj() const { return reinterpret_cast<uint32_t *>(base + a.lay.adj); }
     __device__ __forceinline__ uint32_t *dirs() const { return reinterpret_cast<uint32_t *>(base + a.lay.dir); }
     __device__ __forceinline__ uint8_t *prow() const { return base + a.lay.prow; }
-    __device__ __forceinline__ uint32_t *pqb() const { return reinterpret_cast<uint32_t *>(base + a.lay.pqb); }
     __device__ __forceinline__ uint32_t *par() const { return reinterpret_cast<uint32_t *>(base + a.lay.par); }
     __device__ __forceinline__ uint8_t *stage() const { return base + a.lay.stage; }
     __device__ __forceinline__ uint64_t *bar() const { return reinterpret_cast<uint64_t *>(base + a.lay.bar); }
@@ -889,7 +888,6 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
     const uint32_t dir_part = align16(dir_words * 4) + align16(dir_words ? W * prow_bytes : 0);
     L.dir = take(std::max(dir_part, gbm_words * 4));
     L.prow = L.dir + align16(dir_words * 4);
-    L.pqb = take(W * w * 4);
     L.par = take(W * 4);
     L.stage = take(stage_rows * stage_stride);
     L.bar = take(16);

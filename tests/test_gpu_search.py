@@ -211,3 +211,14 @@ def test_visited_set_under_collisions(params):
     from gpu_cases import hub_case
     g, o = hub_case().run(O.F32, seed=5, **params)
     assert_parity(g, o)
+
+
+def test_bounded_wait_timeout_is_reported_and_recoverable():
+    """A device wait on a barrier nothing completes runs out, is reported
+    through the error word as ANN_ETIMEOUT, and the index keeps working."""
+    c = tiny_case()
+    gi = c.gpu_index(O.F32)
+    gi.selftest_timeout()
+    gi.sync()                                   # the error word was cleared
+    g, o = c.run(O.F32, seed=4001, itopk=64, max_iters=64, entry=1)
+    assert_parity(g, o)
