@@ -172,22 +172,24 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ forms
-# Operating points on the 1M x 96 workload (measured sweeps). Ghost staging
-# from random ghost seeds (ghost-stage length 24-64, DGS discard 0.5-0.75,
-# iteration cap itopk + 16 or 2 itopk + 32, at itopk 32): 48 ghost
-# iterations, discard 0.7, cap itopk + 16 is the fastest setting whose
-# recall@10 stays at or above 0.95. From the learned entry's seeds (4 or 8
-# ghost iterations, discard 0.5 or 0.7, itopk 16 and 32): 4 ghost
-# iterations and discard 0.5 reach 0.973 at itopk 16, where discard 0.7
-# stops at 0.942.
-GHOST_ITERS = 48
-DGS_DISCARD = 0.7
+# Operating points on the 1M x 96 workload (measured sweeps at itopk 32).
+# Ghost staging from random ghost seeds: ghost-stage length 8-64 with 1, 2
+# or 4 parents per ghost iteration, DGS discard 0.5-0.75, iteration cap
+# itopk + 16 or 2 itopk + 32; 12 ghost iterations of 4 parents, discard
+# 0.75 and cap itopk + 16 reach recall@10 0.967 at 7.5M QPS (one parent per
+# ghost iteration needs 48 iterations for 0.968 at 6.9M; 8 iterations of 4
+# fall to 0.948). From the learned entry's seeds (4 or 8 ghost iterations,
+# discard 0.5 or 0.7): 4 ghost iterations and discard 0.5 reach 0.973 at
+# itopk 16, where discard 0.7 stops at 0.942.
+GHOST_ITERS = 12
+GHOST_WIDTH = 4
+DGS_DISCARD = 0.75
 DGS_DISCARD_LEARNED = 0.5
 
 
 def forms_for(spec):
     """Search configurations compared (each swept over itopk)."""
-    base = dict(k=10, search_width=1, dgs_cooldown=0.3, ghost_max_iters=GHOST_ITERS)
+    base = dict(k=10, search_width=1, dgs_cooldown=0.3, ghost_max_iters=GHOST_ITERS, ghost_search_width=GHOST_WIDTH)
     return {
         # the paper's method: ghost staging + DGS, FP32 storage (headline)
         "paper_fp32": dict(storage=0, entry=1, dgs_discard=DGS_DISCARD, rerank=0, **base),
@@ -621,8 +623,9 @@ def run_ours(args):
         "config": {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "nq": nq,
                    "form": headline, "k": 10, "itopk": L, "search_width": 1, "max_iters": p["max_iters"],
                    "entry": ("random", "ghost", "learned")[form["entry"]], "ghost_n": spec.ghost_n,
-                   "ghost_max_iters": form["ghost_max_iters"], "dgs_discard": form["dgs_discard"],
-                   "dgs_cooldown": form["dgs_cooldown"], "storage": ("f32", "f16", "e4m3")[form["storage"]],
+                   "ghost_max_iters": form["ghost_max_iters"], "ghost_search_width": form["ghost_search_width"],
+                   "dgs_discard": form["dgs_discard"], "dgs_cooldown": form["dgs_cooldown"],
+                   "storage": ("f32", "f16", "e4m3")[form["storage"]],
                    "recall_at_10": head_recall, "recall_target": RECALL_TARGET,
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "parallelism": f"replicas x{world}"},
@@ -697,8 +700,9 @@ def run_reference(args):
             "config": {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree,
                        "nq": sample, "form": "paper_fp32", "k": 10, "itopk": chosen, "search_width": 1,
                        "max_iters": p["max_iters"], "entry": "ghost", "ghost_n": spec.ghost_n,
-                       "ghost_max_iters": form["ghost_max_iters"], "dgs_discard": form["dgs_discard"],
-                       "dgs_cooldown": form["dgs_cooldown"], "storage": "f32", "recall_at_10": rec_at},
+                       "ghost_max_iters": form["ghost_max_iters"], "ghost_search_width": form["ghost_search_width"],
+                       "dgs_discard": form["dgs_discard"], "dgs_cooldown": form["dgs_cooldown"], "storage": "f32",
+                       "recall_at_10": rec_at},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{sample} queries per step of the {spec.nq}-query workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

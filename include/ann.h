@@ -75,6 +75,8 @@ typedef struct {
     uint32_t rerank;            /* 1: rescore the final queue on the FP32 originals (low precision) */
     uint64_t seed;              /* search RNG seed (splitmix64 counter stream) */
     uint64_t qid_base;          /* global index of query 0 of this call (RNG stream per query) */
+    uint32_t ghost_search_width; /* parents per ghost iteration, 1..ANN_MAX_WIDTH (0 or default: 1) */
+    uint32_t reserved;          /* must be 0 */
 } ann_search_params;
 
 /* Per-query event counters (exact counts of the work done). */

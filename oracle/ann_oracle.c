@@ -291,6 +291,8 @@ typedef struct {
     uint32_t rerank;        /* 1: rescore the final queue against the FP32 originals */
     uint64_t seed;
     uint64_t qid_base;      /* global index of query 0 of this call */
+    uint32_t Wg;            /* parents per ghost iteration */
+    uint32_t reserved;
 } oracle_params;
 
 typedef struct {
@@ -454,7 +456,7 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
     uint64_t qid = p->qid_base + qi;
     oracle_counters cn = {0};
     uint32_t m = p->m ? p->m : p->W * ix->deg;
-    uint64_t cap = (uint64_t)p->L + (uint64_t)p->W * ix->deg + m + p->Lg + ix->deg_g + c->P + 16;
+    uint64_t cap = (uint64_t)p->L + (uint64_t)p->W * ix->deg + m + p->Lg + (uint64_t)p->Wg * ix->deg_g + c->P + 16;
     or_state st;
     st.buf = (or_entry *)malloc(sizeof(or_entry) * cap);
     st.tmp = (or_entry *)malloc(sizeof(or_entry) * cap);
@@ -486,7 +488,7 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
         memcpy(st.buf, st.tmp, sizeof(or_entry) * st.cnt);
     } else {
         /* Ghost staging (Section 3.2.2): search the ghost graph first, from
-         * random ghost nodes or from given ones, with width 1 and no DGS. */
+         * random ghost nodes or from given ones, with width Wg and no DGS. */
         or_graph gg = {ix->nS, ix->d, ix->deg_g, ix->Xs, ix->S, ix->Gg, NULL};
         uint8_t *gvis = (uint8_t *)calloc(ix->nS / 8 + 1, 1);
         or_state gs = {st.buf, 0, st.tmp, gvis};
@@ -515,7 +517,7 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
         gs.cnt = nc < p->Lg ? nc : p->Lg;
         memcpy(gs.buf, st.tmp, sizeof(or_entry) * gs.cnt);
         uint64_t no_dgs = 0;
-        or_iterate(&gg, q, &gs, p->Lg, 1, Tg, ix->deg_g, 0, 0,
+        or_iterate(&gg, q, &gs, p->Lg, p->Wg ? p->Wg : 1, Tg, ix->deg_g, 0, 0,
                    &cn.ghost_iters, &cn.ghost_parents, &no_dgs, &cn.ghost_vec_rows);
         /* Transition: the top g ghost results, as base ids with their
          * distances, become the base queue; only they are marked visited. */

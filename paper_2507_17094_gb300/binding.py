@@ -46,7 +46,8 @@ class SearchParams(C.Structure):
                 ("dgs_cooldown", C.c_float), ("dgs_reexpand", C.c_uint32), ("entry", C.c_uint32),
                 ("ghost_itopk", C.c_uint32), ("ghost_max_iters", C.c_uint32),
                 ("ghost_max_iters_given", C.c_uint32), ("ghost_seeds_out", C.c_uint32),
-                ("rerank", C.c_uint32), ("seed", C.c_uint64), ("qid_base", C.c_uint64)]
+                ("rerank", C.c_uint32), ("seed", C.c_uint64), ("qid_base", C.c_uint64),
+                ("ghost_search_width", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class ServerConfig(C.Structure):

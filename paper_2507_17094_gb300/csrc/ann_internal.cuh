@@ -71,7 +71,7 @@ inline uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
 
 // Per-query search parameters (derived from ann_search_params).
 struct QParams {
-    uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank, n_given, pad;
+    uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank, n_given, Wg;
     uint64_t seed, qid_base;
 };
 

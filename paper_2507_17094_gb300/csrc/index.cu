@@ -263,6 +263,7 @@ void ann_default_params(ann_search_params *p)
     p->dgs_cooldown = 0.3f;
     p->ghost_max_iters = 16;
     p->ghost_max_iters_given = 4;
+    p->ghost_search_width = 1;
 }
 
 ann_status ann_encode(const float *x, uint64_t n, uint32_t dim, ann_storage storage, void *codes, float *scales,

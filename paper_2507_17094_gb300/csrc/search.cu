@@ -732,7 +732,7 @@ struct WarpSearch {
                               qp.seed, stage ? 0 : kGhostTag, lcap, rows);
             }
             if (ok)
-                ok = iterate<ST>(v, lcap, stage ? qp.W : 1, stage ? qp.T : (given ? qp.Tg_given : qp.Tg),
+                ok = iterate<ST>(v, lcap, stage ? qp.W : qp.Wg, stage ? qp.T : (given ? qp.Tg_given : qp.Tg),
                                  stage ? qp.n_keep : v.deg, stage ? qp.it_cool : 0, stage ? qp.reexpand : 0, iters,
                                  parents, dgs_parents, rows);
             if (stage) {
@@ -958,6 +958,11 @@ ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint3
         set_error("ann_search: ghost_itopk > %u", ANN_MAX_ITOPK);
         return ANN_EINVAL;
     }
+    const uint32_t Wg = p->ghost_search_width ? p->ghost_search_width : 1;
+    if (Wg > ANN_MAX_WIDTH || p->reserved) {
+        set_error("ann_search: ghost_search_width must be <= %u (and reserved 0)", ANN_MAX_WIDTH);
+        return ANN_EINVAL;
+    }
     QParams q{};
     q.n_given = n_given;
     q.k = p->k;
@@ -980,6 +985,7 @@ ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint3
     q.Lg = Lg;
     q.Tg = p->ghost_max_iters;
     q.Tg_given = p->ghost_max_iters_given;
+    q.Wg = Wg;
     q.g = p->ghost_seeds_out ? p->ghost_seeds_out : Lg;
     q.rerank = p->rerank ? 1 : 0;
     q.seed = p->seed;
@@ -1007,10 +1013,10 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     a.qp = q;
     const uint32_t cap_buf = std::max(q.L, q.entry != ANN_ENTRY_RANDOM ? q.Lg : 1u);
     uint32_t cap_cand = std::max(q.W * deg, 32u);
-    if (q.entry != ANN_ENTRY_RANDOM) cap_cand = std::max(cap_cand, ix->ghost_degree);
+    if (q.entry != ANN_ENTRY_RANDOM) cap_cand = std::max(cap_cand, q.Wg * ix->ghost_degree);
     cap_cand = round_up(cap_cand, 32);
     a.cap_cand = cap_cand;
-    const uint32_t adj_words = std::max(q.W * ix->deg_pad, ix->gdeg_pad);
+    const uint32_t adj_words = std::max(q.W * ix->deg_pad, q.Wg * ix->gdeg_pad);
     const bool dgs = q.n_keep < deg;
     const uint32_t dir_words = dgs ? q.W * ix->deg_pad * ix->words : 0;
     a.prow_bytes = ix->row_bytes;

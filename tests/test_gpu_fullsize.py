@@ -66,16 +66,16 @@ def check_sample(ds, storage, g_ids, g_d, idx, params, recall_min):
 
 def test_scale_1m_bench_configuration():
     """Workload 2 (1M x 96, degree 64, 10,000 queries) at the benchmark's
-    headline setting (ghost staging with 48 ghost iterations + DGS with
-    discard 0.7, FP32, itopk 32, 48 iterations) and at the paper's discard
-    0.5 with 64 ghost and 96 base iterations."""
+    headline setting (ghost staging with 12 ghost iterations of 4 parents +
+    DGS with discard 0.75, FP32, itopk 32, 48 iterations) and at the paper's
+    discard 0.5 with 64 one-parent ghost and 96 base iterations."""
     import paper_2507_17094_gb300 as A
     from workloads import CONFIGS, load_dataset
     ds = load_dataset(CONFIGS[2], device="cuda")
     ix = A.Index(ds.X, ds.G, storage=A.F32, ghost_ids=ds.S, ghost_graph=ds.Gg)
-    for rho, tg, T in ((0.7, 48, 48), (0.5, 64, 96)):
+    for rho, tg, wg, T in ((0.75, 12, 4, 48), (0.5, 64, 1, 96)):
         p = dict(k=10, itopk=32, search_width=1, max_iters=T, entry=1, dgs_discard=rho, dgs_cooldown=0.3,
-                 ghost_max_iters=tg, seed=4002)
+                 ghost_max_iters=tg, ghost_search_width=wg, seed=4002)
         g_ids, g_d, st = gpu_search(ix, ds.Q, **p)
         assert (st["status"] == 0).all()
         check_sample(ds, O.F32, g_ids, g_d, sample_rows(len(ds.Q), 300, 1), p, 0.95)

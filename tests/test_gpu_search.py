@@ -92,6 +92,8 @@ TINY_PARAMS = [
     dict(itopk=512, k=100, max_iters=600, search_width=8, entry=1, ghost_itopk=100, ghost_seeds_out=7),
     dict(itopk=64, max_iters=0),                                              # seeds only
     dict(itopk=64, max_iters=0, entry=1),                                     # ghost stage only
+    dict(itopk=32, max_iters=48, entry=1, dgs_discard=0.7, ghost_search_width=2, ghost_max_iters=24),
+    dict(itopk=64, max_iters=64, entry=1, ghost_search_width=4, ghost_itopk=48),
 ]
 
 

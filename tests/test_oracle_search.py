@@ -133,6 +133,13 @@ def test_ghost_stage_over_whole_graph_is_brute_force(int_data):
     ids0, _, cnt0 = O.search(ix, Q, k=10, itopk=512, max_iters=0, entry=1, ghost_itopk=512,
                              ghost_max_iters=2000, seed=5)
     assert np.array_equal(ids0, gt) and (cnt0["iters"] == 0).all()
+    # a ghost stage with several parents per iteration reaches the same exact
+    # answer in fewer iterations
+    ids3, _, cnt3 = O.search(ix, Q, k=10, itopk=512, max_iters=0, entry=1, ghost_itopk=512,
+                             ghost_max_iters=2000, seed=5, ghost_search_width=3)
+    assert np.array_equal(ids3, gt) and (cnt3["ghost_vec_rows"] == n).all()
+    assert (cnt3["ghost_iters"] < cnt0["ghost_iters"]).all()
+    assert (cnt3["ghost_parents"] <= 3 * cnt3["ghost_iters"]).all()
 
 
 def test_given_ghost_seeds_and_fallback(int_data):
