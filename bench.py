@@ -178,13 +178,16 @@ class ClockSampler:
 # itopk + 16 or 2 itopk + 32; 12 ghost iterations of 4 parents, discard
 # 0.75 and cap itopk + 16 reach recall@10 0.967 at 7.5M QPS (one parent per
 # ghost iteration needs 48 iterations for 0.968 at 6.9M; 8 iterations of 4
-# fall to 0.948). From the learned entry's seeds (4 or 8 ghost iterations,
-# discard 0.5 or 0.7): 4 ghost iterations and discard 0.5 reach 0.973 at
-# itopk 16, where discard 0.7 stops at 0.942.
+# fall to 0.948). From the learned entry's seeds (2 or 4 ghost iterations of
+# 1, 2 or 4 parents, discard 0.5 or 0.6, itopk 16): 2 iterations of one
+# parent and discard 0.5 reach 0.967 at 9.8M QPS with the prediction
+# included (4 parents: 9.0M); the few queries below the confidence
+# threshold fall back to one-parent ghost staging of 48 iterations.
 GHOST_ITERS = 12
 GHOST_WIDTH = 4
 DGS_DISCARD = 0.75
 DGS_DISCARD_LEARNED = 0.5
+LEARNED = dict(dgs_discard=DGS_DISCARD_LEARNED, ghost_max_iters_given=2, ghost_max_iters=48, ghost_search_width=1)
 
 
 def forms_for(spec):
@@ -199,11 +202,9 @@ def forms_for(spec):
         "f16_rerank": dict(storage=1, entry=1, dgs_discard=DGS_DISCARD, rerank=1, **base),
         "e4m3_rerank": dict(storage=2, entry=1, dgs_discard=DGS_DISCARD, rerank=1, **base),
         # low precision + learned entry: the MLP's top-8 ghost nodes seed a
-        # 4-iteration ghost stage (fallback to ghost staging below tau)
-        "f16_learned": dict(storage=1, entry=2, dgs_discard=DGS_DISCARD_LEARNED, rerank=1, ghost_max_iters_given=4,
-                            **base),
-        "e4m3_learned": dict(storage=2, entry=2, dgs_discard=DGS_DISCARD_LEARNED, rerank=1, ghost_max_iters_given=4,
-                             **base),
+        # 2-iteration ghost stage (fallback to ghost staging below tau)
+        "f16_learned": dict(base, storage=1, entry=2, rerank=1, **LEARNED),
+        "e4m3_learned": dict(base, storage=2, entry=2, rerank=1, **LEARNED),
     }
 
 
