@@ -355,13 +355,13 @@ def recall_at(ann_ids: np.ndarray, gt_dists: np.ndarray, X: np.ndarray, Q: np.nd
 def run_ours(args):
     import torch
     import paper_2507_17094_gb300 as A
-    from workloads import CONFIGS, load_dataset
+    from workloads import WORKLOADS, load_dataset
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dist = dist_init(world, "nccl")
     dev = torch.device("cuda", local)
-    spec = CONFIGS[args.workload]
+    spec = WORKLOADS[args.workload]
     if args.nq:
         import dataclasses
         spec = dataclasses.replace(spec, nq=args.nq)
@@ -657,8 +657,8 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle as O
-    from workloads import CONFIGS, load_dataset
-    spec = CONFIGS[args.workload]
+    from workloads import WORKLOADS, load_dataset
+    spec = WORKLOADS[args.workload]
     if args.nq:
         import dataclasses
         spec = dataclasses.replace(spec, nq=args.nq)

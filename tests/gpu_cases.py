@@ -10,7 +10,7 @@ import functools
 import numpy as np
 
 import oracle as O
-from workloads import CONFIGS, build_graph, ghost_sample, make_queries
+from workloads import WORKLOADS, build_graph, ghost_sample, make_queries
 
 # Distances are FP32 on both sides, one fused multiply-add per element into
 # four interleaved partial sums combined pairwise, so the expected agreement
@@ -85,7 +85,7 @@ def assert_parity(g, o, counters=True):
 def tiny_case():
     """Workload 1 as specified: 10,000 x 128 FP32, 50 clusters, degree 32,
     100 queries, ghost set 1% (100 nodes) with a degree-16 graph."""
-    s = CONFIGS[1]
+    s = WORKLOADS[1]
     X, _ = s.mixture().sample(s.n, s.seeds["base"])
     G = build_graph(X, s.degree, s.knn_k, s.graph)
     S = ghost_sample(s.n, s.ghost_n, s.seeds["ghost"])
@@ -110,7 +110,7 @@ def ragged_case(n=3000, d=40, deg=12, nq=77, gdeg=6, seed=7):
 def int_case(n=4000, d=128, deg=16, nq=64, seed=9):
     """Integer data in [0, 255] (the precision workload's recipe): many exact
     distance ties, FP16 storage exact."""
-    s = CONFIGS[3].scaled(n, nq=nq, n_clusters=20)
+    s = WORKLOADS[3].scaled(n, nq=nq, n_clusters=20)
     X, _ = s.mixture().sample(n, s.seeds["base"])
     Q = make_queries(s)
     G = build_graph(X, deg, 2 * deg, "exact")

@@ -70,8 +70,8 @@ def test_scale_1m_bench_configuration():
     DGS with discard 0.75, FP32, itopk 32, 48 iterations) and at the paper's
     discard 0.5 with 64 one-parent ghost and 96 base iterations."""
     import paper_2507_17094_gb300 as A
-    from workloads import CONFIGS, load_dataset
-    ds = load_dataset(CONFIGS[2], device="cuda")
+    from workloads import WORKLOADS, load_dataset
+    ds = load_dataset(WORKLOADS[2], device="cuda")
     ix = A.Index(ds.X, ds.G, storage=A.F32, ghost_ids=ds.S, ghost_graph=ds.Gg)
     for rho, tg, wg, T in ((0.75, 12, 4, 48), (0.5, 64, 1, 96)):
         p = dict(k=10, itopk=32, search_width=1, max_iters=T, entry=1, dgs_discard=rho, dgs_cooldown=0.3,
@@ -87,8 +87,8 @@ def test_precision_10m(storage, k, itopk):
     """Workload 3 (10M x 128 integers, degree 32): FP16 and E4M3 storage with
     FP32 rerank, k = 10 and k = 100."""
     import paper_2507_17094_gb300 as A
-    from workloads import CONFIGS, load_dataset
-    ds = load_dataset(CONFIGS[3], device="cuda")
+    from workloads import WORKLOADS, load_dataset
+    ds = load_dataset(WORKLOADS[3], device="cuda")
     ix = A.Index(ds.X, ds.G, storage=storage, ghost_ids=ds.S, ghost_graph=ds.Gg)
     p = dict(k=k, itopk=itopk, max_iters=2 * itopk + 32, entry=1, dgs_discard=0.5, ghost_max_iters=64,
              rerank=1, seed=4003)
@@ -108,8 +108,8 @@ def test_learned_entry_5m():
     plain ghost staging on 10,000 held-out queries (20% between clusters)."""
     import paper_2507_17094_gb300 as A
     from paper_2507_17094_gb300.entry import LearnedEntry, ghost_labels
-    from workloads import CONFIGS, init_mlp_params, load_dataset, make_queries
-    spec = CONFIGS[4]
+    from workloads import WORKLOADS, init_mlp_params, load_dataset, make_queries
+    spec = WORKLOADS[4]
     ds = load_dataset(spec, off_fraction=0.2, device="cuda")
     ix = A.Index(ds.X, ds.G, storage=A.F16, ghost_ids=ds.S, ghost_graph=ds.Gg)
     Qtr = torch.from_numpy(make_queries(spec, nq=200_000, seed=spec.seeds["query"] + 100)).cuda()
@@ -150,8 +150,8 @@ def test_serving_20m_poisson():
     1-4,096 queries with k in {10, 100} and itopk in {64, 256}, ghost staging
     + FP16 distances + rerank; sampled requests match the batch search."""
     import paper_2507_17094_gb300 as A
-    from workloads import CONFIGS, load_dataset
-    spec = CONFIGS[5]
+    from workloads import WORKLOADS, load_dataset
+    spec = WORKLOADS[5]
     ds = load_dataset(spec, device="cuda")
     ix = A.Index(ds.X, ds.G, storage=A.F16, ghost_ids=ds.S, ghost_graph=ds.Gg)
     srv = A.Server(ix, capacity=32768, max_requests=64,

@@ -16,10 +16,10 @@ torch = pytest.importorskip("torch")
 @pytest.fixture(scope="module")
 def setup():
     import paper_2507_17094_gb300 as A
-    from workloads import CONFIGS, build_graph, ghost_sample, make_queries
+    from workloads import WORKLOADS, build_graph, ghost_sample, make_queries
     assert torch.cuda.is_available()
     A.build()
-    spec = dataclasses.replace(CONFIGS[2].scaled(200_000, nq=2000, n_clusters=200, ghost_n=2000))
+    spec = dataclasses.replace(WORKLOADS[2].scaled(200_000, nq=2000, n_clusters=200, ghost_n=2000))
     X, _ = spec.mixture().sample(spec.n, spec.seeds["base"])
     G = build_graph(X, spec.degree, spec.knn_k, "partitioned", n_parts=200, seed=1)
     S = ghost_sample(spec.n, spec.ghost_n, spec.seeds["ghost"])

@@ -12,10 +12,10 @@ torch = pytest.importorskip("torch")
 @pytest.fixture(scope="module")
 def served():
     import paper_2507_17094_gb300 as A
-    from workloads import CONFIGS, build_graph, ghost_sample, make_queries
+    from workloads import WORKLOADS, build_graph, ghost_sample, make_queries
     assert torch.cuda.is_available()
     A.build()
-    spec = CONFIGS[2].scaled(50_000, nq=4000, n_clusters=50, ghost_n=500)
+    spec = WORKLOADS[2].scaled(50_000, nq=4000, n_clusters=50, ghost_n=500)
     X, _ = spec.mixture().sample(spec.n, spec.seeds["base"])
     G = build_graph(X, 32, 64, "partitioned", n_parts=50, seed=1)
     S = ghost_sample(spec.n, spec.ghost_n, spec.seeds["ghost"])

@@ -1,11 +1,11 @@
 """The input generators are deterministic and produce well-formed graphs."""
 import numpy as np
 
-from workloads import CONFIGS, build_graph, ghost_sample, make_queries
+from workloads import WORKLOADS, build_graph, ghost_sample, make_queries
 
 
 def test_mixture_is_seeded_and_shaped():
-    s = CONFIGS[2].scaled(5000, nq=50, n_clusters=20, ghost_n=50)
+    s = WORKLOADS[2].scaled(5000, nq=50, n_clusters=20, ghost_n=50)
     a, _ = s.mixture().sample(s.n, s.seeds["base"])
     b, _ = s.mixture().sample(s.n, s.seeds["base"])
     assert a.shape == (5000, 96) and a.dtype == np.float32 and np.array_equal(a, b)
@@ -15,13 +15,13 @@ def test_mixture_is_seeded_and_shaped():
 
 
 def test_integer_recipe():
-    s = CONFIGS[3].scaled(2000, nq=10, n_clusters=10)
+    s = WORKLOADS[3].scaled(2000, nq=10, n_clusters=10)
     x, _ = s.mixture().sample(s.n, s.seeds["base"])
     assert x.min() >= 0 and x.max() <= 255 and np.array_equal(x, np.rint(x))
 
 
 def test_graph_is_fixed_degree_without_self_loops_or_duplicates():
-    s = CONFIGS[1]
+    s = WORKLOADS[1]
     x, _ = s.mixture().sample(3000, s.seeds["base"])
     g = build_graph(x, 16, 32, "exact", device="cpu")
     assert g.shape == (3000, 16) and g.dtype == np.uint32

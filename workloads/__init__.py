@@ -9,12 +9,12 @@ the method (the paper assumes it pre-constructed, Section 2.1), so its builder
 lives here too.
 """
 
-from .mixtures import Mixture, CONFIGS, WorkloadSpec, make_mixture, make_queries, init_mlp_params
+from .mixtures import Mixture, WORKLOADS, WorkloadSpec, make_mixture, make_queries, init_mlp_params
 from .graph import knn_exact, knn_partitioned, prune_by_detours, build_graph, ghost_sample
 from .dataset import Dataset, load_dataset, write_index_file, cache_dir
 
 __all__ = [
-    "Mixture", "CONFIGS", "WorkloadSpec", "make_mixture", "make_queries", "init_mlp_params",
+    "Mixture", "WORKLOADS", "WorkloadSpec", "make_mixture", "make_queries", "init_mlp_params",
     "knn_exact", "knn_partitioned", "prune_by_detours", "build_graph", "ghost_sample",
     "Dataset", "load_dataset", "write_index_file", "cache_dir",
 ]

@@ -145,7 +145,7 @@ class WorkloadSpec:
 # (measured: U[0,100]^96 recall <= 0.93 at itopk 64 on workload 2;
 # U[0,255]^128 with spread 16, recall 0.86-0.89 at itopk 128 on workload 3;
 # U[0,100]^256, recall 0.39 on workload 4).
-CONFIGS = {
+WORKLOADS = {
     1: WorkloadSpec(1, "tiny-10k-128d", 10_000, 128, 50, 100, 32, 64, "exact", 100, 16,
                     sigma=8.0, search=dict(k=10, itopk=64, search_width=1, max_iters=64)),
     2: WorkloadSpec(2, "scale-1M-96d", 1_000_000, 96, 1000, 10_000, 64, 96, "partitioned",
