@@ -133,23 +133,33 @@ __device__ __forceinline__ float stored_elem(const uint8_t *row, uint32_t i, flo
     return __fmul_rn(scale, __half2float(__half(h)));
 }
 
+// rn(y - x) and rn(acc + df * df) for two elements at once with the packed
+// FP32 pipe: fma(x, -1, y) rounds y - x once, so both results equal the
+// scalar __fsub_rn / __fmaf_rn of each component.
+__device__ __forceinline__ void step2(float2 y, float2 x, float2 &acc)
+{
+    const float2 df = __ffma2_rn(x, make_float2(-1.0f, -1.0f), y);
+    acc = __ffma2_rn(df, df, acc);
+}
+
 // Half of the squared L2 between a staged row and the query (both in
 // shared memory). The distance keeps four partial sums, element i (in index
 // order) fused into sum i mod 4, and is (s0 + s1) + (s2 + s3); half h of the
 // lane pair of a row computes s_{2h} + s_{2h+1}, so one more add of the two
-// halves gives the distance and each lane does half the elements.
+// halves gives the distance and each lane does half the elements. The two
+// sums of a lane are one float2, updated with packed FP32 instructions.
 template <int ST>
 __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *q, float scale, uint32_t d,
                                                uint32_t h)
 {
-    float sa = 0.0f, sb = 0.0f;  // s_{2h}, s_{2h+1}
+    float2 s = make_float2(0.0f, 0.0f);  // s_{2h}, s_{2h+1}
+    const float2 sc = make_float2(scale, scale);
     uint32_t i = 0;
     if (ST == ANN_F32) {
         for (; i + 4 <= d; i += 4) {
             const float2 x = *reinterpret_cast<const float2 *>(row + (size_t)(i + 2 * h) * 4);
             const float2 y = *reinterpret_cast<const float2 *>(q + i + 2 * h);
-            step(y.x, x.x, sa);
-            step(y.y, x.y, sb);
+            step2(y, x, s);
         }
     } else if (ST == ANN_F16) {
         for (; i + 8 <= d; i += 8) {
@@ -157,10 +167,8 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
             for (uint32_t g = 0; g < 2; ++g) {
                 const uint32_t e = i + 4 * g + 2 * h;
                 const __half2 hv = *reinterpret_cast<const __half2 *>(row + (size_t)e * 2);
-                const float2 f = __half22float2(hv);
                 const float2 y = *reinterpret_cast<const float2 *>(q + e);
-                step(y.x, __fmul_rn(scale, f.x), sa);
-                step(y.y, __fmul_rn(scale, f.y), sb);
+                step2(y, __fmul2_rn(sc, __half22float2(hv)), s);
             }
         }
     } else {
@@ -171,19 +179,17 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
             for (uint32_t g = 0; g < 4; ++g) {
                 const __half2_raw pr =
                     __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((wds[g] >> (16 * h)) & 0xffffu), __NV_E4M3);
-                const float2 f = __half22float2(__half2(pr));
                 const float2 y = *reinterpret_cast<const float2 *>(q + i + 4 * g + 2 * h);
-                step(y.x, __fmul_rn(scale, f.x), sa);
-                step(y.y, __fmul_rn(scale, f.y), sb);
+                step2(y, __fmul2_rn(sc, __half22float2(__half2(pr))), s);
             }
         }
     }
     // tail (d not a multiple of the vector width); i is a multiple of 4 here
     for (; i < d; i += 4) {
-        if (i + 2 * h < d) step(q[i + 2 * h], stored_elem<ST>(row, i + 2 * h, scale), sa);
-        if (i + 2 * h + 1 < d) step(q[i + 2 * h + 1], stored_elem<ST>(row, i + 2 * h + 1, scale), sb);
+        if (i + 2 * h < d) step(q[i + 2 * h], stored_elem<ST>(row, i + 2 * h, scale), s.x);
+        if (i + 2 * h + 1 < d) step(q[i + 2 * h + 1], stored_elem<ST>(row, i + 2 * h + 1, scale), s.y);
     }
-    return __fadd_rn(sa, sb);
+    return __fadd_rn(s.x, s.y);
 }
 
 template <int ST>
@@ -567,9 +573,12 @@ struct WarpSearch {
             uint32_t qw[8];
 #pragma unroll
             for (uint32_t x = 0; x < 8; ++x) {
-                const uint32_t i = 32 * (t0 + x) + lane;
-                const bool bit = i < a.d && q()[min(i, a.d - 1)] > stored_elem<ST>(pr, min(i, a.d - 1), ps);
-                qw[x] = __ballot_sync(0xffffffffu, bit);
+                qw[x] = 0;
+                if (t0 + x < w) {   // uniform: the warp skips words past the dimension together
+                    const uint32_t i = 32 * (t0 + x) + lane;
+                    const bool bit = i < a.d && q()[min(i, a.d - 1)] > stored_elem<ST>(pr, min(i, a.d - 1), ps);
+                    qw[x] = __ballot_sync(0xffffffffu, bit);
+                }
             }
 #pragma unroll
             for (uint32_t r = 0; r < NW; ++r)
