@@ -547,76 +547,73 @@ struct WarpSearch {
 
     // DGS keep-mask of parent pi (bit r of the result: slot lane + 32 r is
     // kept). Score = matching sign bits; keep the top n_keep by (score desc,
-    // slot asc): find the threshold score t by binary search with ballots,
-    // keep scores above t and the first ties at t.
-    // NW = number of 32-slot words the degree spans (1, 2 or 4), so no
+    // slot asc): find the threshold score t by a radix select with ballots
+    // (most significant bit first), keep scores above t and the first ties
+    // at t. NW = number of 32-slot words the degree spans (1, 2 or 4), so no
     // ballot is spent on slots past the degree.
     template <uint32_t NW>
     __device__ uint32_t dgs_keep_nw(const View &v, uint32_t pi, uint32_t n_keep, float ps)
     {
         const uint32_t w = a.w, deg = v.deg;
         const uint8_t *pr = prow() + pi * a.prow_bytes;
-        // mismatching sign bits per slot, 8 words of the query's sign bits
+        // mismatching sign bits per slot, 4 words of the query's sign bits
         // relative to the parent ([q > x_parent], one ballot per 32
-        // dimensions) at a time, kept in registers
+        // dimensions) at a time. Words past w have no dimension (their bits
+        // are 0) and count nothing; the loads stay in the row (clamped), so
+        // a chunk has no branch and its loads issue together.
         int diff[NW];
         bool live[NW];
         const uint32_t *db[NW];
 #pragma unroll
         for (uint32_t r = 0; r < NW; ++r) {
-            const uint32_t j = lane + 32 * r;
-            live[r] = j < deg && adj()[pi * v.deg_pad + min(j, deg - 1)] != ANN_INVALID_ID;
-            db[r] = dirs() + (pi * v.deg_pad + min(j, deg - 1)) * w;
+            const uint32_t j = min(lane + 32 * r, deg - 1);
+            live[r] = lane + 32 * r < deg && adj()[pi * v.deg_pad + j] != ANN_INVALID_ID;
+            db[r] = dirs() + (pi * v.deg_pad + j) * w;
             diff[r] = 0;
         }
-        for (uint32_t t0 = 0; t0 < w; t0 += 8) {
-            uint32_t qw[8];
+        for (uint32_t t0 = 0; t0 < w; t0 += 4) {
+            uint32_t qw[4];
 #pragma unroll
-            for (uint32_t x = 0; x < 8; ++x) {
-                qw[x] = 0;
-                if (t0 + x < w) {   // uniform: the warp skips words past the dimension together
-                    const uint32_t i = 32 * (t0 + x) + lane;
-                    const bool bit = i < a.d && q()[min(i, a.d - 1)] > stored_elem<ST>(pr, min(i, a.d - 1), ps);
-                    qw[x] = __ballot_sync(0xffffffffu, bit);
-                }
+            for (uint32_t x = 0; x < 4; ++x) {
+                const uint32_t i = 32 * (t0 + x) + lane;
+                const uint32_t ic = min(i, a.d - 1);
+                qw[x] = __ballot_sync(0xffffffffu, i < a.d && q()[ic] > stored_elem<ST>(pr, ic, ps));
             }
 #pragma unroll
             for (uint32_t r = 0; r < NW; ++r)
 #pragma unroll
-                for (uint32_t x = 0; x < 8; ++x)
-                    if (t0 + x < w) diff[r] += __popc(qw[x] ^ db[r][t0 + x]);
+                for (uint32_t x = 0; x < 4; ++x) {
+                    const uint32_t dw = db[r][min(t0 + x, w - 1)];
+                    diff[r] += t0 + x < w ? __popc(qw[x] ^ dw) : 0;
+                }
         }
-        int sc[NW];
+        // u = score + 2: 0 past the degree (never kept), 1 for an empty
+        // slot, 2 + matching bits for a neighbour
+        uint32_t u[NW];
 #pragma unroll
         for (uint32_t r = 0; r < NW; ++r) {
             const uint32_t j = lane + 32 * r;
-            sc[r] = j >= deg ? -2 : (live[r] ? (int)a.d - diff[r] : -1);  // -2: never kept
+            u[r] = j >= deg ? 0u : (live[r] ? a.d + 2 - (uint32_t)diff[r] : 1u);
         }
-        // count(score >= lo) >= n_keep > count(score >= hi); hi starts one
-        // above the best score (warp reductions count across lanes)
-        int best = sc[0];
-#pragma unroll
-        for (uint32_t r = 1; r < NW; ++r) best = max(best, sc[r]);
-        int lo = -1, hi = (int)__reduce_max_sync(0xffffffffu, (uint32_t)(best + 2)) - 1;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
+        // radix select of the n_keep-th largest u: t collects its bits from
+        // the top; `need` counts how many of the values equal to t's bits so
+        // far are still to be kept. At the end every u > t is kept and
+        // `need` of the ties at t.
+        uint32_t t = 0, need = n_keep;
+        for (int bit = 31 - __clz(a.d + 2); bit >= 0; --bit) {
+            const uint32_t hi = (t >> bit) | 1u;
             uint32_t c = 0;
 #pragma unroll
-            for (uint32_t r = 0; r < NW; ++r) c += sc[r] >= mid ? 1u : 0u;
-            if (__reduce_add_sync(0xffffffffu, c) >= n_keep) lo = mid;
-            else hi = mid;
+            for (uint32_t r = 0; r < NW; ++r) c += __popc(__ballot_sync(0xffffffffu, (u[r] >> bit) == hi));
+            if (c >= need) t |= 1u << bit;
+            else need -= c;
         }
-        uint32_t above = 0;
-#pragma unroll
-        for (uint32_t r = 0; r < NW; ++r) above += sc[r] > lo ? 1u : 0u;
-        above = __reduce_add_sync(0xffffffffu, above);
-        const uint32_t need = n_keep - above;
         uint32_t keep = 0, ties_before = 0;
 #pragma unroll
         for (uint32_t r = 0; r < NW; ++r) {
-            const uint32_t tm = __ballot_sync(0xffffffffu, sc[r] == lo);
-            const bool tie_kept = sc[r] == lo && ties_before + __popc(tm & lanemask_lt()) < need;
-            if (sc[r] > lo || tie_kept) keep |= 1u << r;
+            const uint32_t tm = __ballot_sync(0xffffffffu, u[r] == t);
+            const bool tie_kept = u[r] == t && ties_before + __popc(tm & lanemask_lt()) < need;
+            if (u[r] > t || tie_kept) keep |= 1u << r;
             ties_before += __popc(tm);
         }
         return keep;
