@@ -147,7 +147,10 @@ __device__ __forceinline__ void step2(float2 y, float2 x, float2 &acc)
 // order) fused into sum i mod 4, and is (s0 + s1) + (s2 + s3); half h of the
 // lane pair of a row computes s_{2h} + s_{2h+1}, so one more add of the two
 // halves gives the distance and each lane does half the elements. The two
-// sums of a lane are one float2, updated with packed FP32 instructions.
+// sums of a lane are one float2, updated with packed FP32 instructions. The
+// loops unroll by two only: with 24 warps per SM spread over the whole
+// iteration, the kernel is bound by instruction fetch, and the compiler's
+// deeper unrolling cost 6% of throughput (measured on the 1M x 96 workload).
 template <int ST>
 __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *q, float scale, uint32_t d,
                                                uint32_t h)
@@ -156,12 +159,14 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
     const float2 sc = make_float2(scale, scale);
     uint32_t i = 0;
     if (ST == ANN_F32) {
+#pragma unroll 2
         for (; i + 4 <= d; i += 4) {
             const float2 x = *reinterpret_cast<const float2 *>(row + (size_t)(i + 2 * h) * 4);
             const float2 y = *reinterpret_cast<const float2 *>(q + i + 2 * h);
             step2(y, x, s);
         }
     } else if (ST == ANN_F16) {
+#pragma unroll 2
         for (; i + 8 <= d; i += 8) {
 #pragma unroll
             for (uint32_t g = 0; g < 2; ++g) {
@@ -172,6 +177,7 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
             }
         }
     } else {
+#pragma unroll 2
         for (; i + 16 <= d; i += 16) {
             const uint4 raw = *reinterpret_cast<const uint4 *>(row + i);
             const uint32_t wds[4] = {raw.x, raw.y, raw.z, raw.w};
@@ -371,12 +377,15 @@ struct WarpSearch {
             nc = kept;
         }
         if (nc == 0) return;
-        // 2. insertion point in the queue and rank among the candidates
+        // 2. insertion point in the queue and rank among the candidates (the
+        //    counting loops here and in step 3 unroll by two only, to keep the
+        //    kernel's code small: it is bound by instruction fetch)
         uint32_t min_lb = 0xffffffffu;
         for (uint32_t c = lane; c < nc; c += 32) {
             const float dd = kd[c];
             const uint32_t id = kid[c];
             uint32_t r = 0;
+#pragma unroll 2
             for (uint32_t c2 = 0; c2 < nc; ++c2) r += key_less(kd[c2], kid[c2], dd, id);
             uint32_t lo = 0, hi = cnt;
             while (lo < hi) {
@@ -401,6 +410,7 @@ struct WarpSearch {
                     dd = qd[b];
                     id = qi[b];
                     s = qs[b];
+#pragma unroll 2
                     for (uint32_t c = 0; c < nc; ++c) shift += (ks[c] & 0xffffu) <= (uint32_t)b;
                 }
                 __syncwarp();
@@ -487,30 +497,19 @@ struct WarpSearch {
     // Seeds (Step 2): given nodes (ids, the learned entry's ghost nodes;
     // invalid or out-of-range ids skipped) or, with ids NULL, m random nodes
     // deduplicated without redraw: node j is splitmix64(key ^ (qid << 32) ^ j)
-    // mod n, key = splitmix64(seed ^ tag).
-    template <int RST>
-    __device__ bool seed(const View &v, const uint32_t *ids, uint32_t m, uint64_t seed, uint64_t tag, uint32_t lcap,
-                         uint32_t &rows)
+    // mod n, key = splitmix64(seed ^ tag). Seeds [j0, j0 + chunk) that are
+    // new to the visited set become the candidates; returns their count.
+    __device__ uint32_t collect_seeds(const View &v, const uint32_t *ids, uint64_t key, uint32_t j0, uint32_t chunk)
     {
-        const uint64_t key = splitmix64(seed ^ tag);
-        for (uint32_t j0 = 0; j0 < m; j0 += a.cap_cand) {
-            const uint32_t chunk = min(a.cap_cand, m - j0);
-            hash_make_room(chunk);
-            uint32_t nc = 0;
-            for (uint32_t b = 0; b < chunk; b += 32) {
-                const uint32_t j = j0 + b + lane;
-                uint32_t id = kEmpty;
-                if (b + lane < chunk)
-                    id = ids ? __ldcg(ids + j) : (uint32_t)(splitmix64(key ^ (qid << 32) ^ (uint64_t)j) % v.n);
-                nc = collect(id < v.n, id, nc);
-            }
-            __syncwarp();
-            hash_count += nc;
-            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
-            rows += nc;
-            merge(nc, lcap);
+        uint32_t nc = 0;
+        for (uint32_t b = 0; b < chunk; b += 32) {
+            const uint32_t j = j0 + b + lane;
+            uint32_t id = kEmpty;
+            if (b + lane < chunk)
+                id = ids ? __ldcg(ids + j) : (uint32_t)(splitmix64(key ^ (qid << 32) ^ (uint64_t)j) % v.n);
+            nc = collect(id < v.n, id, nc);
         }
-        return true;
+        return nc;
     }
 
     // ---------------------------------------------------------- iterations
@@ -626,59 +625,74 @@ struct WarpSearch {
         return dgs_keep_nw<kMaxDegWords>(v, pi, n_keep, ps);
     }
 
-    // Steps 3-4 repeated, with DGS and its cool-down (Section 3.3.2).
+    // Step 2 (m seeds, in chunks of the candidate capacity), then Steps 3-4
+    // repeated with DGS and its cool-down (Section 3.3.2). Seed chunks and
+    // parent expansions share one loop body, so the distance and merge code
+    // exists once in the kernel (the kernel is bound by instruction fetch).
     template <int RST>
-    __device__ bool iterate(const View &v, uint32_t lcap, uint32_t W, uint32_t T, uint32_t n_keep,
-                            uint32_t it_cool, uint32_t reexpand, uint32_t &c_iters, uint32_t &c_parents,
-                            uint32_t &c_dgs, uint32_t &c_rows)
+    __device__ bool iterate(const View &v, const uint32_t *seed_ids, uint32_t m, uint64_t seed_key, uint32_t lcap,
+                            uint32_t W, uint32_t T, uint32_t n_keep, uint32_t it_cool, uint32_t reexpand,
+                            uint32_t &c_iters, uint32_t &c_parents, uint32_t &c_dgs, uint32_t &c_rows)
     {
         const uint32_t deg = v.deg;
         const bool dgs_on = v.dir != nullptr && n_keep < deg;
         const uint32_t w = a.w;
         bool cool = false;
-        for (uint32_t it = 0; it < T; ++it) {
-            if (dgs_on && it >= it_cool) cool = true;
-            uint32_t np = select_parents(W, cool);
-            if (np == 0 && dgs_on && reexpand && !cool && any_partial()) {
-                cool = true;
-                np = select_parents(W, cool);
-            }
-            if (np == 0) break;
-            ++c_iters;
-            const bool dgs_now = dgs_on && !cool;
-            // mark the parents; fetch adjacency (and, under DGS, direction
-            // and vector) rows in one bulk-copy round
-            const uint32_t adj_bytes = v.deg_pad * 4;
-            const uint32_t dir_bytes = v.deg_pad * w * 4;
-            uint32_t pid = 0;
-            float pscale = 1.0f;
-            if (lane < np) {
-                const uint32_t b = par()[lane];
-                pid = bi()[b];
-                bs()[b] = (dgs_now && reexpand) ? kPartial : kExpanded;
-            }
-            if (lane == 0) {
-                fence_proxy_async();
-                mbar_arrive_expect_tx(bar(), np * (adj_bytes + (dgs_now ? dir_bytes + v.row_bytes : 0)));
-            }
-            __syncwarp();
-            if (lane < np) {
-                bulk_g2s(adj() + lane * v.deg_pad, v.graph + (uint64_t)pid * v.deg_pad, adj_bytes, bar());
-                if (dgs_now) {
-                    bulk_g2s(dirs() + lane * v.deg_pad * w, v.dir + (uint64_t)pid * v.deg_pad * w, dir_bytes, bar());
-                    bulk_g2s(prow() + lane * a.prow_bytes, v.codes + (uint64_t)pid * v.row_bytes, v.row_bytes, bar());
-                    if (RST != ANN_F32) pscale = __ldg(v.scales + pid);
-                }
-            }
-            if (!wait_copies()) return false;
-            c_parents += np;
-            if (dgs_now) c_dgs += np;
-            hash_make_room(np * deg);
+        uint32_t j0 = 0, it = 0;
+        for (;;) {
             uint32_t nc = 0;
-            for (uint32_t pi = 0; pi < np; ++pi) {
-                uint32_t km = 0xffffffffu;
-                if (dgs_now) km = dgs_keep(v, pi, n_keep, __shfl_sync(0xffffffffu, pscale, pi));
-                nc = collect_row(v, pi, km, nc);
+            if (j0 < m) {
+                const uint32_t chunk = min(a.cap_cand, m - j0);
+                hash_make_room(chunk);
+                nc = collect_seeds(v, seed_ids, seed_key, j0, chunk);
+                j0 += chunk;
+            } else {
+                if (it == T) break;
+                if (dgs_on && it >= it_cool) cool = true;
+                uint32_t np = select_parents(W, cool);
+                if (np == 0 && dgs_on && reexpand && !cool && any_partial()) {
+                    cool = true;
+                    np = select_parents(W, cool);
+                }
+                if (np == 0) break;
+                ++it;
+                ++c_iters;
+                const bool dgs_now = dgs_on && !cool;
+                // mark the parents; fetch adjacency (and, under DGS, direction
+                // and vector) rows in one bulk-copy round
+                const uint32_t adj_bytes = v.deg_pad * 4;
+                const uint32_t dir_bytes = v.deg_pad * w * 4;
+                uint32_t pid = 0;
+                float pscale = 1.0f;
+                if (lane < np) {
+                    const uint32_t b = par()[lane];
+                    pid = bi()[b];
+                    bs()[b] = (dgs_now && reexpand) ? kPartial : kExpanded;
+                }
+                if (lane == 0) {
+                    fence_proxy_async();
+                    mbar_arrive_expect_tx(bar(), np * (adj_bytes + (dgs_now ? dir_bytes + v.row_bytes : 0)));
+                }
+                __syncwarp();
+                if (lane < np) {
+                    bulk_g2s(adj() + lane * v.deg_pad, v.graph + (uint64_t)pid * v.deg_pad, adj_bytes, bar());
+                    if (dgs_now) {
+                        bulk_g2s(dirs() + lane * v.deg_pad * w, v.dir + (uint64_t)pid * v.deg_pad * w, dir_bytes,
+                                 bar());
+                        bulk_g2s(prow() + lane * a.prow_bytes, v.codes + (uint64_t)pid * v.row_bytes, v.row_bytes,
+                                 bar());
+                        if (RST != ANN_F32) pscale = __ldg(v.scales + pid);
+                    }
+                }
+                if (!wait_copies()) return false;
+                c_parents += np;
+                if (dgs_now) c_dgs += np;
+                hash_make_room(np * deg);
+                for (uint32_t pi = 0; pi < np; ++pi) {
+                    uint32_t km = 0xffffffffu;
+                    if (dgs_now) km = dgs_keep(v, pi, n_keep, __shfl_sync(0xffffffffu, pscale, pi));
+                    nc = collect_row(v, pi, km, nc);
+                }
             }
             __syncwarp();
             hash_count += nc;
@@ -732,15 +746,14 @@ struct WarpSearch {
                 for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi()[i]);
                 __syncwarp();
                 hash_count = cnt;
-            } else {
-                const bool use_given = stage == 0 && given;
-                ok = seed<ST>(v, use_given ? given : nullptr, use_given ? qp.n_given : (stage ? qp.m : v.deg),
-                              qp.seed, stage ? 0 : kGhostTag, lcap, rows);
             }
-            if (ok)
-                ok = iterate<ST>(v, lcap, stage ? qp.W : qp.Wg, stage ? qp.T : (given ? qp.Tg_given : qp.Tg),
-                                 stage ? qp.n_keep : v.deg, stage ? qp.it_cool : 0, stage ? qp.reexpand : 0, iters,
-                                 parents, dgs_parents, rows);
+            const bool seeded = !(stage == 1 && ghost);
+            const bool use_given = stage == 0 && given;
+            ok = iterate<ST>(v, use_given ? given : nullptr,
+                             seeded ? (use_given ? qp.n_given : (stage ? qp.m : v.deg)) : 0,
+                             splitmix64(qp.seed ^ (stage ? 0 : kGhostTag)), lcap, stage ? qp.W : qp.Wg,
+                             stage ? qp.T : (given ? qp.Tg_given : qp.Tg), stage ? qp.n_keep : v.deg,
+                             stage ? qp.it_cool : 0, stage ? qp.reexpand : 0, iters, parents, dgs_parents, rows);
             if (stage) {
                 st.iters = iters;
                 st.parents = parents;
