@@ -10,23 +10,30 @@
 //     parents' adjacency / direction / vector rows and 16 staged rows, so 24
 //     warps share an SM and hide each other's memory latency;
 //   - the visited set of each warp is a 4,096-entry table in global memory
-//     (L2-resident, 16 KB per warp), probed with one atomicMax per lane;
+//     (L2-resident, 16 KB per warp), probed with one atomicCAS per lane; the
+//     ghost stage of a small ghost set uses an exact shared-memory bitmap;
 //   - every random global read (adjacency rows, direction rows, vector rows,
 //     FP32 rerank rows) is a 1-D TMA bulk copy into shared memory completing
 //     on the warp's mbarrier: one instruction per row, all rows of a round in
 //     flight together;
-//   - distances are computed lane-per-row from shared memory, one fused
-//     multiply-add per element into four interleaved partial sums, the same
-//     FP32 operations as the reference definition, so they agree bit for bit;
+//   - distances are computed by a lane pair per row from shared memory, one
+//     fused multiply-add per element into four interleaved partial sums, the
+//     same FP32 operations as the reference definition, so they agree bit
+//     for bit;
 //   - DGS needs the query's sign bits relative to each parent; they are
 //     recomputed from the parent's row, which arrives in the same bulk-copy
 //     round as its adjacency and direction rows (one ballot per 32 dims);
-//   - DGS keeps its top n neighbours by a ballot binary search on the score
+//   - DGS keeps its top n neighbours by a ballot radix select of the score
 //     threshold, not by sorting;
 //   - the merge works in place: candidates no better than the queue's last
 //     entry are dropped first, each survivor's slot is its rank among the
 //     candidates plus its insertion point in the queue, and only queue
-//     entries behind the first insertion point move.
+//     entries behind the first insertion point move;
+//   - the hot loop is kept small: with 24 warps per SM at different points
+//     of an iteration the kernel is bound by instruction fetch (instruction
+//     requests to the GPC cache near 80% of peak), so seeding shares the
+//     iteration's code and loops with run-time trip counts are not unrolled
+//     ("#pragma unroll 1"; measured +7% on the 1M x 96 workload).
 //
 // Visited set: open addressing with linear probing over entries id + 1 (0 =
 // empty) in the warp's table in global memory, zeroed at the start of each
@@ -191,6 +198,7 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
         }
     }
     // tail (d not a multiple of the vector width); i is a multiple of 4 here
+    #pragma unroll 1
     for (; i < d; i += 4) {
         if (i + 2 * h < d) step(q[i + 2 * h], stored_elem<ST>(row, i + 2 * h, scale), s.x);
         if (i + 2 * h + 1 < d) step(q[i + 2 * h + 1], stored_elem<ST>(row, i + 2 * h + 1, scale), s.y);
@@ -237,6 +245,7 @@ struct WarpSearch {
     __device__ bool hash_finish(uint32_t s, uint32_t want, uint32_t old)
     {
         const uint32_t mask = (1u << a.vbits) - 1;
+        #pragma unroll 1
         for (uint32_t probe = 0; probe <= mask; ++probe) {
             if (old == 0) return true;        // claimed an empty slot
             if (old == want) return false;    // found it
@@ -261,6 +270,7 @@ struct WarpSearch {
     __device__ void hash_clear()
     {
         if (gbm) {
+            #pragma unroll 1
             for (uint32_t i = lane; i < a.gbm_words; i += 32) gbits()[i] = 0;
             __syncwarp();
             hash_count = 0;
@@ -268,6 +278,7 @@ struct WarpSearch {
         }
         const uint32_t H = 1u << a.vbits;
         uint4 *t4 = reinterpret_cast<uint4 *>(vt);
+        #pragma unroll 1
         for (uint32_t i = lane; i < H / 4; i += 32) t4[i] = make_uint4(0, 0, 0, 0);
         __threadfence_block();
         __syncwarp();   // the lanes' zeroing precedes any lane's probes
@@ -279,6 +290,7 @@ struct WarpSearch {
     __device__ void hash_reset()
     {
         hash_clear();
+        #pragma unroll 1
         for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi()[i]);
         __syncwarp();
         hash_count = cnt;
@@ -313,6 +325,7 @@ struct WarpSearch {
                              uint32_t n, float *out)
     {
         const uint32_t R = a.stage_rows;
+        #pragma unroll 1
         for (uint32_t b0 = 0; b0 < n; b0 += R) {
             const uint32_t rows = min(R, n - b0);
             float scale = 1.0f;
@@ -354,6 +367,7 @@ struct WarpSearch {
             const float wd = qd[cnt - 1];
             const uint32_t wi = qi[cnt - 1];
             uint32_t kept = 0;
+            #pragma unroll 1
             for (uint32_t b = 0; b < nc; b += 32) {
                 const uint32_t c = b + lane;
                 float dd = 0.0f;
@@ -381,6 +395,7 @@ struct WarpSearch {
         //    counting loops here and in step 3 unroll by two only, to keep the
         //    kernel's code small: it is bound by instruction fetch)
         uint32_t min_lb = 0xffffffffu;
+        #pragma unroll 1
         for (uint32_t c = lane; c < nc; c += 32) {
             const float dd = kd[c];
             const uint32_t id = kid[c];
@@ -401,6 +416,7 @@ struct WarpSearch {
         // 3. shift queue entries [min_lb, cnt) by the number of candidates
         //    inserted before them, last chunk first (in place)
         if (cnt > min_lb) {
+            #pragma unroll 1
             for (int32_t top = (int32_t)cnt - 1; top >= (int32_t)min_lb; top -= 32) {
                 const int32_t b = top - (int32_t)lane;
                 float dd = 0.0f;
@@ -423,6 +439,7 @@ struct WarpSearch {
             }
         }
         // 4. candidates into their slots
+        #pragma unroll 1
         for (uint32_t c = lane; c < nc; c += 32) {
             const uint32_t pos = (ks[c] & 0xffffu) + (ks[c] >> 16);
             if (pos < lcap) {
@@ -471,6 +488,7 @@ struct WarpSearch {
     __device__ uint32_t collect_row(const View &v, uint32_t pi, uint32_t km, uint32_t nc)
     {
         if (gbm) {
+            #pragma unroll 1
             for (uint32_t r = 0; r * 32 < v.deg; ++r) {
                 const uint32_t j = lane + 32 * r;
                 const uint32_t nb = j < v.deg ? adj()[pi * v.deg_pad + j] : ANN_INVALID_ID;
@@ -479,6 +497,7 @@ struct WarpSearch {
             return nc;
         }
         if (v.deg <= 32) return collect_row_nw<1>(v, pi, km, 0, nc);
+        #pragma unroll 1
         for (uint32_t r0 = 0; r0 * 32 < v.deg; r0 += 2) nc = collect_row_nw<2>(v, pi, km, r0, nc);
         return nc;
     }
@@ -502,6 +521,7 @@ struct WarpSearch {
     __device__ uint32_t collect_seeds(const View &v, const uint32_t *ids, uint64_t key, uint32_t j0, uint32_t chunk)
     {
         uint32_t nc = 0;
+        #pragma unroll 1
         for (uint32_t b = 0; b < chunk; b += 32) {
             const uint32_t j = j0 + b + lane;
             uint32_t id = kEmpty;
@@ -518,6 +538,7 @@ struct WarpSearch {
     {
         uint32_t np = 0;
         const uint8_t *s8 = bs();
+        #pragma unroll 1
         for (uint32_t b = 0; b < cnt && np < W; b += 32) {
             const uint32_t i = b + lane;
             bool e = false;
@@ -540,6 +561,7 @@ struct WarpSearch {
     __device__ bool any_partial()
     {
         bool p = false;
+        #pragma unroll 1
         for (uint32_t i = lane; i < cnt; i += 32) p |= bs()[i] == kPartial;
         return __any_sync(0xffffffffu, p);
     }
@@ -716,6 +738,7 @@ struct WarpSearch {
         const uint32_t dpad = (a.d + 31) & ~31u;
         // read through L2 only: a serving ring rewrites query slots between
         // uses, and L1 is not kept coherent with those copies
+        #pragma unroll 1
         for (uint32_t i = lane; i < dpad; i += 32) q()[i] = i < a.d ? __ldcg(qg + i) : 0.0f;
         __syncwarp();
         const bool ghost = qp.entry != ANN_ENTRY_RANDOM;
@@ -735,6 +758,7 @@ struct WarpSearch {
                 // transition: the top g ghost results become the base queue;
                 // ghost ids are ascending, so the (dist, id) order carries over
                 const uint32_t g = min(min(qp.g, cnt), qp.L);
+                #pragma unroll 1
                 for (uint32_t i = lane; i < g; i += 32) {
                     bi()[i] = __ldg(a.ghost_ids + bi()[i]);
                     bs()[i] = kUnexpanded;
@@ -743,6 +767,7 @@ struct WarpSearch {
                 cnt = g;
                 gbm = false;   // the base stage's visited set is the global table
                 hash_clear();
+                #pragma unroll 1
                 for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi()[i]);
                 __syncwarp();
                 hash_count = cnt;
@@ -770,28 +795,33 @@ struct WarpSearch {
             ok = evaluate<ANN_F32>(a.x32, nullptr, a.row32_bytes, bi(), cnt, bd());
             st.rerank_rows += cnt;
             if (ok) {
+                #pragma unroll 1
                 for (uint32_t e = lane; e < cnt; e += 32) {
                     const float kd = bd()[e];
                     const uint32_t kid = bi()[e];
                     uint32_t r = 0;
+                    #pragma unroll 1
                     for (uint32_t e2 = 0; e2 < cnt; ++e2) r += key_less(bd()[e2], bi()[e2], kd, kid);
                     if (r < qp.k) {
                         oid[r] = kid;
                         odist[r] = kd;
                     }
                 }
+                #pragma unroll 1
                 for (uint32_t j = cnt + lane; j < qp.k; j += 32) {
                     oid[j] = ANN_INVALID_ID;
                     odist[j] = INFINITY;
                 }
             }
         } else if (ok) {
+            #pragma unroll 1
             for (uint32_t j = lane; j < qp.k; j += 32) {
                 oid[j] = j < cnt ? bi()[j] : ANN_INVALID_ID;
                 odist[j] = j < cnt ? bd()[j] : INFINITY;
             }
         }
         if (!ok) {
+            #pragma unroll 1
             for (uint32_t j = lane; j < qp.k; j += 32) {
                 oid[j] = ANN_INVALID_ID;
                 odist[j] = INFINITY;
