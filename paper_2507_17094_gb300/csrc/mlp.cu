@@ -259,10 +259,14 @@ __device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m,
                 tp.sm += cs * ex2_approx((cm - tp.mx) * kLog2e);
             }
         }
+        // most chunks hold nothing above the thread's P-th best: their max
+        // (cm) says so without a per-column test
         uint32_t pend = 0;
         const float th = tp.tv[TOPP - 1];
+        if (cm > th) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) pend |= (x[j] > th ? 1u : 0u) << j;
+            for (int j = 0; j < 32; ++j) pend |= (x[j] > th ? 1u : 0u) << j;
+        }
         if (__any_sync(0xffffffffu, pend != 0)) {
             if (pend) {
 #pragma unroll
