@@ -292,7 +292,7 @@ typedef struct {
     uint64_t seed;
     uint64_t qid_base;      /* global index of query 0 of this call */
     uint32_t Wg;            /* parents per ghost iteration */
-    uint32_t reserved;
+    uint32_t min_match;     /* > 0: DGS keeps the neighbours scoring >= min_match instead of the top n_keep */
 } oracle_params;
 
 typedef struct {
@@ -362,15 +362,18 @@ typedef struct {
  *  - DGS scores a parent's neighbours by matching sign bits against the
  *    query's sign bits relative to the parent and keeps the top n_keep
  *    (ties by adjacency position); dropped neighbours are not marked visited;
+ *  - with min_match > 0, DGS instead keeps every neighbour whose score is at
+ *    least min_match (the similarity-criterion pruning the paper names as an
+ *    alternative to a fixed top n in its comparison with static pruning);
  *  - the cool-down starts at it_cool, or earlier once only PARTIAL entries
  *    are left, and then stays on;
  *  - stop when no eligible parent is left or after T iterations. */
 static void or_iterate(const or_graph *g, const float *q, or_state *st, uint32_t L, uint32_t W, uint32_t T,
-                       uint32_t n_keep, uint32_t it_cool, uint32_t reexpand,
+                       uint32_t n_keep, uint32_t min_match, uint32_t it_cool, uint32_t reexpand,
                        uint64_t *c_iters, uint64_t *c_parents, uint64_t *c_dgs, uint64_t *c_rows)
 {
     uint32_t deg = g->deg, d = g->d, w = (d + 31) / 32;
-    int dgs_on = g->dir != NULL && n_keep < deg;
+    int dgs_on = g->dir != NULL && (min_match > 0 || n_keep < deg);
     int cool = 0;
     uint32_t par[64];
     int score[1024];
@@ -415,12 +418,16 @@ static void or_iterate(const or_graph *g, const float *q, or_state *st, uint32_t
                     for (uint32_t t = 0; t < w; ++t) diff += __builtin_popcount(qbits[t] ^ dr[t]);
                     score[j] = (int)d - diff;
                 }
-                /* rank j = #neighbours ahead of it (higher score, or equal and earlier) */
-                for (uint32_t j = 0; j < deg; ++j) {
-                    uint32_t rank = 0;
-                    for (uint32_t i = 0; i < deg; ++i)
-                        if (score[i] > score[j] || (score[i] == score[j] && i < j)) ++rank;
-                    keep[j] = rank < n_keep;
+                if (min_match > 0) {
+                    for (uint32_t j = 0; j < deg; ++j) keep[j] = score[j] >= (int)min_match;
+                } else {
+                    /* rank j = #neighbours ahead of it (higher score, or equal and earlier) */
+                    for (uint32_t j = 0; j < deg; ++j) {
+                        uint32_t rank = 0;
+                        for (uint32_t i = 0; i < deg; ++i)
+                            if (score[i] > score[j] || (score[i] == score[j] && i < j)) ++rank;
+                        keep[j] = rank < n_keep;
+                    }
                 }
             }
             for (uint32_t j = 0; j < deg; ++j) {
@@ -517,7 +524,7 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
         gs.cnt = nc < p->Lg ? nc : p->Lg;
         memcpy(gs.buf, st.tmp, sizeof(or_entry) * gs.cnt);
         uint64_t no_dgs = 0;
-        or_iterate(&gg, q, &gs, p->Lg, p->Wg ? p->Wg : 1, Tg, ix->deg_g, 0, 0,
+        or_iterate(&gg, q, &gs, p->Lg, p->Wg ? p->Wg : 1, Tg, ix->deg_g, 0, 0, 0,
                    &cn.ghost_iters, &cn.ghost_parents, &no_dgs, &cn.ghost_vec_rows);
         /* Transition: the top g ghost results, as base ids with their
          * distances, become the base queue; only they are marked visited. */
@@ -534,7 +541,7 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
         free(gvis);
     }
 
-    or_iterate(&base, q, &st, p->L, p->W, p->T, p->n_keep, p->it_cool, p->reexpand,
+    or_iterate(&base, q, &st, p->L, p->W, p->T, p->n_keep, p->min_match, p->it_cool, p->reexpand,
                &cn.iters, &cn.parents, &cn.dgs_parents, &cn.vec_rows);
 
     /* Output (Step 4's end): the top k; with rerank, the whole queue is
@@ -561,7 +568,7 @@ int oracle_search(const oracle_index *ix, const float *Q, uint32_t nq, const ora
                   oracle_counters *counters, int threads)
 {
     if (!ix || !p || p->k == 0 || p->L == 0 || p->k > p->L || p->W == 0 || p->W > 64 || ix->deg > 1024 ||
-        ix->d == 0 || ix->n == 0 || (ix->d + 31) / 32 > 64)
+        ix->d == 0 || ix->n == 0 || (ix->d + 31) / 32 > 64 || p->min_match > ix->d)
         return -1;
     search_ctx c = {ix, Q, p, given_ghost_seeds, P, ids, dists, counters};
     or_parallel(search_one, &c, nq, threads, 0);

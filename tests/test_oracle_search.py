@@ -5,7 +5,11 @@
 - the search degenerates to brute force when the queue can hold every node
   (itopk >= n) on a connected graph, with and without DGS re-expansion, and
   for the ghost stage when the ghost set is the whole graph;
-- DGS with discard 0 or cool-down 1.0 is the plain search, bit for bit.
+- DGS with discard 0 or cool-down 1.0 is the plain search, bit for bit;
+- DGS by a similarity threshold: a hand-built star whose neighbours agree
+  with the query in 8, 7, ..., 1 of 8 dimensions keeps exactly the ones at
+  or above ceil(f * d), and a threshold every neighbour meets is the plain
+  search.
 """
 import json
 import os
@@ -79,6 +83,7 @@ def int_data():
     dict(search_width=4),
     dict(dgs_discard=0.5, dgs_reexpand=1),
     dict(dgs_discard=0.75, dgs_reexpand=1, search_width=2),
+    dict(dgs_min_match=0.6, dgs_reexpand=1),
 ])
 def test_full_queue_equals_brute_force(int_data, kw):
     X, Q, G, gt, gd = int_data
@@ -188,3 +193,65 @@ def test_rejects_bad_arguments():
     ix = O.OracleIndex(X, G)
     with pytest.raises(ValueError):
         O.search(ix, X[:1], k=8, itopk=4)
+
+
+def _star_case():
+    """Node 0 at the origin with neighbours 1..8; neighbour j has 9 - j
+    coordinates +1 and the rest -1, so with q = (3, ..., 3) its direction
+    from node 0 agrees with the query's in exactly 9 - j of the 8
+    dimensions. Nodes 1..8 link back to node 0 only."""
+    d = 8
+    X = np.zeros((9, d), np.float32)
+    for j in range(1, 9):
+        X[j] = -1.0
+        X[j, :9 - j] = 1.0
+    G = np.zeros((9, 8), np.uint32)
+    G[0] = np.arange(1, 9)
+    Q = np.full((1, d), 3.0, np.float32)
+    # the seed that makes node 0 the single random seed of query 0
+    seed = next(s for s in range(1000) if O.splitmix64(O.splitmix64(s)) % 9 == 0)
+    return X, G, Q, seed
+
+
+@pytest.mark.parametrize("f,kept", [(1.0, [1]), (0.75, [1, 2, 3]), (0.5, [1, 2, 3, 4, 5]), (0.01, list(range(1, 9)))])
+def test_min_match_star_keeps_the_neighbours_at_or_above_the_threshold(f, kept):
+    X, G, Q, seed = _star_case()
+    ix = O.OracleIndex(X, G)
+    ids, dists, cnt = O.search(ix, Q, k=9, itopk=16, max_iters=1, num_seeds=1, seed=seed,
+                               dgs_min_match=f, dgs_cooldown=0.0)
+    # distance to q = (3, ..., 3): node 0: 72; neighbour j: 4 (9 - j) + 16 (j - 1)
+    expect = sorted([0] + kept, key=lambda j: 72 if j == 0 else 4 * (9 - j) + 16 * (j - 1))
+    got = [int(i) for i in ids[0] if i != O.INVALID]
+    assert got == expect
+    assert int(cnt["vec_rows"][0]) == 1 + len(kept) and int(cnt["dgs_parents"][0]) == 1
+    # the fixed top-n rule at discard 0.5 keeps four whatever their agreement
+    ids, _, cnt = O.search(ix, Q, k=9, itopk=16, max_iters=1, num_seeds=1, seed=seed,
+                           dgs_discard=0.5, dgs_cooldown=0.0)
+    assert int(cnt["vec_rows"][0]) == 1 + 4
+
+
+def test_min_match_met_by_every_neighbour_is_plain():
+    rng = np.random.default_rng(14)
+    n, d = 2000, 40
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Q = rng.standard_normal((50, d)).astype(np.float32)
+    G = _ring_graph(n, 16, rng)
+    # f = 0.01 asks for one agreeing dimension of 40; check on the data that
+    # no (query, parent, neighbour) agrees in none, so every neighbour passes
+    qbits = Q[:, None, :] > X[None, :, :]                  # query vs each parent
+    nbits = X[G] > X[:, None, :]                           # neighbour vs its parent
+    agree = (qbits[:, :, None, :] == nbits[None]).sum(-1)  # 50 x n x 16
+    assert agree.min() >= 1
+    base = O.search(ix := O.OracleIndex(X, G), Q, k=10, itopk=32, max_iters=80, seed=9)
+    got = O.search(ix, Q, k=10, itopk=32, max_iters=80, seed=9, dgs_min_match=0.01)
+    assert np.array_equal(got[0], base[0]) and np.array_equal(got[1], base[1])
+    assert np.array_equal(got[2]["vec_rows"], base[2]["vec_rows"])
+    assert (got[2]["dgs_parents"] > 0).all()
+
+
+def test_min_match_arguments():
+    X, G, Q, seed = _star_case()
+    ix = O.OracleIndex(X, G)
+    for kw in (dict(dgs_min_match=1.5), dict(dgs_min_match=-0.1), dict(dgs_min_match=0.5, dgs_discard=0.5)):
+        with pytest.raises(ValueError):
+            O.search(ix, Q, k=1, itopk=4, **kw)
