@@ -73,7 +73,9 @@ inline uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
 struct QParams {
     uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank, n_given, Wg;
     uint64_t seed, qid_base;
+    uint32_t min_match;   // > 0: DGS keeps the neighbours scoring >= min_match (not the top n_keep)
 };
+static_assert(sizeof(QParams) <= 96, "the serve kernel keeps a request's QParams in 96 bytes of shared memory");
 
 // One request in the serving ring (device memory).
 struct ServeReq {

@@ -570,10 +570,11 @@ struct WarpSearch {
     // kept). Score = matching sign bits; keep the top n_keep by (score desc,
     // slot asc): find the threshold score t by a radix select with ballots
     // (most significant bit first), keep scores above t and the first ties
-    // at t. NW = number of 32-slot words the degree spans (1, 2 or 4), so no
-    // ballot is spent on slots past the degree.
+    // at t. With min_match > 0, keep instead every neighbour scoring at
+    // least min_match. NW = number of 32-slot words the degree spans (1, 2
+    // or 4), so no ballot is spent on slots past the degree.
     template <uint32_t NW>
-    __device__ uint32_t dgs_keep_nw(const View &v, uint32_t pi, uint32_t n_keep, float ps)
+    __device__ uint32_t dgs_keep_nw(const View &v, uint32_t pi, uint32_t n_keep, uint32_t min_match, float ps)
     {
         const uint32_t w = a.w, deg = v.deg;
         const uint8_t *pr = prow() + pi * a.prow_bytes;
@@ -616,6 +617,13 @@ struct WarpSearch {
             const uint32_t j = lane + 32 * r;
             u[r] = j >= deg ? 0u : (live[r] ? a.d + 2 - (uint32_t)diff[r] : 1u);
         }
+        if (min_match > 0) {
+            uint32_t keep = 0;
+#pragma unroll
+            for (uint32_t r = 0; r < NW; ++r)
+                if (u[r] >= min_match + 2) keep |= 1u << r;
+            return keep;
+        }
         // radix select of the n_keep-th largest u: t collects its bits from
         // the top; `need` counts how many of the values equal to t's bits so
         // far are still to be kept. At the end every u > t is kept and
@@ -640,11 +648,11 @@ struct WarpSearch {
         return keep;
     }
 
-    __device__ uint32_t dgs_keep(const View &v, uint32_t pi, uint32_t n_keep, float ps)
+    __device__ uint32_t dgs_keep(const View &v, uint32_t pi, uint32_t n_keep, uint32_t min_match, float ps)
     {
-        if (v.deg <= 32) return dgs_keep_nw<1>(v, pi, n_keep, ps);
-        if (v.deg <= 64) return dgs_keep_nw<2>(v, pi, n_keep, ps);
-        return dgs_keep_nw<kMaxDegWords>(v, pi, n_keep, ps);
+        if (v.deg <= 32) return dgs_keep_nw<1>(v, pi, n_keep, min_match, ps);
+        if (v.deg <= 64) return dgs_keep_nw<2>(v, pi, n_keep, min_match, ps);
+        return dgs_keep_nw<kMaxDegWords>(v, pi, n_keep, min_match, ps);
     }
 
     // Step 2 (m seeds, in chunks of the candidate capacity), then Steps 3-4
@@ -653,11 +661,12 @@ struct WarpSearch {
     // exists once in the kernel (the kernel is bound by instruction fetch).
     template <int RST>
     __device__ bool iterate(const View &v, const uint32_t *seed_ids, uint32_t m, uint64_t seed_key, uint32_t lcap,
-                            uint32_t W, uint32_t T, uint32_t n_keep, uint32_t it_cool, uint32_t reexpand,
+                            uint32_t W, uint32_t T, uint32_t n_keep, uint32_t min_match, uint32_t it_cool,
+                            uint32_t reexpand,
                             uint32_t &c_iters, uint32_t &c_parents, uint32_t &c_dgs, uint32_t &c_rows)
     {
         const uint32_t deg = v.deg;
-        const bool dgs_on = v.dir != nullptr && n_keep < deg;
+        const bool dgs_on = v.dir != nullptr && (min_match > 0 || n_keep < deg);
         const uint32_t w = a.w;
         bool cool = false;
         uint32_t j0 = 0, it = 0;
@@ -712,7 +721,7 @@ struct WarpSearch {
                 hash_make_room(np * deg);
                 for (uint32_t pi = 0; pi < np; ++pi) {
                     uint32_t km = 0xffffffffu;
-                    if (dgs_now) km = dgs_keep(v, pi, n_keep, __shfl_sync(0xffffffffu, pscale, pi));
+                    if (dgs_now) km = dgs_keep(v, pi, n_keep, min_match, __shfl_sync(0xffffffffu, pscale, pi));
                     nc = collect_row(v, pi, km, nc);
                 }
             }
@@ -778,6 +787,7 @@ struct WarpSearch {
                              seeded ? (use_given ? qp.n_given : (stage ? qp.m : v.deg)) : 0,
                              splitmix64(qp.seed ^ (stage ? 0 : kGhostTag)), lcap, stage ? qp.W : qp.Wg,
                              stage ? qp.T : (given ? qp.Tg_given : qp.Tg), stage ? qp.n_keep : v.deg,
+                             stage ? qp.min_match : 0,
                              stage ? qp.it_cool : 0, stage ? qp.reexpand : 0, iters, parents, dgs_parents, rows);
             if (stage) {
                 st.iters = iters;
@@ -986,7 +996,12 @@ ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint3
         set_error("ann_search: dgs_discard must be in [0,1) and dgs_cooldown in [0,1]");
         return ANN_EINVAL;
     }
-    if (p->dgs_discard > 0.0f && !ix->dir) {
+    if (!(p->dgs_min_match >= 0.0f && p->dgs_min_match <= 1.0f) ||
+        (p->dgs_min_match > 0.0f && p->dgs_discard > 0.0f)) {
+        set_error("ann_search: dgs_min_match must be in [0,1], and not set together with dgs_discard");
+        return ANN_EINVAL;
+    }
+    if ((p->dgs_discard > 0.0f || p->dgs_min_match > 0.0f) && !ix->dir) {
         set_error("ann_search: DGS needs an index built with the direction table");
         return ANN_EINVAL;
     }
@@ -1008,8 +1023,8 @@ ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint3
         return ANN_EINVAL;
     }
     const uint32_t Wg = p->ghost_search_width ? p->ghost_search_width : 1;
-    if (Wg > ANN_MAX_WIDTH || p->reserved) {
-        set_error("ann_search: ghost_search_width must be <= %u (and reserved 0)", ANN_MAX_WIDTH);
+    if (Wg > ANN_MAX_WIDTH) {
+        set_error("ann_search: ghost_search_width must be <= %u", ANN_MAX_WIDTH);
         return ANN_EINVAL;
     }
     QParams q{};
@@ -1027,6 +1042,8 @@ ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint3
         n_keep = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(deg, (int64_t)deg - drop));
     }
     q.n_keep = n_keep;
+    // the similarity threshold: ceil(f * d) agreeing dimensions, in double
+    q.min_match = p->dgs_min_match > 0.0f ? (uint32_t)std::ceil((double)p->dgs_min_match * ix->dim) : 0;
     const int64_t n_cool = (int64_t)std::floor((double)p->dgs_cooldown * p->max_iters + 0.5);
     q.it_cool = (uint32_t)std::max<int64_t>(0, (int64_t)p->max_iters - n_cool);
     q.reexpand = p->dgs_reexpand ? 1 : 0;
@@ -1066,7 +1083,7 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     cap_cand = round_up(cap_cand, 32);
     a.cap_cand = cap_cand;
     const uint32_t adj_words = std::max(q.W * ix->deg_pad, q.Wg * ix->gdeg_pad);
-    const bool dgs = q.n_keep < deg;
+    const bool dgs = q.n_keep < deg || q.min_match > 0;
     const uint32_t dir_words = dgs ? q.W * ix->deg_pad * ix->words : 0;
     a.prow_bytes = ix->row_bytes;
     const uint32_t stage_bytes = std::max(ix->row_bytes, q.rerank ? a.row32_bytes : 0u);

@@ -195,7 +195,9 @@ ann_status ann_server_submit(ann_server *s, uint64_t req_id, const float *querie
     const ann_search_params &mp = s->maxp;
     if (p->k > mp.k || p->itopk > mp.itopk || p->search_width > mp.search_width ||
         (p->ghost_search_width ? p->ghost_search_width : 1) > (mp.ghost_search_width ? mp.ghost_search_width : 1) ||
-        (p->dgs_discard > 0.0f && !(mp.dgs_discard > 0.0f)) || (p->rerank && !mp.rerank) ||
+        ((p->dgs_discard > 0.0f || p->dgs_min_match > 0.0f) &&
+         !(mp.dgs_discard > 0.0f || mp.dgs_min_match > 0.0f)) ||
+        (p->rerank && !mp.rerank) ||
         (p->entry != ANN_ENTRY_RANDOM && mp.entry == ANN_ENTRY_RANDOM) ||
         (p->entry == ANN_ENTRY_GIVEN_GHOST && !s->P) ||
         (p->entry != ANN_ENTRY_RANDOM && (p->ghost_itopk ? p->ghost_itopk : std::min(p->itopk, 64u)) >

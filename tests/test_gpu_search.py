@@ -94,6 +94,9 @@ TINY_PARAMS = [
     dict(itopk=64, max_iters=0, entry=1),                                     # ghost stage only
     dict(itopk=32, max_iters=48, entry=1, dgs_discard=0.7, ghost_search_width=2, ghost_max_iters=24),
     dict(itopk=64, max_iters=64, entry=1, ghost_search_width=4, ghost_itopk=48),
+    dict(itopk=64, max_iters=64, dgs_min_match=0.55),                       # DGS by similarity
+    dict(itopk=64, max_iters=64, entry=1, dgs_min_match=0.6, dgs_reexpand=1),
+    dict(itopk=32, max_iters=96, search_width=2, entry=1, dgs_min_match=0.5, dgs_cooldown=0.5),
 ]
 
 
@@ -107,6 +110,12 @@ def test_tiny_f32(params):
 @pytest.mark.parametrize("rerank", [0, 1])
 def test_tiny_low_precision(storage, rerank):
     g, o = tiny_case().run(storage, seed=4001, itopk=64, max_iters=64, entry=1, dgs_discard=0.5, rerank=rerank)
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("storage", [O.F16, O.E4M3])
+def test_tiny_low_precision_min_match(storage):
+    g, o = tiny_case().run(storage, seed=4001, itopk=64, max_iters=64, entry=1, dgs_min_match=0.55, rerank=1)
     assert_parity(g, o)
 
 
@@ -175,6 +184,10 @@ def test_empty_batch_and_errors():
         gi.search(torch.zeros((1, 128), device="cuda"), itopk=1024)
     with pytest.raises(A.AnnError):
         gi.search(torch.zeros((1, 128), device="cuda"), rerank=1, entry=2)   # given seeds missing
+    with pytest.raises(A.AnnError):
+        gi.search(torch.zeros((1, 128), device="cuda"), dgs_min_match=0.5, dgs_discard=0.5)   # alternatives
+    with pytest.raises(A.AnnError):
+        gi.search(torch.zeros((1, 128), device="cuda"), dgs_min_match=1.5)
 
 
 def test_searches_on_two_streams_of_one_index():
