@@ -77,7 +77,7 @@ typedef struct {
     uint64_t qid_base;          /* global index of query 0 of this call (RNG stream per query) */
     uint32_t ghost_search_width; /* parents per ghost iteration, 1..ANN_MAX_WIDTH (0 or default: 1) */
     float dgs_min_match;        /* DGS by similarity (the paper's alternative to a fixed top n, in its
-                                   comparison with static pruning, Section 6): f in (0,1] keeps the
+                                   comparison with static pruning, Section 6.3): f in (0,1] keeps the
                                    neighbours whose direction agrees with the query's in at least
                                    ceil(f * dim) dimensions; 0 = the top-n rule of dgs_discard.
                                    Setting both is ANN_EINVAL. */

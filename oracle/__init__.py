@@ -228,7 +228,7 @@ def derived_counts(degree: int, max_iters: int, dgs_discard: float, dgs_cooldown
 
 def min_match_count(d: int, dgs_min_match: float) -> int:
     """Reading of the similarity-criterion alternative to DGS's fixed top n
-    (the paper's comparison with static pruning, Section 6): a neighbour is
+    (the paper's comparison with static pruning, Section 6.3): a neighbour is
     kept when its direction agrees with the query's in at least
     ceil(f * d) of the d dimensions, f = dgs_min_match in (0, 1] taken at
     FP32 precision and multiplied in double; 0 keeps the top-n rule."""

@@ -364,7 +364,8 @@ typedef struct {
  *    (ties by adjacency position); dropped neighbours are not marked visited;
  *  - with min_match > 0, DGS instead keeps every neighbour whose score is at
  *    least min_match (the similarity-criterion pruning the paper names as an
- *    alternative to a fixed top n in its comparison with static pruning);
+ *    alternative to a fixed top n in its comparison with static pruning,
+ *    Section 6.3);
  *  - the cool-down starts at it_cool, or earlier once only PARTIAL entries
  *    are left, and then stays on;
  *  - stop when no eligible parent is left or after T iterations. */
