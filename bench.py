@@ -217,6 +217,15 @@ def forms_for(spec):
     }
 
 
+def selected_forms(forms: dict, arg: str) -> list:
+    """Forms a run measures: those named in --forms, else every form but the
+    optional ones."""
+    if arg:
+        named = arg.split(",")
+        return [n for n in forms if n in named]
+    return [n for n in forms if n not in OPTIONAL_FORMS]
+
+
 def params_for(form: dict, L: int, seed: int) -> dict:
     p = {k: v for k, v in form.items() if k != "storage"}
     p.update(itopk=L, max_iters=L // form["search_width"] + 16, seed=seed)
@@ -439,9 +448,8 @@ def run_ours(args):
             return ix.search(Qd, given=seeds, stream=stream, out=out, stats=stats, **p)
         return run
 
-    for name, form in forms.items():
-        if (args.forms and name not in args.forms.split(",")) or (not args.forms and name in OPTIONAL_FORMS):
-            continue
+    for name in selected_forms(forms, args.forms):
+        form = forms[name]
         ix = index_for(form["storage"])
         if form["entry"] == 2 and form["storage"] not in entries:
             entries[form["storage"]], info = train_entry(ds, spec, ix, dev, verbose, args.train_queries,

@@ -26,3 +26,16 @@ def test_truth_knn_and_recall_match_the_oracle():
     got = bench.recall_at(ann.view(np.int32), d, X, Q, 10)
     assert abs(got - want) < 1e-12
     assert np.array_equal(bench.pair_dist(X, Q, ann[:, :5]), O.pair_dist_f64(X, Q, ann[:, :5]))
+
+
+def test_form_selection_and_operating_points():
+    import bench
+    from workloads import WORKLOADS
+    forms = bench.forms_for(WORKLOADS[2])
+    default = bench.selected_forms(forms, "")
+    assert "paper_fp32" in default and "simdgs_fp32" not in default      # optional forms only on request
+    assert bench.selected_forms(forms, "simdgs_fp32,paper_fp32") == ["paper_fp32", "simdgs_fp32"]
+    sim = forms["simdgs_fp32"]
+    assert sim["dgs_discard"] == 0.0 and 0.0 < sim["dgs_min_match"] <= 1.0   # the two rules are alternatives
+    p = bench.params_for(forms["paper_fp32"], 32, 7)
+    assert p["itopk"] == 32 and p["max_iters"] == 32 + 16 and "storage" not in p
