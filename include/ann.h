@@ -119,8 +119,13 @@ ann_status ann_index_create(int device, ann_storage storage, uint64_t n, uint32_
 ann_status ann_index_load(const char *path, int device, ann_storage storage, uint32_t keep_fp32,
                           uint32_t build_dir, ann_index **out);
 
+/* Release the index and all of its device memory; waits first for the last
+ * search launched on it. NULL is accepted (ANN_OK). The caller must not use
+ * the handle afterwards. */
 ann_status ann_index_free(ann_index *index);
 
+/* Shape of the index; any output pointer may be NULL. ANN_EINVAL for a NULL
+ * index. storage receives the ann_storage value. */
 ann_status ann_index_info(const ann_index *index, uint64_t *n, uint32_t *dim, uint32_t *degree,
                           uint32_t *storage, uint32_t *n_ghost, uint32_t *ghost_degree);
 
