@@ -69,6 +69,14 @@ ann_status cuda_fail(cudaError_t e, const char *what);
 
 inline uint32_t round_up(uint32_t x, uint32_t m) { return (x + m - 1) / m * m; }
 
+// Make `dev` current for an entry point, remembering the caller's device in
+// *prev (-1 if it could not be read). Returns ANN_EDEVICE, with the message
+// set, when the switch fails: the entry point must then return without
+// touching device state, since another device would be current.
+ann_status enter_device(int dev, int *prev, const char *who);
+// Restore the caller's device after enter_device.
+void leave_device(int dev, int prev);
+
 // Per-query search parameters (derived from ann_search_params).
 struct QParams {
     uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank, n_given, Wg;

@@ -58,17 +58,33 @@ ann_status cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? ANN_ENOMEM : ANN_ECUDA;
 }
 
-// Keeps the caller's current device and restores it on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
+ann_status enter_device(int dev, int *prev, const char *who)
+{
+    *prev = -1;
+    if (cudaGetDevice(prev) != cudaSuccess) *prev = -1;
+    if (*prev == dev) return ANN_OK;
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) {
+        set_error("%s: cannot make device %d current: %s", who, dev, cudaGetErrorString(e));
+        return ANN_EDEVICE;
     }
+    return ANN_OK;
+}
+
+void leave_device(int dev, int prev)
+{
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+}
+
+// Keeps the caller's current device and restores it on scope exit; `status`
+// is ANN_EDEVICE when the index's device could not be made current.
+struct DeviceGuard {
+    int dev = 0, prev = -1;
+    ann_status status = ANN_OK;
+    DeviceGuard(int d, const char *who) : dev(d) { status = enter_device(d, &prev, who); }
     ~DeviceGuard()
     {
-        if (prev >= 0) cudaSetDevice(prev);
+        if (status == ANN_OK) leave_device(dev, prev);
     }
 };
 
@@ -296,7 +312,7 @@ ann_status ann_dir_table(const void *vectors, const float *scales, ann_storage s
 ann_status ann_index_free(ann_index *ix)
 {
     if (!ix) return ANN_OK;
-    DeviceGuard g(ix->device);
+    DeviceGuard g(ix->device, "ann_index_free");   // frees best-effort even if the switch failed
     if (ix->busy) {
         cudaEventSynchronize(ix->busy);
         cudaEventDestroy(ix->busy);
@@ -353,7 +369,8 @@ ann_status ann_index_create(int device, ann_storage storage, uint64_t n, uint32_
         set_error("ann_index_create: no CUDA device %d", device);
         return ANN_EDEVICE;
     }
-    DeviceGuard guard(device);
+    DeviceGuard guard(device, "ann_index_create");
+    if (guard.status != ANN_OK) return guard.status;
     ann_index *ix = new ann_index();
     ix->device = device;
     ix->storage = storage;
@@ -498,7 +515,8 @@ ann_status ann_index_info(const ann_index *ix, uint64_t *n, uint32_t *dim, uint3
 ann_status ann_index_export(const ann_index *ix, int which, void *dst, uint64_t bytes)
 {
     if (!ix || !dst) { set_error("ann_index_export: NULL argument"); return ANN_EINVAL; }
-    DeviceGuard g(ix->device);
+    DeviceGuard g(ix->device, "ann_index_export");
+    if (g.status != ANN_OK) return g.status;
     const uint64_t row = (uint64_t)ix->dim * ix->elem_bytes;
     const void *src = nullptr;
     uint64_t rows = 0, pitch = 0, width = 0;
@@ -526,7 +544,8 @@ ann_status ann_ghost_index_of(const ann_index *ix, const uint32_t *ids, uint32_t
     if (!ix || (n && (!ids || !out))) { set_error("ann_ghost_index_of: NULL argument"); return ANN_EINVAL; }
     if (!ix->n_ghost) { set_error("ann_ghost_index_of: the index has no ghost set"); return ANN_EINVAL; }
     if (n == 0) return ANN_OK;
-    DeviceGuard g(ix->device);
+    DeviceGuard g(ix->device, "ann_ghost_index_of");
+    if (g.status != ANN_OK) return g.status;
     ghost_index_kernel<<<(int)std::min<uint64_t>((n + 255) / 256, (uint64_t)ix->num_sms * 8), 256, 0,
                          (cudaStream_t)stream>>>(ix->ghost_ids, ix->n_ghost, ids, n, out);
     ANN_CUDA(cudaGetLastError());
@@ -548,7 +567,8 @@ __global__ void timeout_probe_kernel(int *err, long long cycles)
 ann_status ann_selftest_timeout(ann_index *ix)
 {
     if (!ix) { set_error("ann_selftest_timeout: NULL index"); return ANN_EINVAL; }
-    DeviceGuard g(ix->device);
+    DeviceGuard g(ix->device, "ann_selftest_timeout");
+    if (g.status != ANN_OK) return g.status;
     ANN_CUDA(cudaDeviceSynchronize());
     timeout_probe_kernel<<<1, 32>>>(ix->d_error, 2000000ll);   // about 1 ms at 2 GHz
     ANN_CUDA(cudaGetLastError());
@@ -561,7 +581,8 @@ ann_status ann_selftest_timeout(ann_index *ix)
 ann_status ann_sync(ann_index *ix, void *stream)
 {
     if (!ix) { set_error("ann_sync: NULL index"); return ANN_EINVAL; }
-    DeviceGuard g(ix->device);
+    DeviceGuard g(ix->device, "ann_sync");
+    if (g.status != ANN_OK) return g.status;
     ANN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     int err = 0;
     ANN_CUDA(cudaMemcpy(&err, ix->d_error, sizeof(int), cudaMemcpyDeviceToHost));

@@ -850,8 +850,10 @@ ann_status ann_mlp_create(int device, uint32_t in_dim, uint32_t hidden1, uint32_
         return ANN_EDEVICE;
     }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(device);
+    {
+        const ann_status ds = enter_device(device, &prev, "ann_mlp_create");
+        if (ds != ANN_OK) return ds;
+    }
     ann_mlp *m = new ann_mlp();
     m->device = device;
     m->d = in_dim; m->h1 = hidden1; m->h2 = hidden2; m->out = out_dim; m->maxb = max_batch;
@@ -881,7 +883,7 @@ ann_status ann_mlp_create(int device, uint32_t in_dim, uint32_t hidden1, uint32_
         const std::vector<float> ones(in_dim, 1.0f);
         e = cudaMemcpy(m->inv_std, ones.data(), (size_t)in_dim * 4, cudaMemcpyHostToDevice);
     }
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(device, prev);
     if (e != cudaSuccess) {
         mlp_free_all(m);
         delete m;
@@ -895,10 +897,9 @@ ann_status ann_mlp_free(ann_mlp *m)
 {
     if (!m) return ANN_OK;
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    const bool switched = enter_device(m->device, &prev, "ann_mlp_free") == ANN_OK;   // frees best-effort
     mlp_free_all(m);
-    if (prev >= 0) cudaSetDevice(prev);
+    if (switched) leave_device(m->device, prev);
     delete m;
     return ANN_OK;
 }
@@ -909,8 +910,10 @@ ann_status ann_mlp_set_params(ann_mlp *m, const float *W1, const float *b1, cons
 {
     if (!m || !W1 || !b1 || !W2 || !b2 || !W3 || !b3) { set_error("ann_mlp_set_params: NULL argument"); return ANN_EINVAL; }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_set_params");
+        if (ds != ANN_OK) return ds;
+    }
     const float *Ws[3] = {W1, W2, W3}, *bs[3] = {b1, b2, b3};
     const uint32_t rows[3] = {m->h1, m->h2, m->out}, cols[3] = {m->d, m->h1, m->h2};
     ann_status s = ANN_OK;
@@ -929,7 +932,7 @@ ann_status ann_mlp_set_params(ann_mlp *m, const float *W1, const float *b1, cons
     m->step = 0;
     cudaError_t e = cudaDeviceSynchronize();
     if (s == ANN_OK && e != cudaSuccess) s = cuda_fail(e, "ann_mlp_set_params");
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(m->device, prev);
     return s;
 }
 
@@ -939,8 +942,10 @@ ann_status ann_mlp_get(const ann_mlp *m, int which, float *W1, float *b1, float 
 {
     if (!m || (which != 0 && which != 1)) { set_error("ann_mlp_get: bad arguments"); return ANN_EINVAL; }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_get");
+        if (ds != ANN_OK) return ds;
+    }
     float *Ws[3] = {W1, W2, W3}, *bs[3] = {b1, b2, b3};
     const uint32_t rows[3] = {m->h1, m->h2, m->out}, cols[3] = {m->d, m->h1, m->h2};
     ann_status s = ANN_OK;
@@ -951,7 +956,7 @@ ann_status ann_mlp_get(const ann_mlp *m, int which, float *W1, float *b1, float 
         if (e == cudaSuccess && bs[l]) e = cudaMemcpy(bs[l], which ? m->gb[l] : m->b[l], rows[l] * 4, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) { s = cuda_fail(e, "ann_mlp_get"); break; }
     }
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(m->device, prev);
     return s;
 }
 
@@ -972,11 +977,13 @@ ann_status ann_mlp_set_input_norm(ann_mlp *m, const float *mean, const float *in
         }
     }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_set_input_norm");
+        if (ds != ANN_OK) return ds;
+    }
     cudaError_t e = cudaMemcpy(m->mean, mu.data(), (size_t)m->d * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->inv_std, is.data(), (size_t)m->d * 4, cudaMemcpyHostToDevice);
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(m->device, prev);
     return e == cudaSuccess ? ANN_OK : cuda_fail(e, "ann_mlp_set_input_norm");
 }
 
@@ -985,11 +992,13 @@ ann_status ann_mlp_get_input_norm(const ann_mlp *m, float *mean, float *inv_std)
 {
     if (!m || !mean || !inv_std) { set_error("ann_mlp_get_input_norm: NULL argument"); return ANN_EINVAL; }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_get_input_norm");
+        if (ds != ANN_OK) return ds;
+    }
     cudaError_t e = cudaMemcpy(mean, m->mean, (size_t)m->d * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(inv_std, m->inv_std, (size_t)m->d * 4, cudaMemcpyDeviceToHost);
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(m->device, prev);
     return e == cudaSuccess ? ANN_OK : cuda_fail(e, "ann_mlp_get_input_norm");
 }
 
@@ -1000,10 +1009,12 @@ ann_status ann_mlp_forward(ann_mlp *m, const float *x, uint32_t n, float *logits
     if (n > m->maxb) { set_error("ann_mlp_forward: n = %u > max_batch %u", n, m->maxb); return ANN_EINVAL; }
     if (n == 0) return ANN_OK;
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_forward");
+        if (ds != ANN_OK) return ds;
+    }
     ann_status s = forward(m, x, n, (cudaStream_t)stream, EPI_BIAS_F32, logits, nullptr, 0);
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(m->device, prev);
     return s;
 }
 
@@ -1019,8 +1030,10 @@ ann_status ann_mlp_train_step(ann_mlp *m, const float *x, const uint32_t *labels
         return ANN_EINVAL;
     }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_train_step");
+        if (ds != ANN_OK) return ds;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     ann_status s = ensure_train_buffers(m, n);
     auto chk = [&]() { cudaError_t e = cudaGetLastError(); if (e != cudaSuccess && s == ANN_OK) s = cuda_fail(e, "ann_mlp_train_step"); };
@@ -1079,7 +1092,7 @@ ann_status ann_mlp_train_step(ann_mlp *m, const float *x, const uint32_t *labels
         cudaError_t ce = cudaMemcpyAsync(loss_out, m->loss, 4, cudaMemcpyDeviceToDevice, st);
         if (ce != cudaSuccess) s = cuda_fail(ce, "ann_mlp_train_step loss");
     }
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(m->device, prev);
     return s;
 }
 
@@ -1096,8 +1109,10 @@ ann_status ann_mlp_predict(ann_mlp *m, const float *x, uint32_t n, uint32_t P, f
     }
     if (n == 0) return ANN_OK;
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_predict");
+        if (ds != ANN_OK) return ds;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     ann_status s = ANN_OK;
     for (uint32_t r0 = 0; r0 < n && s == ANN_OK; r0 += m->maxb) {
@@ -1123,7 +1138,7 @@ ann_status ann_mlp_predict(ann_mlp *m, const float *x, uint32_t n, uint32_t P, f
             if (e != cudaSuccess) s = cuda_fail(e, "topp_merge_kernel");
         }
     }
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(m->device, prev);
     return s;
 }
 
@@ -1141,8 +1156,10 @@ ann_status ann_mlp_train_epochs(ann_mlp *m, const float *x, const uint32_t *labe
         return ANN_EINVAL;
     }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_train_epochs");
+        if (ds != ANN_OK) return ds;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     ann_status s = ANN_OK;
     if (n > m->perm_cap) {
@@ -1182,7 +1199,7 @@ ann_status ann_mlp_train_epochs(ann_mlp *m, const float *x, const uint32_t *labe
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) s = cuda_fail(e, "ann_mlp_train_epochs");
     }
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(m->device, prev);
     return s;
 }
 
@@ -1191,8 +1208,10 @@ ann_status ann_mlp_sync(ann_mlp *m, void *stream)
 {
     if (!m) { set_error("ann_mlp_sync: NULL"); return ANN_EINVAL; }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(m->device);
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_sync");
+        if (ds != ANN_OK) return ds;
+    }
     ann_status s = ANN_OK;
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     int err = 0;
@@ -1203,7 +1222,7 @@ ann_status ann_mlp_sync(ann_mlp *m, void *stream)
         set_error("a bounded device wait ran out in an MLP kernel");
         s = ANN_ETIMEOUT;
     }
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(m->device, prev);
     return s;
 }
 

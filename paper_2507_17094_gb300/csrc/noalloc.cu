@@ -19,9 +19,12 @@
 //     call's contents, so each call zeroes the work counter and error word it
 //     relies on, and calls that overlap on the GPU (other streams, other host
 //     threads) race on it;
+//   - the call is synchronous: it returns once the results are in the
+//     caller's host buffers;
 //   - the first call on a device looks up that device's address of the array
-//     (cudaGetSymbolAddress, with that device current) and caches it; make
-//     that first call before any stream capture.
+//     (cudaGetSymbolAddress, with that device current) and caches it; that
+//     lookup is a set-up step, so make the first call on each device before
+//     any stream capture starts there.
 #include <mutex>
 
 #include "ann_internal.cuh"
@@ -77,11 +80,13 @@ extern "C" ann_status ann_search_host_noalloc(ann_index *ix, const float *querie
                   "scratch holds %u (split the batch)", nq, ix->dim, p->k, need, (unsigned)ANN_NOALLOC_SCRATCH_BYTES);
         return ANN_EINVAL;
     }
+    // the array's address is looked up (and cached) only with the index's
+    // device current: return before that if the switch fails
     int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != ix->device) cudaSetDevice(ix->device);
+    ann_status s = enter_device(ix->device, &prev, "ann_search_host_noalloc");
+    if (s != ANN_OK) return s;
     uint8_t *base = nullptr;
-    ann_status s = scratch_for(ix->device, &base);
+    s = scratch_for(ix->device, &base);
     if (s == ANN_OK) {
         cudaStream_t st = (cudaStream_t)stream;
         uint32_t *counter = reinterpret_cast<uint32_t *>(base);
@@ -106,6 +111,6 @@ extern "C" ann_status ann_search_host_noalloc(ann_index *ix, const float *querie
             s = ANN_ETIMEOUT;
         }
     }
-    if (prev >= 0 && prev != ix->device) cudaSetDevice(prev);
+    leave_device(ix->device, prev);
     return s;
 }

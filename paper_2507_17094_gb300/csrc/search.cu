@@ -1259,10 +1259,10 @@ ann_status ann_search(ann_index *ix, const float *queries, uint32_t nq, const an
 {
     if (!ix) { set_error("ann_search: NULL index"); return ANN_EINVAL; }
     int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != ix->device) cudaSetDevice(ix->device);
-    ann_status s = search_launch(ix, queries, nq, p, given, n_given, ids, dists, stats, (cudaStream_t)stream);
-    if (prev >= 0 && prev != ix->device) cudaSetDevice(prev);
+    ann_status s = enter_device(ix->device, &prev, "ann_search");
+    if (s != ANN_OK) return s;
+    s = search_launch(ix, queries, nq, p, given, n_given, ids, dists, stats, (cudaStream_t)stream);
+    leave_device(ix->device, prev);
     return s;
 }
 
@@ -1273,15 +1273,14 @@ ann_status ann_search_host(ann_index *ix, const float *queries, uint32_t nq, con
     if (nq == 0) return ANN_OK;
     if (!queries || !ids || !dists) { set_error("ann_search_host: NULL buffers"); return ANN_EINVAL; }
     int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != ix->device) cudaSetDevice(ix->device);
+    ann_status s = enter_device(ix->device, &prev, "ann_search_host");
+    if (s != ANN_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t qb = (size_t)nq * ix->dim * 4;
     const size_t gb = (p->entry == ANN_ENTRY_GIVEN_GHOST && given) ? (size_t)nq * n_given * 4 : 0;
     const size_t ob = (size_t)nq * p->k * 4;
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t need = up(qb) + up(gb) + 2 * up(ob);
-    ann_status s = ANN_OK;
     if (need > ix->ws_bytes) {
         if (ix->ws) cudaFree(ix->ws);
         ix->ws = nullptr;
@@ -1307,7 +1306,7 @@ ann_status ann_search_host(ann_index *ix, const float *queries, uint32_t nq, con
             if (e != cudaSuccess) s = cuda_fail(e, "ann_search_host download");
         }
     }
-    if (prev >= 0 && prev != ix->device) cudaSetDevice(prev);
+    leave_device(ix->device, prev);
     return s;
 }
 

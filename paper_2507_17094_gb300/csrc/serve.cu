@@ -132,8 +132,10 @@ ann_status ann_server_create(ann_index *ix, const ann_server_config *cfg, ann_ml
         return ANN_EINVAL;
     }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(ix->device);
+    {
+        const ann_status ds = enter_device(ix->device, &prev, "ann_server_create");
+        if (ds != ANN_OK) return ds;
+    }
     ann_server *s = new ann_server();
     s->ix = ix;
     s->mlp = mlp;
@@ -177,7 +179,7 @@ ann_status ann_server_create(ann_index *ix, const ann_server_config *cfg, ann_ml
         if (e != cudaSuccess) st = cuda_fail(e, "ann_server_create");
         else memset(s->h_flags, 0, (size_t)s->nreq * 4);
     }
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(ix->device, prev);
     if (st != ANN_OK) {
         server_release(s);
         delete s;
@@ -215,8 +217,10 @@ ann_status ann_server_submit(ann_server *s, uint64_t req_id, const float *querie
         return ANN_EBUSY;
     }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(s->ix->device);
+    {
+        const ann_status ds = enter_device(s->ix->device, &prev, "ann_server_submit");
+        if (ds != ANN_OK) return ds;
+    }
     const uint32_t ri = (uint32_t)(s->seq % s->nreq);
     const uint32_t dim = s->ix->dim;
     const uint32_t slot0 = (uint32_t)(s->tail % s->cap);
@@ -278,7 +282,7 @@ ann_status ann_server_submit(ann_server *s, uint64_t req_id, const float *querie
         s->tail += nq;
         s->seq++;
     }
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(s->ix->device, prev);
     return st;
 }
 
@@ -286,8 +290,10 @@ ann_status ann_server_poll(ann_server *s, ann_completion *out, uint32_t max, uin
 {
     if (!s || (max && !out) || !n_out) { set_error("ann_server_poll: NULL argument"); return ANN_EINVAL; }
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(s->ix->device);
+    {
+        const ann_status ds = enter_device(s->ix->device, &prev, "ann_server_poll");
+        if (ds != ANN_OK) return ds;
+    }
     ann_status st = ANN_OK;
     for (Pending &pd : s->inflight) {
         if (pd.done || !reinterpret_cast<volatile uint32_t *>(s->h_flags)[pd.ri]) continue;
@@ -304,7 +310,7 @@ ann_status ann_server_poll(ann_server *s, ann_completion *out, uint32_t max, uin
         s->ready.pop_front();
     }
     *n_out = n;
-    if (prev >= 0) cudaSetDevice(prev);
+    leave_device(s->ix->device, prev);
     return st;
 }
 
@@ -314,10 +320,9 @@ ann_status ann_server_destroy(ann_server *s)
 {
     if (!s) return ANN_OK;
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(s->ix->device);
+    const bool switched = enter_device(s->ix->device, &prev, "ann_server_destroy") == ANN_OK;   // frees best-effort
     server_release(s);
-    if (prev >= 0) cudaSetDevice(prev);
+    if (switched) leave_device(s->ix->device, prev);
     delete s;
     return ANN_OK;
 }

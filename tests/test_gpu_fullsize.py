@@ -10,7 +10,7 @@ import pytest
 
 import oracle as O
 
-pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+pytestmark = [pytest.mark.gpu, pytest.mark.fullsize]
 torch = pytest.importorskip("torch")
 
 
