@@ -255,15 +255,39 @@ ann_status ann_mlp_sync(ann_mlp *mlp, void *stream);
 ann_status ann_mlp_set_input_norm(ann_mlp *mlp, const float *mean, const float *inv_std);
 /* Host copies of the standardisation (in_dim floats each). */
 ann_status ann_mlp_get_input_norm(const ann_mlp *mlp, float *mean, float *inv_std);
-/* Save the FP32 parameters to a file: the 8 bytes "ANNMLP01", the four sizes
- * (in_dim, hidden1, hidden2, out_dim) as little-endian uint32, then W1, b1,
- * W2, b2, W3, b3, mean, inv_std as little-endian FP32 in the row-major layout
- * above. The optimizer state is not saved. ANN_EIO if the file cannot be
+/* Standardisation statistics computed on the device (no counterpart in the
+ * paper): x holds n training queries (device, n x in_dim FP32, n >= 1). Per
+ * dimension j, mean_j = (1/n) sum_i x_ij and std_j = sqrt((1/n) sum_i
+ * (x_ij - mean_j)^2), accumulated in FP64 in a fixed order (deterministic);
+ * inv_std_j = 1 / max(std_j, 1e-6 * max(max_j std_j, 1e-30)); both rounded
+ * once to FP32 and installed as by ann_mlp_set_input_norm. The call
+ * allocates a temporary of about (n/512 + 2) x in_dim doubles and is
+ * synchronous on `stream`. ANN_EINVAL for NULL x or n = 0. */
+ann_status ann_mlp_fit_input_norm(ann_mlp *mlp, const float *x, uint32_t n, void *stream);
+/* The fallback threshold tau of the learned entry (no counterpart in the
+ * paper), computed on the device: with q = min(fallback, 1), the value of
+ * 0-based rank floor(q * (n - 1)) (q and the product in double) among the n
+ * values pmax (device FP32, e.g. ann_mlp_predict's largest softmax
+ * probabilities of validation queries) in ascending order, i.e. numpy's
+ * quantile with method "lower". *tau (host) receives it; 0 when n = 0 or
+ * fallback <= 0 (no query falls back). Values are ordered as FP32 numbers
+ * (-0 before +0; NaN, which pmax never holds, after +inf). Synchronous on
+ * `stream`. ANN_EINVAL for NULL tau, NULL pmax with n > 0, or a NaN fallback. */
+ann_status ann_mlp_confidence_threshold(ann_mlp *mlp, const float *pmax, uint32_t n, double fallback, float *tau,
+                                        void *stream);
+/* Save the network and its training state to a file: the 8 bytes "ANNMLP02",
+ * the four sizes (in_dim, hidden1, hidden2, out_dim) as little-endian uint32,
+ * then W1, b1, W2, b2, W3, b3, mean, inv_std as little-endian FP32 in the
+ * row-major layout above, then the AdamW step count (uint32) and, per layer
+ * 1..3, the first and second moments of W and then of b (FP32, same layouts),
+ * so that training resumes where it stopped. ANN_EIO if the file cannot be
  * written. */
 ann_status ann_mlp_save(const ann_mlp *mlp, const char *path);
 /* Create an MLP on `device` with room for max_batch rows from a file written
- * by ann_mlp_save (fresh optimizer state). ANN_EIO if the file cannot be read
- * or is short, ANN_EINVAL if its magic or sizes are not valid. */
+ * by ann_mlp_save: version "ANNMLP02" restores the optimizer state too;
+ * version "ANNMLP01" (parameters and standardisation only) starts with a
+ * fresh one. ANN_EIO if the file cannot be read or is short, ANN_EINVAL if
+ * its magic or sizes are not valid. */
 ann_status ann_mlp_load(const char *path, int device, uint32_t max_batch, ann_mlp **out);
 
 /* ------------------------------------------------------------------------

@@ -157,3 +157,33 @@ def top_p(z: np.ndarray, P: int):
     order = np.lexsort((np.broadcast_to(np.arange(z.shape[1]), z.shape), -z), axis=1)[:, :P]
     p_max = 1.0 / np.exp(z - z.max(axis=1, keepdims=True)).sum(axis=1)
     return order.astype(np.uint32), p_max
+
+
+def input_norm_stats(X: np.ndarray):
+    """Per-dimension standardisation of training queries, written out as its
+    definition in FP64: mean_j = (1/n) sum_i x_ij; std_j = sqrt((1/n) sum_i
+    (x_ij - mean_j)^2) (population standard deviation); a floor of 1e-6 times
+    the largest std (at least 1e-30) keeps constant dimensions finite;
+    inv_std_j = 1 / max(std_j, floor). Returns (mean, inv_std) rounded to
+    FP32, the precision the network applies them in."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    mean = X.sum(axis=0) / n
+    dev = X - mean[None, :]
+    std = np.sqrt((dev * dev).sum(axis=0) / n)
+    floor = 1e-6 * max(float(std.max()), 1e-30)
+    inv_std = 1.0 / np.maximum(std, floor)
+    return mean.astype(np.float32), inv_std.astype(np.float32)
+
+
+def lower_quantile(values: np.ndarray, q: float) -> float:
+    """The fallback threshold tau: the value at 0-based position
+    floor(min(q, 1) * (n - 1)) of the values sorted ascending (the "lower"
+    quantile: no interpolation, always one of the values); 0 when there are
+    no values or q <= 0 (nothing falls back)."""
+    v = np.asarray(values, dtype=np.float32).ravel()
+    if v.size == 0 or q <= 0.0:
+        return 0.0
+    pos = int(np.floor(min(float(q), 1.0) * (v.size - 1)))
+    return float(np.sort(v, kind="stable")[pos])
+

@@ -29,6 +29,7 @@ EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_inde
            "ann_encode", "ann_dir_table", "ann_mlp_create", "ann_mlp_free", "ann_mlp_set_params", "ann_mlp_get",
            "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_train_epochs", "ann_mlp_predict", "ann_mlp_sync",
            "ann_mlp_save", "ann_mlp_load", "ann_mlp_set_input_norm", "ann_mlp_get_input_norm",
+           "ann_mlp_fit_input_norm", "ann_mlp_confidence_threshold",
            "ann_selftest_timeout",
            "ann_ghost_index_of", "ann_server_create", "ann_server_submit", "ann_server_poll",
            "ann_server_in_flight", "ann_server_destroy", "ann_last_error")
@@ -102,6 +103,8 @@ def lib() -> C.CDLL:
             L.ann_mlp_save.argtypes = [vp, C.c_char_p]
             L.ann_mlp_set_input_norm.argtypes = [vp, vp, vp]
             L.ann_mlp_get_input_norm.argtypes = [vp, vp, vp]
+            L.ann_mlp_fit_input_norm.argtypes = [vp, vp, u32, vp]
+            L.ann_mlp_confidence_threshold.argtypes = [vp, vp, u32, C.c_double, C.POINTER(f32), vp]
             L.ann_mlp_load.argtypes = [C.c_char_p, C.c_int, u32, C.POINTER(vp)]
             L.ann_mlp_train_epochs.argtypes = [vp, vp, vp, u32, u32, u32, f32, f32, f32, f32, f32, u64, vp, vp]
             L.ann_ghost_index_of.argtypes = [vp, vp, u32, vp, vp]
@@ -324,6 +327,21 @@ class MLP:
         mu = np.ascontiguousarray(mean, dtype=np.float32).reshape(self.dims[0])
         isd = np.ascontiguousarray(inv_std, dtype=np.float32).reshape(self.dims[0])
         _check(lib().ann_mlp_set_input_norm(self._h, _np_ptr(mu), _np_ptr(isd)))
+
+    def fit_input_norm(self, x, stream=None):
+        """Standardisation statistics of the device queries x (n x in_dim),
+        computed and installed on the device (synchronous)."""
+        assert x.is_cuda and x.is_contiguous() and x.shape[1] == self.dims[0]
+        _check(lib().ann_mlp_fit_input_norm(self._h, x.data_ptr(), x.shape[0], _stream_ptr(stream)))
+
+    def confidence_threshold(self, pmax, fallback: float, stream=None) -> float:
+        """The `fallback` lower quantile of the device values pmax (see
+        include/ann.h), computed on the device."""
+        tau = C.c_float()
+        assert pmax.is_cuda and pmax.is_contiguous()
+        _check(lib().ann_mlp_confidence_threshold(self._h, pmax.data_ptr(), pmax.numel(), float(fallback),
+                                                  C.byref(tau), _stream_ptr(stream)))
+        return float(tau.value)
 
     def get_input_norm(self):
         mu = np.empty(self.dims[0], np.float32)

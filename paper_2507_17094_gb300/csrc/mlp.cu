@@ -642,6 +642,108 @@ __global__ void accumulate_kernel(float *__restrict__ acc, const float *__restri
     if (threadIdx.x == 0 && blockIdx.x == 0) *acc += w * *v;
 }
 
+// ---------------------------------------------------------- input statistics
+// Column sums of an n x d row-major FP32 matrix, in FP64, by row chunks: the
+// block of chunk `blockIdx.x` and columns `blockIdx.y * blockDim.x + tid`
+// adds its rows in row order (a warp reads consecutive columns of one row,
+// so every load is coalesced) and writes one partial per (chunk, column).
+// With `mean`, it sums the squared deviations (x - mean)^2 instead. The
+// partials are added in chunk order by col_finish_kernel, so the result does
+// not depend on scheduling.
+__global__ void col_partial_kernel(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t rows_per_chunk,
+                                   const double *__restrict__ mean, double *__restrict__ partial)
+{
+    const uint32_t c = blockIdx.y * blockDim.x + threadIdx.x;
+    if (c >= d) return;
+    const uint64_t r0 = (uint64_t)blockIdx.x * rows_per_chunk;
+    const uint64_t r1 = (r0 + rows_per_chunk < (uint64_t)n) ? r0 + rows_per_chunk : (uint64_t)n;
+    const double mu = mean ? mean[c] : 0.0;
+    double s = 0.0;
+    for (uint64_t r = r0; r < r1; ++r) {
+        const double v = (double)x[r * d + c];
+        if (mean) {
+            const double t = __dsub_rn(v, mu);
+            s = __dadd_rn(s, __dmul_rn(t, t));
+        } else {
+            s = __dadd_rn(s, v);
+        }
+    }
+    partial[(size_t)blockIdx.x * d + c] = s;
+}
+
+// out[c] = (sum of the chunk partials of column c, in chunk order) / n.
+__global__ void col_finish_kernel(const double *__restrict__ partial, uint32_t chunks, uint32_t d, uint32_t n,
+                                  double *__restrict__ out)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d) return;
+    double s = 0.0;
+    for (uint32_t k = 0; k < chunks; ++k) s = __dadd_rn(s, partial[(size_t)k * d + c]);
+    out[c] = __ddiv_rn(s, (double)n);
+}
+
+// Standardisation from the FP64 mean and variance (one block): std = sqrt(var),
+// the floor 1e-6 * max(largest std, 1e-30) keeps constant dimensions finite,
+// inv_std = 1 / max(std, floor); both rounded once to FP32.
+__global__ void norm_finish_kernel(const double *__restrict__ mean, const double *__restrict__ var, uint32_t d,
+                                   float *__restrict__ mean_out, float *__restrict__ inv_std_out)
+{
+    __shared__ double red[32];
+    double mx = 0.0;
+    for (uint32_t c = threadIdx.x; c < d; c += blockDim.x) mx = fmax(mx, __dsqrt_rn(var[c]));
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (threadIdx.x == 0) red[0] = mx;
+    }
+    __syncthreads();
+    const double fl = 1e-6 * fmax(red[0], 1e-30);
+    for (uint32_t c = threadIdx.x; c < d; c += blockDim.x) {
+        mean_out[c] = __double2float_rn(mean[c]);
+        inv_std_out[c] = __double2float_rn(__ddiv_rn(1.0, fmax(__dsqrt_rn(var[c]), fl)));
+    }
+}
+
+// ---------------------------------------------------------- rank selection
+// A total order on FP32 values as unsigned keys: negative values flip all
+// bits, non-negative ones set the sign bit.
+__device__ __forceinline__ uint32_t order_key(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// The value of 0-based rank `rank` among v[0..n) in ascending order (one
+// block). The key is found bit by bit from the most significant: a bit is
+// set when fewer than rank + 1 keys lie below the candidate, so the result is
+// the largest key with at most `rank` keys below it -- the rank-th smallest.
+__global__ void select_rank_kernel(const float *__restrict__ v, uint32_t n, uint32_t rank, float *__restrict__ out)
+{
+    __shared__ uint32_t red[32];
+    __shared__ uint32_t total;
+    uint32_t key = 0;
+    for (int b = 31; b >= 0; --b) {
+        const uint32_t t = key | (1u << b);
+        uint32_t c = 0;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) c += order_key(v[i]) < t ? 1u : 0u;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            c = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0u;
+            c = __reduce_add_sync(0xffffffffu, c);
+            if (threadIdx.x == 0) total = c;
+        }
+        __syncthreads();
+        if (total <= rank) key = t;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = __uint_as_float((key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key);
+}
+
 uint64_t mix64(uint64_t x)
 {
     uint64_t z = x + 0x9E3779B97F4A7C15ull;
@@ -987,6 +1089,73 @@ ann_status ann_mlp_set_input_norm(ann_mlp *m, const float *mean, const float *in
     return e == cudaSuccess ? ANN_OK : cuda_fail(e, "ann_mlp_set_input_norm");
 }
 
+// Standardisation statistics of n device queries (n x in_dim FP32): per
+// dimension the mean and 1 / std (population std, FP64 on the device), with
+// std floored at 1e-6 of the largest; installed as the input standardisation.
+// Synchronous on `stream`.
+ann_status ann_mlp_fit_input_norm(ann_mlp *m, const float *x, uint32_t n, void *stream)
+{
+    if (!m || !x || n == 0) { set_error("ann_mlp_fit_input_norm: NULL argument or no rows"); return ANN_EINVAL; }
+    int prev = -1;
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_fit_input_norm");
+        if (ds != ANN_OK) return ds;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t d = m->d, rows_per_chunk = 512;
+    const uint32_t chunks = (n + rows_per_chunk - 1) / rows_per_chunk;
+    double *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, ((size_t)chunks * d + 2 * (size_t)d) * sizeof(double));
+    if (e == cudaSuccess) {
+        double *partial = buf, *mean = buf + (size_t)chunks * d, *var = mean + d;
+        const dim3 grid(chunks, (d + 127) / 128);
+        col_partial_kernel<<<grid, 128, 0, st>>>(x, n, d, rows_per_chunk, nullptr, partial);
+        col_finish_kernel<<<(d + 127) / 128, 128, 0, st>>>(partial, chunks, d, n, mean);
+        col_partial_kernel<<<grid, 128, 0, st>>>(x, n, d, rows_per_chunk, mean, partial);
+        col_finish_kernel<<<(d + 127) / 128, 128, 0, st>>>(partial, chunks, d, n, var);
+        norm_finish_kernel<<<1, 1024, 0, st>>>(mean, var, d, m->mean, m->inv_std);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(buf);
+    }
+    leave_device(m->device, prev);
+    return e == cudaSuccess ? ANN_OK : cuda_fail(e, "ann_mlp_fit_input_norm");
+}
+
+// The confidence threshold tau: the value of 0-based rank
+// floor(min(fallback, 1) * (n - 1)) among the n device values pmax in
+// ascending order (numpy's "lower" quantile); 0 when fallback <= 0 or n = 0.
+// Written to *tau on the host (synchronous on `stream`).
+ann_status ann_mlp_confidence_threshold(ann_mlp *m, const float *pmax, uint32_t n, double fallback, float *tau,
+                                        void *stream)
+{
+    if (!m || !tau || (n && !pmax) || !(fallback == fallback)) {
+        set_error("ann_mlp_confidence_threshold: NULL argument or NaN fallback");
+        return ANN_EINVAL;
+    }
+    *tau = 0.0f;
+    if (n == 0 || fallback <= 0.0) return ANN_OK;
+    const double q = fallback < 1.0 ? fallback : 1.0;
+    const uint32_t rank = (uint32_t)std::floor(q * (double)(n - 1));
+    int prev = -1;
+    {
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_confidence_threshold");
+        if (ds != ANN_OK) return ds;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    float *dv = nullptr;
+    cudaError_t e = cudaMalloc(&dv, 16);
+    if (e == cudaSuccess) {
+        select_rank_kernel<<<1, 1024, 0, st>>>(pmax, n, rank, dv);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tau, dv, sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dv);
+    }
+    leave_device(m->device, prev);
+    return e == cudaSuccess ? ANN_OK : cuda_fail(e, "ann_mlp_confidence_threshold");
+}
+
 // Host copies of the input standardisation (in_dim floats each).
 ann_status ann_mlp_get_input_norm(const ann_mlp *m, float *mean, float *inv_std)
 {
@@ -1230,7 +1399,27 @@ ann_status ann_mlp_sync(ann_mlp *m, void *stream)
 // Parameter file: magic, four uint32 sizes, then W1 b1 W2 b2 W3 b3 and the
 // input standardisation (mean, inv_std) as FP32;
 // both hosts this builds for are little-endian, so the bytes go out as they are.
-static const char kMlpMagic[8] = {'A', 'N', 'N', 'M', 'L', 'P', '0', '1'};
+// Parameter files: "ANNMLP01" (parameters and input standardisation) and
+// "ANNMLP02" (the same, then the AdamW state: the step count and the first
+// and second moments of every parameter array). Saving writes version 02.
+static const char kMlpMagic1[8] = {'A', 'N', 'N', 'M', 'L', 'P', '0', '1'};
+static const char kMlpMagic2[8] = {'A', 'N', 'N', 'M', 'L', 'P', '0', '2'};
+
+namespace {
+
+// Copy one device array to the host (or the host to the device).
+bool copy_d2h(std::vector<float> &h, const float *d, size_t n)
+{
+    h.resize(n);
+    return cudaMemcpy(h.data(), d, n * 4, cudaMemcpyDeviceToHost) == cudaSuccess;
+}
+
+bool copy_h2d(float *d, const std::vector<float> &h)
+{
+    return cudaMemcpy(d, h.data(), h.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+}  // namespace
 
 ann_status ann_mlp_save(const ann_mlp *m, const char *path)
 {
@@ -1243,13 +1432,31 @@ ann_status ann_mlp_save(const ann_mlp *m, const char *path)
     std::vector<float> mu(m->d), is(m->d);
     if (s == ANN_OK) s = ann_mlp_get_input_norm(m, mu.data(), is.data());
     if (s != ANN_OK) return s;
+    // optimizer moments, in the order mW, vW, mb, vb per layer
+    std::vector<float> opt[12];
+    {
+        int prev = -1;
+        const ann_status ds = enter_device(m->device, &prev, "ann_mlp_save");
+        if (ds != ANN_OK) return ds;
+        bool ok = true;
+        for (int l = 0; l < 3 && ok; ++l) {
+            const size_t nw = (size_t)rows[l] * cols[l];
+            ok = copy_d2h(opt[4 * l], m->mW[l], nw) && copy_d2h(opt[4 * l + 1], m->vW[l], nw) &&
+                 copy_d2h(opt[4 * l + 2], m->mb[l], rows[l]) && copy_d2h(opt[4 * l + 3], m->vb[l], rows[l]);
+        }
+        leave_device(m->device, prev);
+        if (!ok) { set_error("ann_mlp_save: reading the optimizer state failed"); return ANN_ECUDA; }
+    }
     FILE *f = std::fopen(path, "wb");
     if (!f) { set_error("ann_mlp_save: cannot open %s", path); return ANN_EIO; }
-    bool ok = std::fwrite(kMlpMagic, 1, 8, f) == 8 && std::fwrite(dims, 4, 4, f) == 4;
+    bool ok = std::fwrite(kMlpMagic2, 1, 8, f) == 8 && std::fwrite(dims, 4, 4, f) == 4;
     for (int l = 0; l < 3 && ok; ++l)
         ok = std::fwrite(W[l].data(), 4, W[l].size(), f) == W[l].size() &&
              std::fwrite(b[l].data(), 4, b[l].size(), f) == b[l].size();
     ok = ok && std::fwrite(mu.data(), 4, m->d, f) == m->d && std::fwrite(is.data(), 4, m->d, f) == m->d;
+    const uint32_t step = m->step;
+    ok = ok && std::fwrite(&step, 4, 1, f) == 1;
+    for (int i = 0; i < 12 && ok; ++i) ok = std::fwrite(opt[i].data(), 4, opt[i].size(), f) == opt[i].size();
     ok = (std::fclose(f) == 0) && ok;
     if (!ok) { set_error("ann_mlp_save: write to %s failed", path); return ANN_EIO; }
     return ANN_OK;
@@ -1268,7 +1475,8 @@ ann_status ann_mlp_load(const char *path, int device, uint32_t max_batch, ann_ml
         set_error("ann_mlp_load: %s is too short", path);
         return ANN_EIO;
     }
-    if (std::memcmp(magic, kMlpMagic, 8) != 0) {
+    const bool v2 = std::memcmp(magic, kMlpMagic2, 8) == 0;
+    if (!v2 && std::memcmp(magic, kMlpMagic1, 8) != 0) {
         std::fclose(f);
         set_error("ann_mlp_load: %s is not an MLP parameter file", path);
         return ANN_EINVAL;
@@ -1290,12 +1498,38 @@ ann_status ann_mlp_load(const char *path, int device, uint32_t max_batch, ann_ml
     }
     std::vector<float> mu(dims[0]), is(dims[0]);
     ok = ok && std::fread(mu.data(), 4, dims[0], f) == dims[0] && std::fread(is.data(), 4, dims[0], f) == dims[0];
+    uint32_t step = 0;
+    std::vector<float> opt[12];
+    if (v2 && ok) {
+        ok = std::fread(&step, 4, 1, f) == 1;
+        for (int l = 0; l < 3 && ok; ++l) {
+            const size_t sz[4] = {(size_t)rows[l] * cols[l], (size_t)rows[l] * cols[l], rows[l], rows[l]};
+            for (int j = 0; j < 4 && ok; ++j) {
+                opt[4 * l + j].resize(sz[j]);
+                ok = std::fread(opt[4 * l + j].data(), 4, sz[j], f) == sz[j];
+            }
+        }
+    }
     std::fclose(f);
     if (!ok) { set_error("ann_mlp_load: %s is too short", path); return ANN_EIO; }
     ann_mlp *m = nullptr;
     ann_status s = ann_mlp_create(device, dims[0], dims[1], dims[2], dims[3], max_batch, &m);
     if (s == ANN_OK) s = ann_mlp_set_params(m, W[0].data(), b[0].data(), W[1].data(), b[1].data(), W[2].data(), b[2].data());
     if (s == ANN_OK) s = ann_mlp_set_input_norm(m, mu.data(), is.data());
+    if (s == ANN_OK && v2) {
+        // set_params zeroed the moments and the step: restore the saved ones
+        int prev = -1;
+        s = enter_device(device, &prev, "ann_mlp_load");
+        if (s == ANN_OK) {
+            bool ok2 = true;
+            for (int l = 0; l < 3 && ok2; ++l)
+                ok2 = copy_h2d(m->mW[l], opt[4 * l]) && copy_h2d(m->vW[l], opt[4 * l + 1]) &&
+                      copy_h2d(m->mb[l], opt[4 * l + 2]) && copy_h2d(m->vb[l], opt[4 * l + 3]);
+            leave_device(device, prev);
+            if (!ok2) s = cuda_fail(cudaGetLastError(), "ann_mlp_load: restoring the optimizer state");
+            m->step = step;
+        }
+    }
     if (s != ANN_OK) { ann_mlp_free(m); return s; }
     *out = m;
     return ANN_OK;

@@ -23,16 +23,6 @@ def ghost_labels(index: Index, queries, seed: int, ghost_itopk: int = 64, ghost_
     return index.ghost_index_of(ids[:, 0].contiguous(), stream=stream)
 
 
-def choose_tau(pmax: np.ndarray, fallback: float = 0.05) -> float:
-    """Confidence threshold: the `fallback` quantile of the validation
-    queries' top softmax probabilities, so that fraction of in-distribution
-    queries (and any query the network is less sure of) falls back to plain
-    ghost staging."""
-    if len(pmax) == 0 or fallback <= 0.0:
-        return 0.0
-    return float(np.quantile(np.asarray(pmax, dtype=np.float64), min(fallback, 1.0), method="lower"))
-
-
 class LearnedEntry:
     """An MLP over the ghost set, trained on the index's own ghost staging."""
 
@@ -50,21 +40,21 @@ class LearnedEntry:
         takes each query dimension to zero mean and unit variance over the
         training queries (the library applies it on the device)."""
         if standardise:
-            x = train_queries.detach().cpu().numpy().astype(np.float64)
-            mean = x.mean(axis=0)
-            std = x.std(axis=0)
-            self.mlp.set_input_norm(mean.astype(np.float32),
-                                    (1.0 / np.maximum(std, 1e-6 * max(float(std.max()), 1e-30))).astype(np.float32))
+            self.mlp.fit_input_norm(train_queries)
         self.losses = self.mlp.train_epochs(train_queries, labels, batch=batch, epochs=epochs, lr=lr, seed=seed)
         return self.losses
 
     def calibrate(self, val_queries, val_labels, fallback: float = 0.05):
-        """Set tau from a validation split (see choose_tau); returns tau and
-        the fraction of validation queries whose label is among the P seeds."""
+        """Set tau from a validation split: the `fallback` quantile of the
+        validation queries' top softmax probabilities (ann_mlp_confidence_
+        threshold), so that fraction of in-distribution queries, and any query
+        the network is less sure of, falls back to plain ghost staging.
+        Returns tau and the fraction of validation queries whose label is
+        among the P seeds."""
         seeds, pmax = self.mlp.predict(val_queries, P=self.P, tau=0.0)
-        hit = (seeds == val_labels[:, None]).any(dim=1).cpu().numpy()
-        self.tau = choose_tau(pmax.cpu().numpy(), fallback)
-        return self.tau, float(hit.mean())
+        hit = (seeds == val_labels[:, None]).any(dim=1).float().mean().item()
+        self.tau = self.mlp.confidence_threshold(pmax, fallback)
+        return self.tau, float(hit)
 
     def seeds(self, queries, stream=None):
         s, pmax = self.mlp.predict(queries, P=self.P, tau=self.tau, stream=stream)

@@ -216,3 +216,85 @@ def test_forward_with_input_standardisation():
     err = np.abs(z.cpu().numpy().astype(np.float64) - f["z"])
     assert (err <= 2.0 ** -7 * scale + 1e-5).all(), float((err / (scale + 1e-12)).max())
     g.close()
+
+
+def ulp_diff(a, b):
+    """Distance in FP32 units in the last place (same-sign finite values)."""
+    ia = np.asarray(a, np.float32).view(np.int32).astype(np.int64)
+    ib = np.asarray(b, np.float32).view(np.int32).astype(np.int64)
+    return np.abs(ia - ib)
+
+
+@pytest.mark.parametrize("n,d", [(20_000, 96), (777, 256), (1, 64)])
+def test_fit_input_norm_vs_oracle(n, d):
+    """The device statistics (FP64 sums in chunk order) against the oracle's
+    FP64 definition: both round one FP64 value to FP32, and the two FP64
+    values differ only by summation order (relative 1e-15 at these sizes),
+    so the FP32 results agree within one unit in the last place. A constant
+    dimension takes the floored inverse."""
+    rng = np.random.default_rng(n)
+    X = (rng.standard_normal((n, d)) * rng.uniform(0.1, 60, d) + rng.uniform(-90, 90, d)).astype(np.float32)
+    X[:, 3] = 12.5
+    m = make_model(d, 128, 128, 64, seed=3)
+    g = gpu_mlp(m, 64)
+    g.fit_input_norm(torch.from_numpy(X).cuda())
+    mu, isd = g.get_input_norm()
+    want_mu, want_isd = M.input_norm_stats(X)
+    assert (ulp_diff(mu, want_mu) <= 1).all() and (ulp_diff(isd, want_isd) <= 1).all()
+    g.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 5000, 100_003])
+def test_confidence_threshold_vs_oracle(n):
+    """tau is a rank selection, so it is bit-exact: random top
+    probabilities with ties, at fallback fractions 0 .. 1 and beyond."""
+    rng = np.random.default_rng(n + 1)
+    v = rng.uniform(0.0, 1.0, n).astype(np.float32)
+    if n > 4:
+        v[: n // 4] = v[n // 2]
+        v[-1] = 1.0
+    m = make_model(64, 128, 128, 64, seed=3)
+    g = gpu_mlp(m, 64)
+    vt = torch.from_numpy(v).cuda()
+    for q in (0.0, 1e-4, 0.05, 0.5, 0.95, 1.0, 2.0):
+        assert g.confidence_threshold(vt, q) == M.lower_quantile(v, q), q
+    g.close()
+
+
+def test_checkpoint_resumes_training(tmp_path):
+    """Saving after a few AdamW steps and loading restores the step count
+    and the moments: the next step from the loaded copy gives the same
+    parameters, bit for bit, as the next step of the original."""
+    import paper_2507_17094_gb300 as A
+    d, out, n = 64, 128, 64
+    m = make_model(d, 128, 128, out, seed=11)
+    g = gpu_mlp(m, n)
+    rng = np.random.default_rng(12)
+    X = torch.from_numpy(rng.standard_normal((n, d)).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.integers(0, out, n).astype(np.int32)).cuda()
+    for _ in range(3):
+        g.train_step(X, y, lr=1e-3)
+    g.sync()
+    path = str(tmp_path / "mlp2.bin")
+    g.save(path)
+    h = A.MLP.load(path, max_batch=n)
+    for a, b in zip(g.get(0), h.get(0)):
+        assert np.array_equal(a, b)
+    g.train_step(X, y, lr=1e-3)
+    h.train_step(X, y, lr=1e-3)
+    g.sync()
+    h.sync()
+    for a, b in zip(g.get(0), h.get(0)):
+        assert np.array_equal(a, b)
+    # a version-1 file (parameters only) still loads, with a fresh optimizer
+    raw = open(path, "rb").read()
+    dims = np.frombuffer(raw[8:24], np.uint32)
+    body = 4 * (dims[1] * dims[0] + dims[1] + dims[2] * dims[1] + dims[2] + dims[3] * dims[2] + dims[3] + 2 * d)
+    p1 = str(tmp_path / "mlp1.bin")
+    open(p1, "wb").write(b"ANNMLP01" + raw[8:24 + int(body)])
+    k = A.MLP.load(p1, max_batch=n)
+    for a, b in zip(A.MLP.load(path, max_batch=n).get(0), k.get(0)):
+        assert np.array_equal(a, b)
+    g.close()
+    h.close()
+    k.close()

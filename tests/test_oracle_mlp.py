@@ -124,3 +124,46 @@ def test_standardisation_folds_into_the_first_layer():
     mi = m.copy()
     mi.mean, mi.inv_std = np.zeros(d, np.float32), np.ones(d, np.float32)
     assert np.array_equal(M.forward(mi, X)["z"], M.forward(m, X)["z"])
+
+
+def test_input_norm_stats_closed_forms():
+    """Column 0 is 0..n-1 (mean (n-1)/2, population variance (n^2-1)/12),
+    column 1 is constant (std 0: floored at 1e-6 of the largest std),
+    column 2 alternates -a, +a (mean 0, std a), column 3 is 2x column 0 + 5."""
+    n = 1001
+    i = np.arange(n, dtype=np.float64)
+    X = np.stack([i, np.full(n, 7.25), np.where(i % 2 == 0, -3.0, 3.0)[:n], 2 * i + 5], axis=1)
+    X[-1, 2] = 0.0   # n odd: make the +-a column balance exactly (mean 0)
+    mean, inv_std = M.input_norm_stats(X.astype(np.float32))
+    sd0 = np.sqrt((n * n - 1) / 12.0)
+    sd2 = np.sqrt(2 * 500 * 9.0 / n)
+    assert mean[0] == np.float32((n - 1) / 2) and mean[1] == np.float32(7.25) and mean[2] == 0.0
+    assert mean[3] == np.float32(n - 1 + 5)
+    np.testing.assert_allclose(inv_std[[0, 2, 3]], np.float32([1 / sd0, 1 / sd2, 1 / (2 * sd0)]), rtol=1e-7)
+    assert inv_std[1] == np.float32(1.0 / (1e-6 * 2 * sd0))
+
+
+def test_input_norm_stats_matches_numpy_and_a_planted_mistake_fails():
+    rng = np.random.default_rng(5)
+    X = (rng.standard_normal((3000, 40)) * rng.uniform(0.1, 50, 40) + rng.uniform(-100, 100, 40)).astype(np.float32)
+    mean, inv_std = M.input_norm_stats(X)
+    x = X.astype(np.float64)
+    assert np.array_equal(mean, x.mean(axis=0).astype(np.float32))
+    np.testing.assert_allclose(inv_std, (1.0 / x.std(axis=0)).astype(np.float32), rtol=2.5e-7)
+    # sample (n - 1) variance instead of the population one is detected
+    wrong = (1.0 / x.std(axis=0, ddof=1)).astype(np.float32)
+    assert not np.allclose(inv_std, wrong, rtol=1e-5)
+
+
+def test_lower_quantile_matches_numpy():
+    rng = np.random.default_rng(6)
+    for n in (1, 2, 7, 100, 5000):
+        v = rng.uniform(0, 1, n).astype(np.float32)
+        v[: n // 3] = v[n // 2]    # ties
+        for q in (0.0001, 0.05, 0.25, 0.5, 0.999, 1.0):
+            assert M.lower_quantile(v, q) == np.quantile(v, q, method="lower")
+    v = np.float32([0.9, 0.1, 0.5, 0.3, 0.7])
+    assert M.lower_quantile(v, 0.25) == np.float32(0.3)     # position floor(0.25 * 4) = 1
+    assert M.lower_quantile(v, 0.2) == np.float32(0.1)      # position floor(0.8) = 0
+    assert M.lower_quantile(v, 0.0) == 0.0 and M.lower_quantile(np.float32([]), 0.5) == 0.0
+    assert M.lower_quantile(v, 3.0) == np.float32(0.9)
