@@ -129,10 +129,13 @@ ann_status serve_launch(void *plan, const ServeRing &ring, uint32_t queries, cud
                         uint32_t stream_index);
 
 // The search launch (search.cu) with caller-chosen device scratch: the work
-// counter (zeroed on `stream` before the launch) and the error word.
+// counter (zeroed on `stream` before the launch) and the error word. With
+// `prof` (one row of ANN_PROFILE_STAGES x ANN_PROFILE_PHASES counters per
+// visited-table slot) the profiling build of the kernel runs instead.
 ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
                             const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
-                            ann_query_stats *stats, cudaStream_t stream, uint32_t *counter, int *err);
+                            ann_query_stats *stats, cudaStream_t stream, uint32_t *counter, int *err,
+                            unsigned long long *prof = nullptr);
 
 // Device row stride for `bytes` of payload: a multiple of 16 bytes (the
 // bulk-copy granule).

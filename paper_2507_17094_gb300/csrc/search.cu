@@ -50,6 +50,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <vector>
 
 #include "ann_internal.cuh"
 
@@ -101,7 +102,16 @@ struct Args {
     uint32_t *vtab;
     uint32_t vbits, vstride_bits, slot_base;
     uint32_t gbm_words;   // > 0: the ghost stage's visited set is a bitmap of this many words
+    // profile build only: per warp slot, ANN_PROFILE_STAGES x ANN_PROFILE_PHASES
+    // cycle counters (slot_base + warp slot selects a row)
+    unsigned long long *prof;
 };
+
+// Phases of the per-phase clock profile (ann_search_profile); a stage is the
+// ghost stage, the base stage, or the rerank and output.
+enum Phase : uint32_t { PH_SELECT = 0, PH_DGS, PH_VISIT, PH_GATHER, PH_DIST, PH_MERGE, PH_OTHER };
+enum ProfStage : uint32_t { PS_GHOST = 0, PS_BASE, PS_FINISH };
+static_assert(PH_OTHER < ANN_PROFILE_PHASES && PS_FINISH < ANN_PROFILE_STAGES, "profile table too small");
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 {
@@ -206,7 +216,7 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
     return __fadd_rn(s.x, s.y);
 }
 
-template <int ST>
+template <int ST, bool PROF = false>
 struct WarpSearch {
     const Args &a;
     uint8_t *base;
@@ -217,9 +227,28 @@ struct WarpSearch {
     ann_query_stats st;
     uint32_t *vt;        // this warp's visited table
     bool gbm = false;    // the visited set is the ghost bitmap (ghost stage, small ghost sets)
+    // profile build: this warp slot's counters, the stage being timed and the
+    // clock at the last phase boundary (lane 0)
+    unsigned long long *pacc = nullptr;
+    uint32_t pstage = 0;
+    long long pt = 0;
 
     __device__ WarpSearch(const Args &args, uint8_t *b, uint32_t slot)
-        : a(args), base(b), lane(threadIdx.x & 31), vt(args.vtab + ((size_t)slot << args.vstride_bits)) {}
+        : a(args), base(b), lane(threadIdx.x & 31), vt(args.vtab + ((size_t)slot << args.vstride_bits))
+    {
+        if (PROF) pacc = args.prof + (size_t)slot * (ANN_PROFILE_STAGES * ANN_PROFILE_PHASES);
+    }
+
+    // Profile build: charge the cycles since the last boundary to phase ph
+    // of the current stage (a fire-and-forget add to this slot's counter).
+    __device__ __forceinline__ void mark(uint32_t ph)
+    {
+        if (PROF && lane == 0) {
+            const long long t = clock64();
+            atomicAdd(pacc + pstage * ANN_PROFILE_PHASES + ph, (unsigned long long)(t - pt));
+            pt = t;
+        }
+    }
 
     // shared-memory arrays of this warp
     __device__ __forceinline__ float *q() const { return reinterpret_cast<float *>(base + a.lay.q); }
@@ -340,6 +369,7 @@ struct WarpSearch {
                 if (RST != ANN_F32) scale = __ldg(scales + v);
             }
             if (!wait_copies()) return false;
+            mark(PH_GATHER);
             const uint32_t r = lane >> 1;
             const float rs = __shfl_sync(0xffffffffu, scale, r);
             float part = 0.0f;
@@ -347,6 +377,7 @@ struct WarpSearch {
             const float other = __shfl_xor_sync(0xffffffffu, part, 1);
             if (r < rows && (lane & 1) == 0) out[b0 + r] = __fadd_rn(part, other);
             __syncwarp();
+            mark(PH_DIST);
         }
         return true;
     }
@@ -677,6 +708,7 @@ struct WarpSearch {
                 hash_make_room(chunk);
                 nc = collect_seeds(v, seed_ids, seed_key, j0, chunk);
                 j0 += chunk;
+                mark(PH_VISIT);
             } else {
                 if (it == T) break;
                 if (dgs_on && it >= it_cool) cool = true;
@@ -716,13 +748,18 @@ struct WarpSearch {
                     }
                 }
                 if (!wait_copies()) return false;
+                mark(PH_SELECT);
                 c_parents += np;
                 if (dgs_now) c_dgs += np;
                 hash_make_room(np * deg);
                 for (uint32_t pi = 0; pi < np; ++pi) {
                     uint32_t km = 0xffffffffu;
-                    if (dgs_now) km = dgs_keep(v, pi, n_keep, min_match, __shfl_sync(0xffffffffu, pscale, pi));
+                    if (dgs_now) {
+                        km = dgs_keep(v, pi, n_keep, min_match, __shfl_sync(0xffffffffu, pscale, pi));
+                        mark(PH_DGS);
+                    }
                     nc = collect_row(v, pi, km, nc);
+                    mark(PH_VISIT);
                 }
             }
             __syncwarp();
@@ -730,6 +767,7 @@ struct WarpSearch {
             if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
             c_rows += nc;
             merge(nc, lcap);
+            mark(PH_MERGE);
         }
         return true;
     }
@@ -744,6 +782,10 @@ struct WarpSearch {
         qid = qp.qid_base + qidx;
         st = ann_query_stats{};
         cnt = 0;
+        if (PROF) {
+            pt = clock64();
+            pstage = qp.entry != ANN_ENTRY_RANDOM ? PS_GHOST : PS_BASE;
+        }
         const uint32_t dpad = (a.d + 31) & ~31u;
         // read through L2 only: a serving ring rewrites query slots between
         // uses, and L1 is not kept coherent with those copies
@@ -763,6 +805,10 @@ struct WarpSearch {
             const View v = stage ? a.base : a.ghost;
             const uint32_t lcap = stage ? qp.L : qp.Lg;
             uint32_t rows = 0, iters = 0, parents = 0, dgs_parents = 0;
+            if (PROF && stage == 1 && ghost) {
+                mark(PH_OTHER);   // the rest of the ghost stage
+                pstage = PS_BASE;
+            }
             if (stage == 1 && ghost) {
                 // transition: the top g ghost results become the base queue;
                 // ghost ids are ascending, so the (dist, id) order carries over
@@ -780,6 +826,7 @@ struct WarpSearch {
                 for (uint32_t i = lane; i < cnt; i += 32) hash_insert(bi()[i]);
                 __syncwarp();
                 hash_count = cnt;
+                mark(PH_VISIT);
             }
             const bool seeded = !(stage == 1 && ghost);
             const bool use_given = stage == 0 && given;
@@ -799,6 +846,10 @@ struct WarpSearch {
                 st.ghost_parents = parents;
                 st.ghost_vec_rows = rows;
             }
+        }
+        if (PROF) {
+            mark(PH_OTHER);
+            pstage = PS_FINISH;
         }
         if (ok && qp.rerank) {
             // FP32 distances of the whole queue on the originals, then the top k
@@ -840,15 +891,16 @@ struct WarpSearch {
         }
         if (stats_out && lane == 0) *stats_out = st;
         __syncwarp();
+        mark(PH_OTHER);
     }
 };
 
-template <int ST>
+template <int ST, bool PROF = false>
 __global__ void __launch_bounds__(128, 6) search_kernel(const Args a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSearch<ST> ws(a, smem + (size_t)warp * a.lay.total, a.slot_base + blockIdx.x * (blockDim.x >> 5) + warp);
+    WarpSearch<ST, PROF> ws(a, smem + (size_t)warp * a.lay.total, a.slot_base + blockIdx.x * (blockDim.x >> 5) + warp);
     if (lane == 0) mbar_init(ws.bar(), 1);
     fence_mbar_init();
     __syncwarp();
@@ -955,12 +1007,13 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
     return L;
 }
 
-template <int ST>
+template <int ST, bool PROF = false>
 cudaError_t launch(const Args &a, int warps, int blocks, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(search_kernel<ST, PROF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    search_kernel<ST><<<blocks, warps * 32, smem, st>>>(a);
+    search_kernel<ST, PROF><<<blocks, warps * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1147,7 +1200,8 @@ using namespace planning;
 
 ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
                             const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
-                            ann_query_stats *stats, cudaStream_t stream, uint32_t *counter, int *err)
+                            ann_query_stats *stats, cudaStream_t stream, uint32_t *counter, int *err,
+                            unsigned long long *prof)
 {
     QParams q;
     ann_status s = derive_qparams(ix, p, given ? n_given : 0, &q);
@@ -1170,6 +1224,7 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
     a.stats = stats;
     a.counter = counter;
     a.err = err;
+    a.prof = prof;
     const uint64_t want = ((uint64_t)nq + warps - 1) / warps;
     // every resident warp needs its own visited table
     const uint64_t cap = std::min<uint64_t>((uint64_t)nb * ix->num_sms, ix->visited.slots / (uint32_t)warps);
@@ -1179,10 +1234,18 @@ ann_status search_launch_ex(ann_index *ix, const float *queries, uint32_t nq, co
     if (ix->busy_set && ix->busy_stream != stream) ANN_CUDA(cudaStreamWaitEvent(stream, ix->busy, 0));
     ANN_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), stream));
     cudaError_t e;
-    switch (ix->storage) {
-    case ANN_F32: e = launch<ANN_F32>(a, warps, blocks, smem, stream); break;
-    case ANN_F16: e = launch<ANN_F16>(a, warps, blocks, smem, stream); break;
-    default: e = launch<ANN_E4M3>(a, warps, blocks, smem, stream); break;
+    if (prof) {
+        switch (ix->storage) {
+        case ANN_F32: e = launch<ANN_F32, true>(a, warps, blocks, smem, stream); break;
+        case ANN_F16: e = launch<ANN_F16, true>(a, warps, blocks, smem, stream); break;
+        default: e = launch<ANN_E4M3, true>(a, warps, blocks, smem, stream); break;
+        }
+    } else {
+        switch (ix->storage) {
+        case ANN_F32: e = launch<ANN_F32>(a, warps, blocks, smem, stream); break;
+        case ANN_F16: e = launch<ANN_F16>(a, warps, blocks, smem, stream); break;
+        default: e = launch<ANN_E4M3>(a, warps, blocks, smem, stream); break;
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "search_kernel launch");
     ANN_CUDA(cudaEventRecord(ix->busy, stream));
@@ -1246,7 +1309,7 @@ ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const
 {
     if (!ix) { set_error("ann_search: NULL index or params"); return ANN_EINVAL; }
     return search_launch_ex(ix, queries, nq, p, given, n_given, ids, dists, stats, stream, ix->d_counter,
-                            ix->d_error);
+                            ix->d_error, nullptr);
 }
 
 }  // namespace ann
@@ -1306,6 +1369,41 @@ ann_status ann_search_host(ann_index *ix, const float *queries, uint32_t nq, con
             if (e != cudaSuccess) s = cuda_fail(e, "ann_search_host download");
         }
     }
+    leave_device(ix->device, prev);
+    return s;
+}
+
+// The search with the per-phase clock profile: the same results as
+// ann_search, from a build of the kernel that reads the SM clock at every
+// phase boundary and charges each warp's elapsed cycles to (stage, phase).
+ann_status ann_search_profile(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
+                              const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
+                              uint64_t *cycles, void *stream)
+{
+    if (!ix || !cycles) { set_error("ann_search_profile: NULL index or cycles"); return ANN_EINVAL; }
+    constexpr uint32_t kCells = ANN_PROFILE_STAGES * ANN_PROFILE_PHASES;
+    for (uint32_t i = 0; i < kCells; ++i) cycles[i] = 0;
+    int prev = -1;
+    ann_status s = enter_device(ix->device, &prev, "ann_search_profile");
+    if (s != ANN_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t cells = (size_t)ix->visited.slots * kCells;
+    unsigned long long *acc = nullptr;
+    cudaError_t e = cudaMalloc(&acc, cells * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, cells * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) s = cuda_fail(e, "ann_search_profile counters");
+    if (s == ANN_OK)
+        s = search_launch_ex(ix, queries, nq, p, given, n_given, ids, dists, nullptr, st, ix->d_counter,
+                             ix->d_error, acc);
+    if (s == ANN_OK) {
+        std::vector<unsigned long long> h(cells);
+        e = cudaMemcpyAsync(h.data(), acc, cells * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "ann_search_profile");
+        else
+            for (size_t i = 0; i < cells; ++i) cycles[i % kCells] += h[i];
+    }
+    if (acc) cudaFree(acc);
     leave_device(ix->device, prev);
     return s;
 }

@@ -56,7 +56,8 @@ def load_dataset(spec: WorkloadSpec, off_fraction: float = 0.0, device=None, use
     Q = make_queries(spec, off_fraction=off_fraction)
     if verbose:
         print(f"[dataset] {spec.name}: vectors in {time.time() - t0:.1f}s", file=sys.stderr, flush=True)
-    G = build_graph(X, spec.degree, spec.knn_k, spec.graph, device=device, seed=spec.seeds["base"])
+    G = build_graph(X, spec.degree, spec.knn_k, spec.graph, device=device, seed=spec.seeds["base"],
+                    n_near=spec.n_near)
     if verbose:
         print(f"[dataset] {spec.name}: graph in {time.time() - t0:.1f}s", file=sys.stderr, flush=True)
     S = ghost_sample(spec.n, spec.ghost_n, spec.seeds["ghost"])

@@ -69,10 +69,15 @@ class Mixture:
 
 def make_mixture(d: int, n_clusters: int, seed: int, *, center_range=(0.0, 100.0),
                  sigma=8.0, sigma_range=None, zipf_s: Optional[float] = None,
-                 normalize=False, integer_range=None) -> Mixture:
+                 normalize=False, integer_range=None, spectrum_decay: Optional[float] = None) -> Mixture:
     """Build a mixture: centers ~ U[center_range]^d; sigma fixed (isotropic) or
     per-cluster per-dimension ~ U[sigma_range]; weights equal or Zipf(s) over
-    a seeded permutation of the clusters."""
+    a seeded permutation of the clusters. With ``spectrum_decay`` a > 0 the
+    isotropic spread becomes a power-law spectrum: in each cluster the
+    dimension of (seeded, per-cluster) rank r has standard deviation
+    proportional to (r + 1)^-a, scaled so the total variance stays d sigma^2
+    (a = 0.5 concentrates the variance in about 20 of 256 dimensions by the
+    participation ratio, as the spectra of real descriptors do)."""
     rng = np.random.Generator(np.random.PCG64(seed ^ 0x5EED))
     lo, hi = center_range
     centers = rng.uniform(lo, hi, size=(n_clusters, d))
@@ -85,6 +90,11 @@ def make_mixture(d: int, n_clusters: int, seed: int, *, center_range=(0.0, 100.0
         w = w[rng.permutation(n_clusters)]
     else:
         w = np.ones(n_clusters)
+    if spectrum_decay:
+        prof = (np.arange(1, d + 1, dtype=np.float64)) ** (-float(spectrum_decay))
+        prof *= np.sqrt(d / (prof * prof).sum())
+        ranks = np.argsort(rng.random((n_clusters, d)), axis=1)
+        sigmas = sigmas * prof[ranks]
     return Mixture(centers, sigmas, w / w.sum(), normalize, integer_range)
 
 
@@ -110,6 +120,8 @@ class WorkloadSpec:
     normalize: bool = False
     integer_range: Optional[Tuple[int, int]] = None
     search: dict = field(default_factory=dict)
+    spectrum_decay: Optional[float] = None
+    n_near: int = 2                # partitions beside a node's own in its kNN pool
 
     @property
     def seeds(self) -> dict:
@@ -121,7 +133,8 @@ class WorkloadSpec:
         return make_mixture(self.d, self.n_clusters, self.seeds["base"],
                             center_range=self.center_range, sigma=self.sigma,
                             sigma_range=self.sigma_range, zipf_s=self.zipf_s,
-                            normalize=self.normalize, integer_range=self.integer_range)
+                            normalize=self.normalize, integer_range=self.integer_range,
+                            spectrum_decay=self.spectrum_decay)
 
     def scaled(self, n: int, nq: Optional[int] = None, n_clusters: Optional[int] = None,
                ghost_n: Optional[int] = None) -> "WorkloadSpec":
