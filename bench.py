@@ -495,6 +495,16 @@ def run_ours(args):
     bytes_per_launch = float(algorithmic_bytes(st_np, spec, form["storage"], bool(form["rerank"])).sum())
     head_recall = next(s["recall"] for s in results[headline]["sweep"] if s["itopk"] == L)
 
+    # per-phase split of the headline search (a separate profiling build of
+    # the kernel, run once outside the timed region; Section 5.5's method)
+    phase_profile = None
+    if form["entry"] != 2:
+        _, _, cyc = ix.search_profile(Qd, stream=stream, **p)
+        tot = float(cyc.sum())
+        phase_profile = {"kernel": "search_kernel profiling build (same results)", "total_warp_cycles": tot,
+                         "share": {f"{sn}/{pn}": float(cyc[i, j]) / tot
+                                   for i, sn in enumerate(A.PROFILE_STAGE_NAMES)
+                                   for j, pn in enumerate(A.PROFILE_PHASE_NAMES) if cyc[i, j] > 0}}
     for _ in range(args.warmup):
         head_run(p)
     torch.cuda.synchronize(dev)
@@ -657,6 +667,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "cpu_baseline": cpu_baseline,
         "serving": serving,
+        "phase_profile": phase_profile,
     }
     for le in entries.values():
         le.close()

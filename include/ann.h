@@ -173,6 +173,25 @@ ann_status ann_search_host(ann_index *index, const float *queries, uint32_t nq,
 ann_status ann_search_host_noalloc(ann_index *index, const float *queries, uint32_t nq,
                                    const ann_search_params *params, uint32_t *ids, float *dists, void *stream);
 
+/* Per-phase time of the search (the measurement of Section 5.5, Fig. 11:
+ * SM clock readings around the parts of the kernel). The same search and
+ * results as ann_search (ids, dists device nq x k; no stats), run by a build
+ * of the kernel that reads the clock at every phase boundary and adds each
+ * warp's elapsed cycles to cycles[stage * ANN_PROFILE_PHASES + phase] (host,
+ * ANN_PROFILE_STAGES x ANN_PROFILE_PHASES uint64, summed over all warps;
+ * zeroed first). Stages: 0 ghost stage, 1 base graph, 2 rerank and output.
+ * Phases: 0 parent selection and the adjacency / direction / parent-row
+ * fetch, 1 DGS selection, 2 visited-set test-and-insert (and seeding),
+ * 3 waiting for gathered rows, 4 distances, 5 merge, 6 the rest (query load,
+ * set clears, stage switch, output). Cycles are per-warp wall time, so they
+ * include time a warp waits while others issue. Allocates a temporary of
+ * 192 bytes per warp slot; synchronous on `stream`. */
+#define ANN_PROFILE_STAGES 3u
+#define ANN_PROFILE_PHASES 8u
+ann_status ann_search_profile(ann_index *index, const float *queries, uint32_t nq, const ann_search_params *params,
+                              const uint32_t *given_seeds, uint32_t n_given, uint32_t *ids, float *dists,
+                              uint64_t *cycles, void *stream);
+
 /* Ghost index of each node id (device ids, n) by binary search over the
  * ascending ghost ids, into out (device, n); ANN_INVALID_ID where an id is
  * not a ghost node. Turns ghost-staging results into training labels. */

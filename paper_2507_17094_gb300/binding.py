@@ -20,12 +20,17 @@ from .build import LIB
 INVALID = 0xFFFFFFFF
 F32, F16, E4M3 = 0, 1, 2
 ENTRY_RANDOM, ENTRY_GHOST, ENTRY_GIVEN_GHOST = 0, 1, 2
+# ann_search_profile's table: stages x phases (see include/ann.h)
+PROFILE_STAGES, PROFILE_PHASES = 3, 8
+PROFILE_STAGE_NAMES = ("ghost", "base", "finish")
+PROFILE_PHASE_NAMES = ("select+adjacency", "dgs", "visited", "gather_wait", "distance", "merge", "other", "unused")
 STATUS = {0: "ANN_OK", 1: "ANN_EINVAL", 2: "ANN_ENOMEM", 3: "ANN_ECUDA", 4: "ANN_EIO", 5: "ANN_ETIMEOUT",
           6: "ANN_EBUSY", 7: "ANN_EDEVICE"}
 
 # Every symbol include/ann.h declares (checked by the tests).
 EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_index_free", "ann_index_info",
-           "ann_index_export", "ann_search", "ann_search_host", "ann_search_host_noalloc", "ann_sync",
+           "ann_index_export", "ann_search", "ann_search_host", "ann_search_host_noalloc", "ann_search_profile",
+           "ann_sync",
            "ann_encode", "ann_dir_table", "ann_mlp_create", "ann_mlp_free", "ann_mlp_set_params", "ann_mlp_get",
            "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_train_epochs", "ann_mlp_predict", "ann_mlp_sync",
            "ann_mlp_save", "ann_mlp_load", "ann_mlp_set_input_norm", "ann_mlp_get_input_norm",
@@ -89,6 +94,7 @@ def lib() -> C.CDLL:
             L.ann_search.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp, vp]
             L.ann_search_host.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp]
             L.ann_search_host_noalloc.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, vp, vp]
+            L.ann_search_profile.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp, vp]
             L.ann_sync.argtypes = [vp, vp]
             L.ann_selftest_timeout.argtypes = [vp]
             f32 = C.c_float
@@ -252,6 +258,23 @@ class Index:
         _check(lib().ann_search_host_noalloc(self._h, _np_ptr(Q), nq, C.byref(p), _np_ptr(ids), _np_ptr(dists),
                                              _stream_ptr(stream)))
         return ids, dists
+
+    def search_profile(self, queries, given=None, stream=None, **params):
+        """The search through ann_search_profile: (ids, dists, cycles) with
+        cycles a (stage, phase) uint64 array of summed warp cycles."""
+        import torch
+        p = make_params(**params)
+        nq = queries.shape[0]
+        assert queries.is_cuda and queries.dtype == torch.float32 and queries.is_contiguous()
+        ids = torch.empty((nq, p.k), dtype=torch.int32, device=queries.device)
+        dists = torch.empty((nq, p.k), dtype=torch.float32, device=queries.device)
+        cyc = np.zeros((PROFILE_STAGES, PROFILE_PHASES), dtype=np.uint64)
+        g_ptr, n_given = None, 0
+        if given is not None:
+            g_ptr, n_given = given.data_ptr(), given.shape[1]
+        _check(lib().ann_search_profile(self._h, queries.data_ptr(), nq, C.byref(p), g_ptr, n_given, ids.data_ptr(),
+                                        dists.data_ptr(), _np_ptr(cyc), _stream_ptr(stream)))
+        return ids, dists, cyc
 
     def sync(self, stream=None):
         _check(lib().ann_sync(self._h, _stream_ptr(stream)))

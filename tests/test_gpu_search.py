@@ -237,3 +237,31 @@ def test_bounded_wait_timeout_is_reported_and_recoverable():
     gi.sync()                                   # the error word was cleared
     g, o = c.run(O.F32, seed=4001, itopk=64, max_iters=64, entry=1)
     assert_parity(g, o)
+
+
+@pytest.mark.parametrize("params", [dict(itopk=32, max_iters=48, entry=1, dgs_discard=0.75, ghost_search_width=4,
+                                         ghost_max_iters=12),
+                                    dict(itopk=64, max_iters=64, entry=0, rerank=1)])
+def test_search_profile_same_results_and_phases(params):
+    """The profiling build returns what ann_search returns, and charges
+    cycles to the phases that ran: no ghost stage without ghost entry, no
+    DGS cycles without DGS."""
+    import paper_2507_17094_gb300 as A
+    c = tiny_case()
+    storage = O.F16 if params.get("rerank") else O.F32
+    gi = c.gpu_index(storage)
+    Q = torch.from_numpy(c.Q).cuda()
+    ids, d, _ = gi.search(Q, seed=3, **params)
+    pids, pd, cyc = gi.search_profile(Q, seed=3, **params)
+    torch.cuda.synchronize()
+    assert torch.equal(ids, pids) and torch.equal(d, pd)
+    S = {n: i for i, n in enumerate(A.PROFILE_STAGE_NAMES)}
+    P = {n: i for i, n in enumerate(A.PROFILE_PHASE_NAMES)}
+    base = cyc[S["base"]]
+    assert base[P["select+adjacency"]] > 0 and base[P["gather_wait"]] > 0 and base[P["distance"]] > 0
+    assert base[P["merge"]] > 0 and base[P["visited"]] > 0
+    assert (cyc[S["ghost"]].sum() > 0) == (params["entry"] == 1)
+    assert (base[P["dgs"]] > 0) == (params.get("dgs_discard", 0) > 0)
+    assert cyc[:, P["unused"]].sum() == 0
+    if params.get("rerank"):
+        assert cyc[S["finish"], P["distance"]] > 0
