@@ -52,8 +52,13 @@ typedef enum { ANN_F32 = 0, ANN_F16 = 1, ANN_E4M3 = 2 } ann_storage;
 typedef enum {
     ANN_ENTRY_RANDOM = 0,      /* Section 2.2 Step 2: m random nodes */
     ANN_ENTRY_GHOST = 1,       /* Section 3.2.2: ghost staging from random ghost nodes */
-    ANN_ENTRY_GIVEN_GHOST = 2  /* ghost staging from caller-given ghost nodes (learned entry);
+    ANN_ENTRY_GIVEN_GHOST = 2, /* ghost staging from caller-given ghost nodes (learned entry);
                                   a query whose first given id is ANN_INVALID_ID falls back to 1 */
+    ANN_ENTRY_GIVEN_BASE = 3   /* Step 2 from caller-given base nodes instead of random ones (the
+                                  start of an extended path, Section 3.1.2: the node I(z) of this
+                                  shard linked to the previous shard's result z); invalid or
+                                  out-of-range ids are skipped, and a query whose first given id is
+                                  ANN_INVALID_ID falls back to 0 */
 } ann_entry;
 
 /* Search parameters. Paper notation: itopk = l (queue size), search_width =
@@ -139,7 +144,8 @@ ann_status ann_index_export(const ann_index *index, int which, void *host_dst, u
 
 /* Batched search (Section 2.2 Steps 1-4, Section 3.2.2, Section 3.3.2).
  *   queries      device, nq x dim FP32 row-major
- *   given_seeds  device, nq x n_given ghost indices (entry ANN_ENTRY_GIVEN_GHOST), else NULL
+ *   given_seeds  device, nq x n_given ghost indices (entry ANN_ENTRY_GIVEN_GHOST) or base
+ *                node ids (entry ANN_ENTRY_GIVEN_BASE), else NULL
  *   ids, dists   device, nq x k (caller-owned)
  *   stats        device, nq ann_query_stats, or NULL
  *   stream       cudaStream_t (NULL = legacy default stream)

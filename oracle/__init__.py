@@ -279,10 +279,12 @@ def make_params(index: OracleIndex, k=10, itopk=64, search_width=1, max_iters=64
 
 
 def search(index: OracleIndex, Q: np.ndarray, given_ghost_seeds: Optional[np.ndarray] = None,
-           threads: Optional[int] = None, **kw):
+           threads: Optional[int] = None, given_seeds: Optional[np.ndarray] = None, **kw):
     """Batched beam search (Section 2.2) with ghost staging (Section 3.2.2)
-    and DGS (Section 3.3.2). Returns (ids uint32 nq x k, dists float32
-    nq x k, per-query counters)."""
+    and DGS (Section 3.3.2). Given seeds (nq x P) are ghost indices for
+    entry 2 (`given_ghost_seeds`) or base node ids for entry 3
+    (`given_seeds`, the start of an extended path, Section 3.1.2). Returns
+    (ids uint32 nq x k, dists float32 nq x k, per-query counters)."""
     Q = np.ascontiguousarray(Q, dtype=np.float32)
     p = make_params(index, **kw)
     nq = Q.shape[0]
@@ -291,6 +293,10 @@ def search(index: OracleIndex, Q: np.ndarray, given_ghost_seeds: Optional[np.nda
     cnt = np.zeros(nq, dtype=COUNTER_DTYPE)
     P = 0
     g = None
+    if given_ghost_seeds is not None and given_seeds is not None:
+        raise ValueError("give ghost seeds or base seeds, not both")
+    if given_seeds is not None:
+        given_ghost_seeds = given_seeds
     if given_ghost_seeds is not None:
         g = np.ascontiguousarray(given_ghost_seeds, dtype=np.uint32)
         P = g.shape[1]

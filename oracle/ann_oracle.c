@@ -31,7 +31,7 @@
 
 enum { OR_F32 = 0, OR_F16 = 1, OR_E4M3 = 2 };
 enum { OR_UNEXPANDED = 0, OR_PARTIAL = 1, OR_EXPANDED = 2 };
-enum { OR_ENTRY_RANDOM = 0, OR_ENTRY_GHOST = 1, OR_ENTRY_GIVEN_GHOST = 2 };
+enum { OR_ENTRY_RANDOM = 0, OR_ENTRY_GHOST = 1, OR_ENTRY_GIVEN_GHOST = 2, OR_ENTRY_GIVEN_BASE = 3 };
 
 /* ------------------------------------------------------------------------ */
 /* Number formats: round-to-nearest-even into a binary format with p       */
@@ -283,7 +283,8 @@ typedef struct {
     uint32_t n_keep;        /* DGS keeps the top n_keep neighbours; >= degree disables DGS */
     uint32_t it_cool;       /* first cool-down iteration (no selection from here on) */
     uint32_t reexpand;      /* 1: DGS parents are PARTIAL and expand fully in cool-down */
-    uint32_t entry;         /* 0 random, 1 ghost staging, 2 ghost staging from given seeds */
+    uint32_t entry;         /* 0 random, 1 ghost staging, 2 ghost staging from given seeds,
+                               3 given base nodes as the Step-2 seeds */
     uint32_t Lg;            /* ghost queue size */
     uint32_t Tg;            /* ghost iterations, random ghost seeds */
     uint32_t Tg_given;      /* ghost iterations, given ghost seeds */
@@ -473,16 +474,27 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
 
     or_graph base = {ix->n, ix->d, ix->deg, ix->Xs, NULL, ix->G, ix->dir};
     int use_ghost = (p->entry == OR_ENTRY_GHOST || p->entry == OR_ENTRY_GIVEN_GHOST) && ix->nS > 0;
+    const uint32_t *given_base = (p->entry == OR_ENTRY_GIVEN_BASE && c->given) ? c->given + (uint64_t)qi * c->P : NULL;
+    if (given_base && given_base[0] == OR_INVALID) given_base = NULL;   /* fall back to random seeds */
     if (!use_ghost) {
         /* Steps 1-3: m random nodes, deduplicated by the visited set without
          * redraw, sorted into the queue. Node j of query qid is
          * splitmix64(key ^ (qid << 32) ^ j) mod n with key = splitmix64(seed):
          * mixing the seed first keeps seeds that differ in low bits from
-         * drawing permutations of one seed set. */
+         * drawing permutations of one seed set. With given base nodes (the
+         * first node of an extended path, Section 3.1.2), those nodes are the
+         * seeds instead: invalid or out-of-range ones are skipped. */
         const uint64_t key = oracle_splitmix64(p->seed);
         uint32_t nc = 0;
-        for (uint32_t j = 0; j < m; ++j) {
-            uint64_t v = oracle_splitmix64(key ^ (qid << 32) ^ (uint64_t)j) % ix->n;
+        const uint32_t ms = given_base ? c->P : m;
+        for (uint32_t j = 0; j < ms; ++j) {
+            uint64_t v;
+            if (given_base) {
+                if (given_base[j] == OR_INVALID || given_base[j] >= ix->n) continue;
+                v = given_base[j];
+            } else {
+                v = oracle_splitmix64(key ^ (qid << 32) ^ (uint64_t)j) % ix->n;
+            }
             if (bit_get(st.visited, v)) continue;
             bit_set(st.visited, v);
             st.tmp[nc].dist = dist_f32(q, ix->Xs + v * ix->d, ix->d);

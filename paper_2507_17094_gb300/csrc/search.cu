@@ -63,6 +63,17 @@ constexpr uint64_t kGhostTag = 0x67686F7374ull;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kMaxDegWords = ANN_MAX_DEGREE / 32;
 
+// Entries that run the ghost stage first.
+__host__ __device__ __forceinline__ bool ghost_entry(uint32_t e)
+{
+    return e == ANN_ENTRY_GHOST || e == ANN_ENTRY_GIVEN_GHOST;
+}
+// Entries that read a row of caller-given seeds.
+__host__ __device__ __forceinline__ bool given_entry(uint32_t e)
+{
+    return e == ANN_ENTRY_GIVEN_GHOST || e == ANN_ENTRY_GIVEN_BASE;
+}
+
 struct View {
     const uint8_t *codes;
     const float *scales;   // nullptr for FP32
@@ -784,7 +795,7 @@ struct WarpSearch {
         cnt = 0;
         if (PROF) {
             pt = clock64();
-            pstage = qp.entry != ANN_ENTRY_RANDOM ? PS_GHOST : PS_BASE;
+            pstage = ghost_entry(qp.entry) ? PS_GHOST : PS_BASE;
         }
         const uint32_t dpad = (a.d + 31) & ~31u;
         // read through L2 only: a serving ring rewrites query slots between
@@ -792,12 +803,12 @@ struct WarpSearch {
         #pragma unroll 1
         for (uint32_t i = lane; i < dpad; i += 32) q()[i] = i < a.d ? __ldcg(qg + i) : 0.0f;
         __syncwarp();
-        const bool ghost = qp.entry != ANN_ENTRY_RANDOM;
+        const bool ghost = ghost_entry(qp.entry);
         gbm = ghost && a.gbm_words > 0;
         hash_clear();
         const uint32_t *given = nullptr;
-        if (qp.entry == ANN_ENTRY_GIVEN_GHOST && given_row && given_row[0] != ANN_INVALID_ID)
-            given = given_row;   // else: fall back to random ghost seeds
+        if (given_entry(qp.entry) && given_row && given_row[0] != ANN_INVALID_ID)
+            given = given_row;   // else: fall back to random (ghost) seeds
         // stage 0: the ghost stage (Section 3.2.2) on the ghost graph; stage
         // 1: the search on the base graph. One loop body serves both.
         bool ok = true;
@@ -829,7 +840,9 @@ struct WarpSearch {
                 mark(PH_VISIT);
             }
             const bool seeded = !(stage == 1 && ghost);
-            const bool use_given = stage == 0 && given;
+            // given seeds start the ghost stage (learned entry) or, without
+            // one, the base stage (an extended path's first node)
+            const bool use_given = given && (stage == 0 || !ghost);
             ok = iterate<ST>(v, use_given ? given : nullptr,
                              seeded ? (use_given ? qp.n_given : (stage ? qp.m : v.deg)) : 0,
                              splitmix64(qp.seed ^ (stage ? 0 : kGhostTag)), lcap, stage ? qp.W : qp.Wg,
@@ -911,7 +924,7 @@ __global__ void __launch_bounds__(128, 6) search_kernel(const Args a)
         if (qi >= a.nq) break;
         const QParams &qp = a.qp;
         ws.run(qp, qi, a.queries + (uint64_t)qi * a.d,
-               (qp.entry == ANN_ENTRY_GIVEN_GHOST && a.given) ? a.given + (uint64_t)qi * qp.n_given : nullptr,
+               (given_entry(qp.entry) && a.given) ? a.given + (uint64_t)qi * qp.n_given : nullptr,
                a.out_ids + (uint64_t)qi * qp.k, a.out_dists + (uint64_t)qi * qp.k, a.stats ? a.stats + qi : nullptr);
         if (ws.failed) break;
     }
@@ -1058,12 +1071,12 @@ ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint3
         set_error("ann_search: DGS needs an index built with the direction table");
         return ANN_EINVAL;
     }
-    if (p->entry > ANN_ENTRY_GIVEN_GHOST || (p->entry != ANN_ENTRY_RANDOM && ix->n_ghost == 0)) {
-        set_error("ann_search: entry %u needs a ghost set", p->entry);
+    if (p->entry > ANN_ENTRY_GIVEN_BASE || (ghost_entry(p->entry) && ix->n_ghost == 0)) {
+        set_error("ann_search: entry %u is unknown or needs a ghost set", p->entry);
         return ANN_EINVAL;
     }
-    if (p->entry == ANN_ENTRY_GIVEN_GHOST && n_given == 0) {
-        set_error("ann_search: given ghost seeds missing");
+    if (given_entry(p->entry) && n_given == 0) {
+        set_error("ann_search: given seeds missing");
         return ANN_EINVAL;
     }
     if (p->rerank && !ix->x32) {
@@ -1130,9 +1143,9 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     a.d = ix->dim;
     a.w = ix->words;
     a.qp = q;
-    const uint32_t cap_buf = std::max(q.L, q.entry != ANN_ENTRY_RANDOM ? q.Lg : 1u);
+    const uint32_t cap_buf = std::max(q.L, ghost_entry(q.entry) ? q.Lg : 1u);
     uint32_t cap_cand = std::max(q.W * deg, 32u);
-    if (q.entry != ANN_ENTRY_RANDOM) cap_cand = std::max(cap_cand, q.Wg * ix->ghost_degree);
+    if (ghost_entry(q.entry)) cap_cand = std::max(cap_cand, q.Wg * ix->ghost_degree);
     cap_cand = round_up(cap_cand, 32);
     a.cap_cand = cap_cand;
     const uint32_t adj_words = std::max(q.W * ix->deg_pad, q.Wg * ix->gdeg_pad);
@@ -1152,7 +1165,7 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     a.vstride_bits = ix->visited.bits;
     a.vbits = ix->visited.bits;   // 4,096 entries: measured faster than 2,048 or 1,024 (L2-resident either way)
     a.slot_base = 0;
-    a.gbm_words = (q.entry != ANN_ENTRY_RANDOM && ix->n_ghost <= kGhostBitmapMax) ? (ix->n_ghost + 31) / 32 : 0;
+    a.gbm_words = (ghost_entry(q.entry) && ix->n_ghost <= kGhostBitmapMax) ? (ix->n_ghost + 31) / 32 : 0;
     warps = 4;
     Layout lay{};
     for (;;) {
@@ -1340,7 +1353,7 @@ ann_status ann_search_host(ann_index *ix, const float *queries, uint32_t nq, con
     if (s != ANN_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t qb = (size_t)nq * ix->dim * 4;
-    const size_t gb = (p->entry == ANN_ENTRY_GIVEN_GHOST && given) ? (size_t)nq * n_given * 4 : 0;
+    const size_t gb = (given_entry(p->entry) && given) ? (size_t)nq * n_given * 4 : 0;
     const size_t ob = (size_t)nq * p->k * 4;
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t need = up(qb) + up(gb) + 2 * up(ob);

@@ -127,6 +127,10 @@ ann_status ann_server_create(ann_index *ix, const ann_server_config *cfg, ann_ml
         return ANN_EINVAL;
     }
     const ann_search_params &mp = cfg->max_params;
+    if (mp.entry > ANN_ENTRY_GIVEN_GHOST) {
+        set_error("ann_server_create: entry %u is not served (given base seeds need ann_search)", mp.entry);
+        return ANN_EINVAL;
+    }
     if (mp.entry == ANN_ENTRY_GIVEN_GHOST && (!mlp || cfg->seeds_per_query == 0 || cfg->seeds_per_query > 8)) {
         set_error("ann_server_create: the learned entry needs an MLP and 1..8 seeds per query");
         return ANN_EINVAL;
@@ -199,7 +203,7 @@ ann_status ann_server_submit(ann_server *s, uint64_t req_id, const float *querie
         (p->ghost_search_width ? p->ghost_search_width : 1) > (mp.ghost_search_width ? mp.ghost_search_width : 1) ||
         ((p->dgs_discard > 0.0f || p->dgs_min_match > 0.0f) &&
          !(mp.dgs_discard > 0.0f || mp.dgs_min_match > 0.0f)) ||
-        (p->rerank && !mp.rerank) ||
+        (p->rerank && !mp.rerank) || p->entry > ANN_ENTRY_GIVEN_GHOST ||
         (p->entry != ANN_ENTRY_RANDOM && mp.entry == ANN_ENTRY_RANDOM) ||
         (p->entry == ANN_ENTRY_GIVEN_GHOST && !s->P) ||
         (p->entry != ANN_ENTRY_RANDOM && (p->ghost_itopk ? p->ghost_itopk : std::min(p->itopk, 64u)) >
