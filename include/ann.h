@@ -35,6 +35,8 @@ extern "C" {
 #define ANN_MAX_DIM 1024u
 #define ANN_MAX_DEGREE 128u
 #define ANN_MAX_WIDTH 8u
+#define ANN_MAX_SHARDS 16u      /* shards in one path-extension ring */
+#define ANN_MAX_FORWARD 8u      /* nodes forwarded per query between shards */
 
 typedef enum {
     ANN_OK = 0,
@@ -197,6 +199,50 @@ ann_status ann_search_host_noalloc(ann_index *index, const float *queries, uint3
 ann_status ann_search_profile(ann_index *index, const float *queries, uint32_t nq, const ann_search_params *params,
                               const uint32_t *given_seeds, uint32_t n_given, uint32_t *ids, float *dists,
                               uint64_t *cycles, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Pipelining-based path extension (Section 3.1.2, Eq. 3, Section 4) with
+ * the shards as separate indexes on one GPU. The dataset is partitioned into
+ * N shards (each an ann_index over its own points, local ids 0..n_i-1, with
+ * its own graph and, optionally, ghost set); shard i links every node u to
+ * I(u), its nearest node in shard (i + 1) mod N (Eq. 3). A search splits the
+ * queries into N chunks (chunk c = rows [c nq / N, (c + 1) nq / N)); chunk c
+ * starts on shard c with the entry of `params` (random or ghost staging) and
+ * continues on shards c + 1, ... from I(z) for the best n_forward nodes z of
+ * its previous local result (the paper forwards one), until it has searched
+ * every shard; the N local top-k lists are reduced to the top k by
+ * (distance, dataset id). With n_forward = 0 every shard starts from the
+ * entry of `params`: the paper's baseline sharding. The RNG stream of query
+ * row r is qid_base + r on every shard.
+ * ------------------------------------------------------------------------ */
+typedef struct ann_shards ann_shards;
+/* A ring over n_shards (1..ANN_MAX_SHARDS) indexes on one device with equal
+ * dimension and storage; global_ids[i] (host, n_i uint32) maps shard i's
+ * local ids to dataset ids (copied). The ring does not own the indexes:
+ * free it before them. Searches of the ring use the indexes' own visited
+ * tables, so do not search a shard's index on its own while a ring search
+ * of it runs. */
+ann_status ann_shards_create(ann_index *const *shards, uint32_t n_shards, const uint32_t *const *global_ids,
+                             ann_shards **out);
+ann_status ann_shards_free(ann_shards *shards);
+/* Build every shard's links as Section 4 does: node u of shard i (its FP32
+ * vector; the index must keep FP32 originals unless its storage is FP32) is
+ * the query of a search of shard i + 1 with `params` (k is taken as 1; entry
+ * random or ghost staging; node u's RNG stream is qid_base + u), and I(u) is
+ * the top-1 result. Synchronous on `stream`. */
+ann_status ann_shards_link(ann_shards *shards, const ann_search_params *params, void *stream);
+/* Set shard `shard`'s links from host memory (n_shard local ids of the next
+ * shard, e.g. the exact Eq. 3 links); ANN_EINVAL for an id out of range. */
+ann_status ann_shards_set_links(ann_shards *shards, uint32_t shard, const uint32_t *links);
+/* Host copy of shard `shard`'s links (n_shard uint32). */
+ann_status ann_shards_get_links(const ann_shards *shards, uint32_t shard, uint32_t *links);
+/* The sharded search. queries device nq x dim; ids (dataset ids) and dists
+ * device nq x k; stats device N x nq ann_query_stats (row t: every query's
+ * stage-t search) or NULL. n_forward <= min(k, ANN_MAX_FORWARD); with
+ * n_forward > 0 every shard must be linked. Asynchronous on `stream` (the
+ * chunks run on the ring's own streams, joined back to `stream`). */
+ann_status ann_shards_search(ann_shards *shards, const float *queries, uint32_t nq, const ann_search_params *params,
+                             uint32_t n_forward, uint32_t *ids, float *dists, ann_query_stats *stats, void *stream);
 
 /* Ghost index of each node id (device ids, n) by binary search over the
  * ascending ghost ids, into out (device, n); ANN_INVALID_ID where an id is

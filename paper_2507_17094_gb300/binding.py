@@ -30,7 +30,8 @@ STATUS = {0: "ANN_OK", 1: "ANN_EINVAL", 2: "ANN_ENOMEM", 3: "ANN_ECUDA", 4: "ANN
 # Every symbol include/ann.h declares (checked by the tests).
 EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_index_free", "ann_index_info",
            "ann_index_export", "ann_search", "ann_search_host", "ann_search_host_noalloc", "ann_search_profile",
-           "ann_sync",
+           "ann_sync", "ann_shards_create", "ann_shards_free", "ann_shards_link", "ann_shards_set_links",
+           "ann_shards_get_links", "ann_shards_search",
            "ann_encode", "ann_dir_table", "ann_mlp_create", "ann_mlp_free", "ann_mlp_set_params", "ann_mlp_get",
            "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_train_epochs", "ann_mlp_predict", "ann_mlp_sync",
            "ann_mlp_save", "ann_mlp_load", "ann_mlp_set_input_norm", "ann_mlp_get_input_norm",
@@ -96,6 +97,12 @@ def lib() -> C.CDLL:
             L.ann_search_host_noalloc.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, vp, vp]
             L.ann_search_profile.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp, vp]
             L.ann_sync.argtypes = [vp, vp]
+            L.ann_shards_create.argtypes = [vp, u32, vp, C.POINTER(vp)]
+            L.ann_shards_free.argtypes = [vp]
+            L.ann_shards_link.argtypes = [vp, C.POINTER(SearchParams), vp]
+            L.ann_shards_set_links.argtypes = [vp, u32, vp]
+            L.ann_shards_get_links.argtypes = [vp, u32, vp]
+            L.ann_shards_search.argtypes = [vp, vp, u32, C.POINTER(SearchParams), u32, vp, vp, vp, vp]
             L.ann_selftest_timeout.argtypes = [vp]
             f32 = C.c_float
             L.ann_mlp_create.argtypes = [C.c_int, u32, u32, u32, u32, u32, C.POINTER(vp)]
@@ -404,6 +411,57 @@ class MLP:
 
     def sync(self, stream=None):
         _check(lib().ann_mlp_sync(self._h, _stream_ptr(stream)))
+
+
+class Shards:
+    """A path-extension ring over shard indexes (see include/ann.h)."""
+
+    def __init__(self, indexes, global_ids):
+        self.indexes = list(indexes)
+        self._gids = [np.ascontiguousarray(g, dtype=np.uint32) for g in global_ids]
+        arr = (C.c_void_p * len(self.indexes))(*[ix._h.value for ix in self.indexes])
+        garr = (C.c_void_p * len(self._gids))(*[g.ctypes.data for g in self._gids])
+        self._h = C.c_void_p()
+        _check(lib().ann_shards_create(arr, len(self.indexes), garr, C.byref(self._h)))
+        self.n_shards = len(self.indexes)
+
+    def link(self, stream=None, **params):
+        _check(lib().ann_shards_link(self._h, C.byref(make_params(**params)), _stream_ptr(stream)))
+
+    def set_links(self, shard: int, links: np.ndarray):
+        a = np.ascontiguousarray(links, dtype=np.uint32)
+        _check(lib().ann_shards_set_links(self._h, shard, _np_ptr(a)))
+
+    def get_links(self, shard: int) -> np.ndarray:
+        out = np.empty(self.indexes[shard].n, dtype=np.uint32)
+        _check(lib().ann_shards_get_links(self._h, shard, _np_ptr(out)))
+        return out
+
+    def search(self, queries, n_forward: int = 1, stats: bool = False, stream=None, **params):
+        """Device queries in; (dataset ids int32-view, dists, stats (N x nq) or None) as CUDA tensors."""
+        import torch
+        p = make_params(**params)
+        nq = queries.shape[0]
+        assert queries.is_cuda and queries.dtype == torch.float32 and queries.is_contiguous()
+        ids = torch.empty((nq, p.k), dtype=torch.int32, device=queries.device)
+        dists = torch.empty((nq, p.k), dtype=torch.float32, device=queries.device)
+        st = (torch.empty((self.n_shards, nq, len(STATS_FIELDS)), dtype=torch.int32, device=queries.device)
+              if stats else None)
+        _check(lib().ann_shards_search(self._h, queries.data_ptr(), nq, C.byref(p), n_forward, ids.data_ptr(),
+                                       dists.data_ptr(), None if st is None else st.data_ptr(),
+                                       _stream_ptr(stream)))
+        return ids, dists, st
+
+    def close(self):
+        if self._h:
+            lib().ann_shards_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stats_to_numpy(st) -> np.ndarray:

@@ -128,6 +128,12 @@ void serve_plan_free(void *plan);
 ann_status serve_launch(void *plan, const ServeRing &ring, uint32_t queries, cudaStream_t stream,
                         uint32_t stream_index);
 
+// The search launch (search.cu) with the index's own work counter and error
+// word (ann_search after its device switch).
+ann_status search_launch(ann_index *ix, const float *queries, uint32_t nq, const ann_search_params *p,
+                         const uint32_t *given, uint32_t n_given, uint32_t *ids, float *dists,
+                         ann_query_stats *stats, cudaStream_t stream);
+
 // The search launch (search.cu) with caller-chosen device scratch: the work
 // counter (zeroed on `stream` before the launch) and the error word. With
 // `prof` (one row of ANN_PROFILE_STAGES x ANN_PROFILE_PHASES counters per

@@ -57,7 +57,7 @@ def load_dataset(spec: WorkloadSpec, off_fraction: float = 0.0, device=None, use
     if verbose:
         print(f"[dataset] {spec.name}: vectors in {time.time() - t0:.1f}s", file=sys.stderr, flush=True)
     G = build_graph(X, spec.degree, spec.knn_k, spec.graph, device=device, seed=spec.seeds["base"],
-                    n_near=spec.n_near)
+                    n_near=spec.n_near, part_size=spec.part_size)
     if verbose:
         print(f"[dataset] {spec.name}: graph in {time.time() - t0:.1f}s", file=sys.stderr, flush=True)
     S = ghost_sample(spec.n, spec.ghost_n, spec.seeds["ghost"])

@@ -290,13 +290,14 @@ def add_bridges(graph: np.ndarray, br: np.ndarray) -> np.ndarray:
 
 
 def build_graph(X: np.ndarray, degree: int, knn_k: int, method: str = "exact",
-                n_parts: int = 0, device=None, seed: int = 0, n_bridge: int = -1, n_near: int = 2) -> np.ndarray:
+                n_parts: int = 0, device=None, seed: int = 0, n_bridge: int = -1, n_near: int = 2,
+                part_size: int = 1000) -> np.ndarray:
     """kNN lists of length ``knn_k`` (exact, or partitioned over each node's
-    partition and its ``n_near`` nearest ones) pruned to ``degree``, with
-    ``n_bridge`` bridge slots (default degree // 8; half to the nearest
-    partitions, half to random ones)."""
+    partition, of about ``part_size`` points, and its ``n_near`` nearest
+    ones) pruned to ``degree``, with ``n_bridge`` bridge slots (default
+    degree // 8; half to the nearest partitions, half to random ones)."""
     n = X.shape[0]
-    parts = n_parts or max(1, n // 1000)
+    parts = n_parts or max(1, n // part_size)
     if method == "exact" or n <= 20_000:
         knn = knn_exact(X, knn_k, device=device)
     else:

@@ -122,6 +122,7 @@ class WorkloadSpec:
     search: dict = field(default_factory=dict)
     spectrum_decay: Optional[float] = None
     n_near: int = 2                # partitions beside a node's own in its kNN pool
+    part_size: int = 1000          # points per k-means partition of the kNN pools
 
     @property
     def seeds(self) -> dict:
