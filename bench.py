@@ -369,6 +369,321 @@ def recall_at(ann_ids: np.ndarray, gt_dists: np.ndarray, X: np.ndarray, Q: np.nd
     return hits / (a.shape[0] * k)
 
 
+# ------------------------------------------------------------------ other workloads
+# Operating points of workloads 3 and 4 (measured on the GB300; the
+# diagnosis that chose them: recall on workload 3 was bounded by the ghost
+# stage reaching the query's cluster -- 85% with a 64-entry one-parent ghost
+# queue, 98-100% with 128-256 entries and 4 parents -- and on workload 4 by
+# the kNN graph, whose rows held 48% of each node's true 10 nearest
+# neighbours).
+W3_GHOST = dict(ghost_itopk=128, ghost_search_width=4, ghost_max_iters=32)
+W3_GHOST_K100 = dict(ghost_itopk=256, ghost_search_width=4, ghost_max_iters=48)
+W4_GHOST = dict(ghost_itopk=128, ghost_search_width=4, ghost_max_iters=48)
+
+
+class Timer:
+    """CUDA-event timing of a step on `stream`, L2 flushed before each step."""
+
+    def __init__(self, dev, stream):
+        import torch
+        self.dev, self.stream = dev, stream
+        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def __call__(self, run, steps=3, warm=1):
+        import torch
+        for _ in range(warm):
+            run()
+        torch.cuda.synchronize(self.dev)
+        ts = []
+        for _ in range(steps):
+            self.flush.add_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            run()
+            e1.record(self.stream)
+            ts.append((e0, e1))
+        torch.cuda.synchronize(self.dev)
+        return statistics.median(a.elapsed_time(b) for a, b in ts)
+
+
+def sweep_forms(A, ds, spec, forms, timer, gt, verbose, tag, entries=None):
+    """Each form: storage, fixed params, an itopk sweep and k. The smallest
+    itopk reaching recall@10 >= 0.95 on the ground-truth sample is the
+    form's operating point (else the best recall seen); there the line gets
+    QPS (all queries), the counted HBM bytes and their fraction, the mean
+    rows and, for low-precision storage, the distance error against FP64
+    before and after the FP32 rerank."""
+    import torch
+    dev, stream = timer.dev, timer.stream
+    Qd = torch.from_numpy(ds.Q).to(dev)
+    nq = Qd.shape[0]
+    gt_ids, gt_d = gt
+    ns = gt_ids.shape[0]
+    indexes, res = {}, {}
+    peak = measured_peaks()["hbm_gbs"]
+
+    def index_for(storage):
+        if storage not in indexes:
+            indexes[storage] = A.Index(ds.X, ds.G, storage=storage, ghost_ids=ds.S, ghost_graph=ds.Gg,
+                                       keep_fp32=True, build_dir=True, device=dev.index or 0)
+        return indexes[storage]
+
+    for name, f in forms.items():
+        ix = index_for(f["storage"])
+        le = (entries or {}).get(f["storage"]) if f["params"].get("entry") == 2 else None
+        if f["params"].get("entry") == 2 and le is None:
+            continue
+
+        def run(p, stats=False, ix=ix, le=le):
+            if le is not None:
+                seeds, _ = le.seeds(Qd, stream=stream)
+                return ix.search(Qd, given=seeds, stream=stream, stats=stats, **p)
+            return ix.search(Qd, stream=stream, stats=stats, **p)
+
+        sweep, chosen = [], None
+        for L in f["sweep"]:
+            p = dict(f["params"], k=f["k"], itopk=L, max_iters=L + 16, seed=spec.seeds["search"])
+            ids, _, _ = run(p)
+            torch.cuda.synchronize(dev)
+            a = ids[:ns].cpu().numpy().view(np.uint32)
+            rec = recall_at(a, gt_d, ds.X, ds.Q[:ns], 10)
+            row = {"itopk": L, "recall": rec}
+            if f["k"] >= 100 and gt_ids.shape[1] >= 100:
+                row["recall_at_100"] = recall_at(a, gt_d, ds.X, ds.Q[:ns], 100)
+            ms = timer(lambda: run(p))
+            row.update(ms=ms, qps=nq / (ms / 1e3))
+            sweep.append(row)
+            if chosen is None and rec >= RECALL_TARGET:
+                chosen = L
+                break
+        if chosen is None:
+            chosen = max(sweep, key=lambda r: r["recall"])["itopk"]
+        at = next(r for r in sweep if r["itopk"] == chosen)
+        p = dict(f["params"], k=f["k"], itopk=chosen, max_iters=chosen + 16, seed=spec.seeds["search"])
+        _, _, st = run(p, stats=True)
+        torch.cuda.synchronize(dev)
+        stn = A.stats_to_numpy(st)
+        b = float(algorithmic_bytes(stn, spec, f["storage"], bool(p.get("rerank"))).sum())
+        gbs = b / (at["ms"] / 1e3) / 1e9
+        r = {"storage": ("f32", "f16", "e4m3")[f["storage"]], "k": f["k"], "itopk": chosen,
+             "params": {k: v for k, v in p.items() if k not in ("itopk", "seed")},
+             "recall": at["recall"], "qps": at["qps"], "ms_per_step": at["ms"], "gbs": gbs, "hbm_frac": gbs / peak,
+             "mean_vec_rows": float(stn["vec_rows"].mean()), "mean_ghost_rows": float(stn["ghost_vec_rows"].mean()),
+             "mean_iters": float(stn["iters"].mean()), "sweep": sweep}
+        if "recall_at_100" in at:
+            r["recall_at_100"] = at["recall_at_100"]
+        if f["storage"] != 0:
+            errs = {}
+            for tagr, rr in (("stored", 0), ("reranked", 1)):
+                ids_e, d_e, _ = run(dict(p, rerank=rr))
+                torch.cuda.synchronize(dev)
+                ie = ids_e[:ns].cpu().numpy().view(np.uint32)
+                de = d_e[:ns].cpu().numpy().astype(np.float64)
+                ok = ie != 0xFFFFFFFF
+                ex = pair_dist(ds.X, ds.Q[:ns], np.where(ok, ie, 0).astype(np.uint32))
+                rel = np.abs(de - ex)[ok] / np.maximum(ex[ok], 1e-30)
+                errs[tagr] = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
+                              "exact_fraction": float((de[ok] == ex[ok]).mean())}
+            r["distance_error_vs_fp64"] = errs
+        if le is not None:
+            pred_ms = timer(lambda: le.seeds(Qd, stream=stream), steps=5, warm=2)
+            flop = 2.0 * nq * (spec.d * 512 + 512 * 512 + 512 * spec.ghost_n)
+            tf = flop / (pred_ms / 1e3) / 1e12
+            pk = measured_peaks()["bf16_tflops"]
+            r["predict"] = {"ms": pred_ms, "fallback_fraction": le.fallback_fraction(le.seeds(Qd)[0]),
+                            "roofline": {"bound": "tensor", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
+                                         "frac": tf / pk, "flop_per_step": flop}}
+        res[name] = r
+        if verbose:
+            print(f"[bench] {tag} {name}: " + ", ".join(f"L{s['itopk']} r={s['recall']:.3f} {s['qps'] / 1e6:.2f}M/s"
+                                                      for s in sweep), file=sys.stderr, flush=True)
+    for ix in indexes.values():
+        ix.close()
+    return res
+
+
+def leg_workload3(A, args, timer, verbose):
+    """Workload 3 (10M x 128 integers): FP32 against FP16 / E4M3 storage with
+    FP32 rerank, k = 10 and k = 100."""
+    from workloads import WORKLOADS, load_dataset
+    spec = WORKLOADS[3]
+    t0 = time.time()
+    ds = load_dataset(spec, device=timer.dev, verbose=verbose)
+    gt = truth_knn(ds.X, ds.Q[:args.gt_sample], 100, timer.dev, shortlist=128)
+    base = dict(entry=1, dgs_discard=0.5, dgs_cooldown=0.3, **W3_GHOST)
+    k100 = dict(entry=1, dgs_discard=0.5, dgs_cooldown=0.3, **W3_GHOST_K100)
+    sw = (32, 64, 128, 256)
+    forms = {
+        "paper_fp32": dict(storage=0, k=10, sweep=sw, params=dict(base, rerank=0)),
+        "f16_rerank": dict(storage=1, k=10, sweep=sw, params=dict(base, rerank=1)),
+        "e4m3_rerank": dict(storage=2, k=10, sweep=sw, params=dict(base, rerank=1)),
+        "f16_rerank_k100": dict(storage=1, k=100, sweep=(128, 256, 512), params=dict(k100, rerank=1)),
+        "e4m3_rerank_k100": dict(storage=2, k=100, sweep=(128, 256, 512), params=dict(k100, rerank=1)),
+    }
+    res = sweep_forms(A, ds, spec, forms, timer, gt, verbose, "w3")
+    return {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "nq": spec.nq,
+            "gt_sample": int(gt[0].shape[0]), "forms": res, "leg_s": time.time() - t0}
+
+
+def leg_workload4(A, args, timer, verbose):
+    """Workload 4 (5M x 256, Zipf cluster sizes, ghost set 50,000): plain
+    ghost staging against the learned entry (MLP 256 -> 512 -> 512 ->
+    50,000 trained on the GPU), FP32 and FP16 / E4M3 with rerank."""
+    from workloads import WORKLOADS, load_dataset
+    spec = WORKLOADS[4]
+    t0 = time.time()
+    ds = load_dataset(spec, off_fraction=0.2, device=timer.dev, verbose=verbose)
+    gt = truth_knn(ds.X, ds.Q[:args.gt_sample], 10, timer.dev)
+    sw = (64, 128, 256, 512)
+    ghost = dict(entry=1, dgs_discard=0.5, dgs_cooldown=0.3, **W4_GHOST)
+    learned = dict(entry=2, dgs_discard=0.5, dgs_cooldown=0.3, ghost_max_iters_given=4, **W4_GHOST)
+    entries, info = {}, {}
+    ix16 = A.Index(ds.X, ds.G, storage=1, ghost_ids=ds.S, ghost_graph=ds.Gg, keep_fp32=True, build_dir=False,
+                   device=timer.dev.index or 0)
+    le, info = train_entry(ds, spec, ix16, timer.dev, verbose, args.train_queries, args.epochs)
+    for st_ in (0, 1, 2):
+        entries[st_] = le    # the network predicts ghost indices: one model serves every storage
+    ix16.close()
+    forms = {
+        "paper_fp32": dict(storage=0, k=10, sweep=sw, params=dict(ghost, rerank=0)),
+        "f16_ghost": dict(storage=1, k=10, sweep=sw, params=dict(ghost, rerank=1)),
+        "f16_learned": dict(storage=1, k=10, sweep=sw, params=dict(learned, rerank=1)),
+        "e4m3_learned": dict(storage=2, k=10, sweep=sw, params=dict(learned, rerank=1)),
+    }
+    res = sweep_forms(A, ds, spec, forms, timer, gt, verbose, "w4", entries)
+    le.close()
+    return {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "nq": spec.nq,
+            "off_distribution_fraction": 0.2, "gt_sample": int(gt[0].shape[0]), "learned_entry": info,
+            "forms": res, "leg_s": time.time() - t0}
+
+
+def leg_workload5(A, args, timer, verbose):
+    """Workload 5 (20M x 96 FP16): the same request trace (batches of 1-4,096
+    queries, k in {10, 100}, itopk in {64, 256}) through the continuous-
+    batching server and as one ann_search per request with identical
+    parameters; capacity of each and the server's latency at half its
+    capacity."""
+    import torch
+    from workloads import WORKLOADS, load_dataset
+    spec = WORKLOADS[5]
+    t0 = time.time()
+    ds = load_dataset(spec, device=timer.dev, verbose=verbose)
+    ix = A.Index(ds.X, ds.G, storage=1, ghost_ids=ds.S, ghost_graph=ds.Gg, keep_fp32=True, build_dir=True,
+                 device=timer.dev.index or 0)
+    rng = np.random.default_rng(spec.seeds["search"] + 7)
+    base = dict(entry=1, dgs_discard=0.5, ghost_itopk=64, ghost_max_iters=32, ghost_search_width=4, rerank=1,
+                seed=spec.seeds["search"])
+    reqs = []
+    for rid in range(args.serve_requests):
+        n = int(rng.integers(1, 4097))
+        off = int(rng.integers(0, len(ds.Q) - n))
+        k = int(rng.choice([10, 100]))
+        L = max(k, int(rng.choice([64, 256])))
+        reqs.append((rid, ds.Q[off:off + n], dict(base, k=k, itopk=L, max_iters=L + 16, qid_base=rid << 20)))
+    nq = sum(len(q) for _, q, _ in reqs)
+    srv = A.Server(ix, capacity=65536, max_requests=128,
+                   max_params=dict(base, k=100, itopk=256, max_iters=272))
+    A.replay(srv, [(0.0, 10**9 + i, ds.Q[:64], dict(reqs[0][2], qid_base=0)) for i in range(4)])
+
+    def play(rate):
+        t, trace = 0.0, []
+        for rid, q, prm in reqs:
+            if rate:
+                t += float(rng.exponential(1.0 / rate))
+            trace.append((t, rid, q, prm))
+        res, wall = A.replay(srv, trace, timeout_s=300)
+        lat = np.array([res[r][2] for _, r, _, _ in trace]) * 1e3
+        return res, {"qps": nq / wall, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99))}
+
+    served, burst = play(0.0)
+    half_rate = 0.5 * burst["qps"] / (nq / len(reqs))
+    _, half = play(half_rate)
+    srv.close()
+    # the same requests, one ann_search each, back to back on one stream
+    # (queries already on the device; results stay there)
+    dq = [torch.from_numpy(np.ascontiguousarray(q)).to(timer.dev) for _, q, _ in reqs]
+
+    def per_request():
+        for (rid, q, prm), qt in zip(reqs, dq):
+            ix.search(qt, stream=timer.stream, **prm)
+
+    ms = timer(per_request, steps=3, warm=1)
+    same = 0
+    for (rid, q, prm), qt in zip(reqs[::10], dq[::10]):
+        ids, d, _ = ix.search(qt, **prm)
+        torch.cuda.synchronize(timer.dev)
+        same += int(np.array_equal(ids.cpu().numpy().view(np.uint32), served[rid][0]))
+    ix.close()
+    per_req_qps = nq / (ms / 1e3)
+    return {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "storage": "f16",
+            "requests": len(reqs), "queries": nq, "entry": "ghost",
+            "server_capacity_qps": burst["qps"], "server_all_at_once": burst,
+            "per_request_search_qps": per_req_qps, "capacity_ratio_server_vs_per_request": burst["qps"] / per_req_qps,
+            "half_load": dict(half, offered_qps=0.5 * burst["qps"]),
+            "sampled_requests_equal_to_batch_search": f"{same}/{len(reqs[::10])}",
+            "mix": "batch 1-4096 uniform, k {10,100}, itopk {64,256} raised to k, Poisson arrivals",
+            "leg_s": time.time() - t0}
+
+
+def leg_ppe(A, args, timer, verbose):
+    """Path extension on simulated shards (Section 3.1.2) on workload 2: the
+    dataset in 4 random shards, each with its graph and 1% ghost set, links
+    built by search (Section 4); recall@10 against the per-shard iteration cap
+    for the unsharded search, the baseline sharding (every shard from ghost
+    staging) and path extension (later shards from the linked node of the
+    previous result), as the paper's Fig. 12 reports it."""
+    import torch
+    from workloads import WORKLOADS, build_shards, load_dataset
+    spec = WORKLOADS[2]
+    t0 = time.time()
+    ds = load_dataset(spec, device=timer.dev, verbose=verbose)
+    gt = truth_knn(ds.X, ds.Q[:args.gt_sample], 10, timer.dev)
+    ns = gt[0].shape[0]
+    N = 4
+    sh = build_shards(ds.X, N, spec.degree, spec.knn_k, spec.graph, 0.01, spec.ghost_degree, seed=77,
+                      device=timer.dev)
+    dev_i = timer.dev.index or 0
+    sidx = [A.Index(t.X, t.G, storage=0, ghost_ids=t.S, ghost_graph=t.Gg, keep_fp32=True, build_dir=False,
+                    device=dev_i) for t in sh]
+    ring = A.Shards(sidx, [t.ids for t in sh])
+    link_p = dict(k=1, itopk=32, max_iters=48, entry=1, ghost_itopk=32, ghost_max_iters=12, ghost_search_width=4,
+                  seed=5)
+    t1 = time.time()
+    ring.link(**link_p)
+    link_s = time.time() - t1
+    full = A.Index(ds.X, ds.G, storage=0, ghost_ids=ds.S, ghost_graph=ds.Gg, keep_fp32=True, build_dir=False,
+                   device=dev_i)
+    Qd = torch.from_numpy(ds.Q).to(timer.dev)
+    nq = Qd.shape[0]
+    p0 = dict(k=10, itopk=32, entry=1, ghost_itopk=32, ghost_max_iters=12, ghost_search_width=4,
+              seed=spec.seeds["search"])
+    curves = {"unsharded": [], "sharded_baseline": [], "sharded_ppe": []}
+    for T in (2, 4, 6, 8, 12, 16, 24, 32, 48):
+        p = dict(p0, max_iters=T)
+        for mode in curves:
+            if mode == "unsharded":
+                run = lambda p=p: full.search(Qd, stream=timer.stream, **p)   # noqa: E731
+            else:
+                fwd = 1 if mode == "sharded_ppe" else 0
+                run = lambda p=p, fwd=fwd: ring.search(Qd, n_forward=fwd, stream=timer.stream, **p)   # noqa: E731
+            ids, _, _ = run()
+            torch.cuda.synchronize(timer.dev)
+            rec = recall_at(ids[:ns].cpu().numpy().view(np.uint32), gt[1], ds.X, ds.Q[:ns], 10)
+            ms = timer(run)
+            curves[mode].append({"max_iters": T, "recall": rec, "qps": nq / (ms / 1e3)})
+    reach = {m: next((c["max_iters"] for c in v if c["recall"] >= 0.90), None) for m, v in curves.items()}
+    ring.close()
+    for ix in sidx:
+        ix.close()
+    full.close()
+    if verbose:
+        print(f"[bench] ppe: iterations to recall 0.90 {reach}", file=sys.stderr, flush=True)
+    return {"workload": spec.name, "shards": N, "shard_n": [int(len(t.ids)) for t in sh], "forwarded": 1,
+            "link_params": link_p, "link_build_s": link_s, "search": {k: v for k, v in p0.items() if k != "seed"},
+            "iters_to_recall_0.90": reach, "curves": curves, "leg_s": time.time() - t0}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -637,6 +952,25 @@ def run_ours(args):
                                   f"parameters (itopk {L}), plain-C oracle on all host cores, {dt:.2f} s wall",
                         "ids_match_gpu": match}
 
+    # ------------------------------------------------------------ workloads 3-5 and path extension
+    legs = {}
+    if rank == 0 and world == 1 and args.workloads:
+        for le_ in entries.values():
+            le_.close()
+        entries.clear()
+        for ix_ in indexes.values():
+            ix_.close()
+        indexes.clear()
+        timer = Timer(dev, stream)
+        fns = {"3": leg_workload3, "4": leg_workload4, "5": leg_workload5, "ppe": leg_ppe}
+        for w in args.workloads.split(","):
+            if w in fns:
+                t0 = time.time()
+                legs[w] = fns[w](A, args, timer, verbose)
+                torch.cuda.empty_cache()
+                if verbose:
+                    print(f"[bench] leg {w} done in {time.time() - t0:.0f}s", file=sys.stderr, flush=True)
+
     peaks = measured_peaks()
     achieved = bytes_per_launch / mean_launch_s / 1e9
     tr = ncu_traffic(spec.name, headline)
@@ -668,6 +1002,7 @@ def run_ours(args):
         "cpu_baseline": cpu_baseline,
         "serving": serving,
         "phase_profile": phase_profile,
+        "workloads": {legs[w]["workload"] if w != "ppe" else "path_extension": legs[w] for w in legs},
     }
     for le in entries.values():
         le.close()
@@ -755,6 +1090,8 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--workloads", default="3,4,5,ppe",
+                    help="legs beside the headline (rank 0, one GPU): 3, 4, 5 and ppe; empty for none")
     ap.add_argument("-v", "--verbose", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

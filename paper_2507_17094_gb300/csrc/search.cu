@@ -113,6 +113,7 @@ struct Args {
     uint32_t *vtab;
     uint32_t vbits, vstride_bits, slot_base;
     uint32_t gbm_words;   // > 0: the ghost stage's visited set is a bitmap of this many words
+    uint32_t lpr;         // lanes per staged row in the distance step: 2, or 4 for wide rows
     // profile build only: per warp slot, ANN_PROFILE_STAGES x ANN_PROFILE_PHASES
     // cycle counters (slot_base + warp slot selects a row)
     unsigned long long *prof;
@@ -227,7 +228,22 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
     return __fadd_rn(s.x, s.y);
 }
 
-template <int ST, bool PROF = false>
+// One of the four partial sums of the squared L2 between a staged row and
+// the query: lane j of a row's four lanes runs sum j (elements i = j, j + 4,
+// ... in index order, one fused multiply-add each), so the four lanes
+// together do the work of one row with the same operations as the
+// definition. Used for wide rows, where a round stages at most 8 rows.
+template <int ST>
+__device__ __forceinline__ float row_dist_quarter(const uint8_t *row, const float *q, float scale, uint32_t d,
+                                                  uint32_t j)
+{
+    float s = 0.0f;
+#pragma unroll 4
+    for (uint32_t i = j; i < d; i += 4) step(q[i], stored_elem<ST>(row, i, scale), s);
+    return s;
+}
+
+template <int ST, bool PROF = false, int LPR = 2>
 struct WarpSearch {
     const Args &a;
     uint8_t *base;
@@ -359,7 +375,8 @@ struct WarpSearch {
 
     // ----------------------------------------------------- evaluate rows
     // Distances of rows ids[0, n) of `codes` into out[0, n), stage_rows
-    // (<= 16) rows per bulk-copy round; lanes 2r and 2r + 1 compute row r.
+    // (<= 32 / LPR) rows per bulk-copy round; lanes LPR r .. LPR r + LPR - 1
+    // compute row r (a lane pair, or four lanes for wide rows).
     template <int RST>
     __device__ bool evaluate(const uint8_t *codes, const float *scales, uint32_t row_bytes, const uint32_t *ids,
                              uint32_t n, float *out)
@@ -381,12 +398,18 @@ struct WarpSearch {
             }
             if (!wait_copies()) return false;
             mark(PH_GATHER);
-            const uint32_t r = lane >> 1;
+            const uint32_t r = lane / LPR;
             const float rs = __shfl_sync(0xffffffffu, scale, r);
             float part = 0.0f;
-            if (r < rows) part = row_dist_half<RST>(stage() + r * a.stage_stride, q(), rs, a.d, lane & 1);
-            const float other = __shfl_xor_sync(0xffffffffu, part, 1);
-            if (r < rows && (lane & 1) == 0) out[b0 + r] = __fadd_rn(part, other);
+            if (LPR == 2) {
+                if (r < rows) part = row_dist_half<RST>(stage() + r * a.stage_stride, q(), rs, a.d, lane & 1);
+            } else {
+                // sum j of the row, then (s0 + s1) and (s2 + s3) on lane pairs
+                if (r < rows) part = row_dist_quarter<RST>(stage() + r * a.stage_stride, q(), rs, a.d, lane & 3);
+                part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, 1));
+            }
+            const float other = __shfl_xor_sync(0xffffffffu, part, LPR / 2);
+            if (r < rows && (lane & (LPR - 1)) == 0) out[b0 + r] = __fadd_rn(part, other);
             __syncwarp();
             mark(PH_DIST);
         }
@@ -840,15 +863,14 @@ struct WarpSearch {
                 mark(PH_VISIT);
             }
             const bool seeded = !(stage == 1 && ghost);
-            // given seeds start the ghost stage (learned entry) or, without
-            // one, the base stage (an extended path's first node)
-            const bool use_given = given && (stage == 0 || !ghost);
-            ok = iterate<ST>(v, use_given ? given : nullptr,
-                             seeded ? (use_given ? qp.n_given : (stage ? qp.m : v.deg)) : 0,
+            ok = iterate<ST>(v, given, seeded ? (given ? qp.n_given : (stage ? qp.m : v.deg)) : 0,
                              splitmix64(qp.seed ^ (stage ? 0 : kGhostTag)), lcap, stage ? qp.W : qp.Wg,
                              stage ? qp.T : (given ? qp.Tg_given : qp.Tg), stage ? qp.n_keep : v.deg,
                              stage ? qp.min_match : 0,
                              stage ? qp.it_cool : 0, stage ? qp.reexpand : 0, iters, parents, dgs_parents, rows);
+            // given seeds start the first stage only: the ghost stage (learned
+            // entry) or, without one, the base stage (an extended path's start)
+            given = nullptr;
             if (stage) {
                 st.iters = iters;
                 st.parents = parents;
@@ -908,12 +930,12 @@ struct WarpSearch {
     }
 };
 
-template <int ST, bool PROF = false>
+template <int ST, bool PROF = false, int LPR = 2>
 __global__ void __launch_bounds__(128, 6) search_kernel(const Args a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSearch<ST, PROF> ws(a, smem + (size_t)warp * a.lay.total, a.slot_base + blockIdx.x * (blockDim.x >> 5) + warp);
+    WarpSearch<ST, PROF, LPR> ws(a, smem + (size_t)warp * a.lay.total, a.slot_base + blockIdx.x * (blockDim.x >> 5) + warp);
     if (lane == 0) mbar_init(ws.bar(), 1);
     fence_mbar_init();
     __syncwarp();
@@ -938,13 +960,13 @@ __global__ void __launch_bounds__(128, 6) search_kernel(const Args a)
 // The request's parameters are copied into the warp's shared memory; the
 // warp that finishes a request's last query raises its completion flag in
 // host-mapped memory after a system-scope fence.
-template <int ST>
+template <int ST, int LPR = 2>
 __global__ void __launch_bounds__(128, 6) serve_kernel(const Args a, const ServeRing r)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *base = smem + (size_t)warp * a.lay.total;
-    WarpSearch<ST> ws(a, base, a.slot_base + blockIdx.x * (blockDim.x >> 5) + warp);
+    WarpSearch<ST, false, LPR> ws(a, base, a.slot_base + blockIdx.x * (blockDim.x >> 5) + warp);
     QParams *qp = reinterpret_cast<QParams *>(base + a.lay.qp);
     if (lane == 0) mbar_init(ws.bar(), 1);
     fence_mbar_init();
@@ -1020,23 +1042,36 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
     return L;
 }
 
-template <int ST, bool PROF = false>
-cudaError_t launch(const Args &a, int warps, int blocks, size_t smem, cudaStream_t st)
+template <int ST, bool PROF, int LPR>
+cudaError_t launch_lpr(const Args &a, int warps, int blocks, size_t smem, cudaStream_t st)
 {
     cudaError_t e =
-        cudaFuncSetAttribute(search_kernel<ST, PROF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(search_kernel<ST, PROF, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    search_kernel<ST, PROF><<<blocks, warps * 32, smem, st>>>(a);
+    search_kernel<ST, PROF, LPR><<<blocks, warps * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int ST>
-int blocks_per_sm(int warps, size_t smem)
+template <int ST, bool PROF = false>
+cudaError_t launch(const Args &a, int warps, int blocks, size_t smem, cudaStream_t st)
+{
+    return a.lpr == 4 ? launch_lpr<ST, PROF, 4>(a, warps, blocks, smem, st)
+                      : launch_lpr<ST, PROF, 2>(a, warps, blocks, smem, st);
+}
+
+template <int ST, int LPR>
+int blocks_per_sm_lpr(int warps, size_t smem)
 {
     int nb = 0;
-    cudaFuncSetAttribute(search_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<ST>, warps * 32, smem);
+    cudaFuncSetAttribute(search_kernel<ST, false, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, search_kernel<ST, false, LPR>, warps * 32, smem);
     return nb;
+}
+
+template <int ST>
+int blocks_per_sm(int warps, size_t smem, uint32_t lpr)
+{
+    return lpr == 4 ? blocks_per_sm_lpr<ST, 4>(warps, smem) : blocks_per_sm_lpr<ST, 2>(warps, smem);
 }
 
 int env_int(const char *name, int dflt)
@@ -1154,7 +1189,11 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     a.prow_bytes = ix->row_bytes;
     const uint32_t stage_bytes = std::max(ix->row_bytes, q.rerank ? a.row32_bytes : 0u);
     a.stage_stride = smem_row_stride(stage_bytes);
-    a.stage_rows = (uint32_t)std::min(16, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
+    // rows of more than 1 KB (wide FP32 vectors, 512 and up to ANN_MAX_DIM
+    // dimensions) are computed by four lanes each, at most 8 per round;
+    // narrower ones by lane pairs, 16 per round
+    a.lpr = stage_bytes > 1024 ? 4 : 2;
+    a.stage_rows = (uint32_t)std::min<int>(32 / (int)a.lpr, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
     // visited tables: the queue plus one iteration's candidates must fit in
     // half a table (the reset threshold)
     if (cap_buf + cap_cand > (1u << (kVisitedBits - 1))) {
@@ -1172,6 +1211,8 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
         lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W, adj_words, dir_words, a.prow_bytes,
                           a.stage_rows, a.stage_stride, a.gbm_words, serve);
         if ((size_t)lay.total * warps <= ix->smem_optin) break;
+        // wide rows: fewer staged rows per round before fewer warps per block
+        if (a.stage_rows > 4) { a.stage_rows /= 2; continue; }
         if (warps > 1) { warps /= 2; continue; }
         set_error("ann_search: per-query state (%u bytes) exceeds shared memory", lay.total);
         return ANN_EINVAL;
@@ -1179,9 +1220,9 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     a.lay = lay;
     smem = (size_t)lay.total * warps;
     switch (ix->storage) {
-    case ANN_F32: nb = blocks_per_sm<ANN_F32>(warps, smem); break;
-    case ANN_F16: nb = blocks_per_sm<ANN_F16>(warps, smem); break;
-    default: nb = blocks_per_sm<ANN_E4M3>(warps, smem); break;
+    case ANN_F32: nb = blocks_per_sm<ANN_F32>(warps, smem, a.lpr); break;
+    case ANN_F16: nb = blocks_per_sm<ANN_F16>(warps, smem, a.lpr); break;
+    default: nb = blocks_per_sm<ANN_E4M3>(warps, smem, a.lpr); break;
     }
     if (nb <= 0) {
         set_error("ann_search: kernel does not fit on an SM (%zu bytes shared)", smem);
@@ -1198,13 +1239,20 @@ struct ServePlanImpl {
     uint32_t slots_per_launch;
 };
 
+template <int ST, int LPR>
+cudaError_t launch_serve_lpr(const ServePlanImpl &pl, const ServeRing &r, int blocks, cudaStream_t st)
+{
+    cudaError_t e =
+        cudaFuncSetAttribute(serve_kernel<ST, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    if (e != cudaSuccess) return e;
+    serve_kernel<ST, LPR><<<blocks, pl.warps * 32, pl.smem, st>>>(pl.a, r);
+    return cudaGetLastError();
+}
+
 template <int ST>
 cudaError_t launch_serve(const ServePlanImpl &pl, const ServeRing &r, int blocks, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(serve_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-    if (e != cudaSuccess) return e;
-    serve_kernel<ST><<<blocks, pl.warps * 32, pl.smem, st>>>(pl.a, r);
-    return cudaGetLastError();
+    return pl.a.lpr == 4 ? launch_serve_lpr<ST, 4>(pl, r, blocks, st) : launch_serve_lpr<ST, 2>(pl, r, blocks, st);
 }
 
 }  // namespace planning

@@ -130,3 +130,19 @@ def test_workload5_recipe_serving_mix():
         if j % 4 == 0:
             o_ids, o_d, _ = O.search(oi, q, **prm)
             assert np.array_equal(b_ids, o_ids) and np.array_equal(b_d.view(np.uint32), o_d.view(np.uint32))
+
+
+@pytest.mark.parametrize("d", [768, 960])
+@pytest.mark.parametrize("storage,params", [
+    (O.F32, dict(k=10, itopk=32, max_iters=48, entry=1, dgs_discard=0.5, ghost_max_iters=12, ghost_search_width=4)),
+    (O.F32, dict(k=10, itopk=32, max_iters=48, entry=1, ghost_max_iters=12, ghost_search_width=4)),
+    (O.F16, dict(k=10, itopk=64, max_iters=48, entry=1, dgs_discard=0.5, ghost_max_iters=12, rerank=1)),
+    (O.E4M3, dict(k=16, itopk=16, max_iters=24, entry=0, dgs_discard=0.75, rerank=1)),
+])
+def test_wide_recipe(d, storage, params):
+    """The wide workloads' recipe (768-d and 960-d: rows of 1.5-3.75 KB,
+    distances by four lanes per row, fewer rows per round; a direction table
+    of 24-30 words per edge) at 30,000 points."""
+    c = workload_case(6 if d == 768 else 7, 30_000, 300, 30, 300)
+    g, o = c.run(storage, seed=4006, **params)
+    assert_parity(g, o)

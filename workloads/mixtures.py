@@ -173,6 +173,16 @@ WORKLOADS = {
     5: WorkloadSpec(5, "serving-20M-96d", 20_000_000, 96, 20_000, 10_000, 32, 64,
                     "partitioned", 200_000, 16, center_range=(0.0, 10.0), sigma_range=(0.5, 4.0), normalize=True,
                     search=dict(k=10, itopk=64, search_width=1, max_iters=160)),
+    # Wide vectors, the shapes of the paper's Wiki (768-d) and Gist (960-d)
+    # sets, where it reports its largest DGS gain: workload 2's recipe
+    # (normalised anisotropic clusters, degree 64, 1% ghosts) at 768 and 960
+    # dimensions, 1M points each.
+    6: WorkloadSpec(6, "wide-1M-768d", 1_000_000, 768, 1000, 10_000, 64, 96, "partitioned",
+                    10_000, 16, center_range=(0.0, 10.0), sigma_range=(0.5, 4.0), normalize=True,
+                    search=dict(k=10, itopk=64, search_width=1, max_iters=80)),
+    7: WorkloadSpec(7, "wide-1M-960d", 1_000_000, 960, 1000, 10_000, 64, 96, "partitioned",
+                    10_000, 16, center_range=(0.0, 10.0), sigma_range=(0.5, 4.0), normalize=True,
+                    search=dict(k=10, itopk=64, search_width=1, max_iters=80)),
 }
 
 
