@@ -626,6 +626,35 @@ def leg_workload5(A, args, timer, verbose):
             "leg_s": time.time() - t0}
 
 
+def leg_wide(A, args, timer, verbose):
+    """Workloads 6 and 7 (1M x 768 and 1M x 960, the shapes of the paper's
+    Wiki and Gist sets): ghost staging with and without DGS, FP32 and FP16
+    with rerank, each at its smallest itopk reaching recall@10 0.95."""
+    from workloads import WORKLOADS, load_dataset
+    out = {}
+    for w in (6, 7):
+        spec = WORKLOADS[w]
+        t0 = time.time()
+        ds = load_dataset(spec, device=timer.dev, verbose=verbose)
+        gt = truth_knn(ds.X, ds.Q[:args.gt_sample], 10, timer.dev)
+        gs = dict(entry=1, dgs_cooldown=0.3, ghost_max_iters=GHOST_ITERS, ghost_search_width=GHOST_WIDTH)
+        sw = (16, 32, 64, 128, 256)
+        forms = {
+            "paper_fp32": dict(storage=0, k=10, sweep=sw, params=dict(gs, dgs_discard=0.5, rerank=0)),
+            "no_dgs_fp32": dict(storage=0, k=10, sweep=sw, params=dict(gs, dgs_discard=0.0, rerank=0)),
+            "f16_rerank": dict(storage=1, k=10, sweep=sw, params=dict(gs, dgs_discard=0.5, rerank=1)),
+            "no_dgs_f16_rerank": dict(storage=1, k=10, sweep=sw, params=dict(gs, dgs_discard=0.0, rerank=1)),
+        }
+        res = sweep_forms(A, ds, spec, forms, timer, gt, verbose, f"w{w}")
+        out[spec.name] = {"n": spec.n, "dim": spec.d, "degree": spec.degree, "nq": spec.nq,
+                          "gt_sample": int(gt[0].shape[0]), "forms": res,
+                          "dgs_speedup_fp32": res["paper_fp32"]["qps"] / res["no_dgs_fp32"]["qps"],
+                          "dgs_speedup_f16": res["f16_rerank"]["qps"] / res["no_dgs_f16_rerank"]["qps"],
+                          "leg_s": time.time() - t0}
+        del ds
+    return {"workload": "wide", "sets": out}
+
+
 def leg_ppe(A, args, timer, verbose):
     """Path extension on simulated shards (Section 3.1.2) on workload 2: the
     dataset in 4 random shards, each with its graph and 1% ghost set, links
@@ -962,7 +991,7 @@ def run_ours(args):
             ix_.close()
         indexes.clear()
         timer = Timer(dev, stream)
-        fns = {"3": leg_workload3, "4": leg_workload4, "5": leg_workload5, "ppe": leg_ppe}
+        fns = {"3": leg_workload3, "4": leg_workload4, "5": leg_workload5, "wide": leg_wide, "ppe": leg_ppe}
         for w in args.workloads.split(","):
             if w in fns:
                 t0 = time.time()
@@ -1002,7 +1031,8 @@ def run_ours(args):
         "cpu_baseline": cpu_baseline,
         "serving": serving,
         "phase_profile": phase_profile,
-        "workloads": {legs[w]["workload"] if w != "ppe" else "path_extension": legs[w] for w in legs},
+        "workloads": {legs[w]["workload"] if w not in ("ppe", "wide") else
+                      {"ppe": "path_extension", "wide": "wide_vectors"}[w]: legs[w] for w in legs},
     }
     for le in entries.values():
         le.close()
@@ -1090,8 +1120,8 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--epochs", type=int, default=8)
-    ap.add_argument("--workloads", default="3,4,5,ppe",
-                    help="legs beside the headline (rank 0, one GPU): 3, 4, 5 and ppe; empty for none")
+    ap.add_argument("--workloads", default="3,4,5,wide,ppe",
+                    help="legs beside the headline (rank 0, one GPU): 3, 4, 5, wide and ppe; empty for none")
     ap.add_argument("-v", "--verbose", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -42,6 +43,15 @@ constexpr int GEMM_STAGE_BYTES = STAGES * (TILE_A + TILE_B);
 constexpr int XS_STRIDE = 33;
 constexpr int GEMM_XS_BYTES = 8 * 32 * XS_STRIDE * 4;
 constexpr int GEMM_SMEM = GEMM_STAGE_BYTES + 256 + GEMM_XS_BYTES + 1024;
+// Resident-A variant (fused top-P logits, K <= RES_K): a CTA keeps its row
+// block's whole A (128 x K, as RES_K / BK swizzled 128 x BK tiles) in shared
+// memory while B streams through a ring of RES_STAGES tiles, so the L2 ->
+// shared-memory stream per tile halves (A is read once per row block).
+constexpr int RES_K = 512;
+constexpr int RES_STAGES = 4;
+constexpr int RES_A_BYTES = (RES_K / BK) * TILE_A;
+constexpr int RES_SMEM = RES_A_BYTES + RES_STAGES * TILE_B + 256 + GEMM_XS_BYTES + 1024;
+static_assert(RES_SMEM <= 232448, "resident-A GEMM exceeds the shared memory of a CTA");
 constexpr int TOPP = 8;   // top-P of the fused inference epilogue
 
 enum { EPI_F32 = 0, EPI_BIAS_F32 = 1, EPI_BIAS_RELU_BF16 = 2, EPI_TOPP = 3 };
@@ -310,7 +320,7 @@ __device__ __forceinline__ void topp_flush(const EpiArgs &e, const TopP &tp, uin
     o[2 * TOPP + 1] = tp.sm;
 }
 
-template <int EPI>
+template <int EPI, bool RESA = false>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, uint32_t M,
                 uint32_t N, uint32_t K, EpiArgs e)
@@ -318,14 +328,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;
     uint8_t *smem = smem_raw + pad;
+    // ring layout: STAGES x (A tile, B tile); resident-A layout: the row
+    // block's A tiles, then RES_STAGES B tiles
+    constexpr int NST = RESA ? RES_STAGES : STAGES;
+    constexpr int BAR_OFF = RESA ? RES_A_BYTES + RES_STAGES * TILE_B : GEMM_STAGE_BYTES;
     uint8_t *sA = smem;
-    uint8_t *sB = smem + STAGES * TILE_A;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + GEMM_STAGE_BYTES);
-    uint64_t *empty = full + STAGES;
-    uint64_t *acc_full = empty + STAGES;     // [2]: MMA -> epilogue
+    uint8_t *sB = smem + (RESA ? RES_A_BYTES : STAGES * TILE_A);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + BAR_OFF);
+    uint64_t *empty = full + NST;
+    uint64_t *acc_full = empty + NST;        // [2]: MMA -> epilogue
     uint64_t *acc_empty = acc_full + 2;      // [2]: epilogue -> MMA
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
-    float *xs_all = reinterpret_cast<float *>(smem + GEMM_STAGE_BYTES + 256);
+    uint64_t *a_full = acc_empty + 2;        // resident A loaded
+    uint64_t *a_empty = a_full + 1;          // resident A no longer read
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_empty + 1);
+    float *xs_all = reinterpret_cast<float *>(smem + BAR_OFF + 256);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t nkb = (K + BK - 1) / BK;
     const uint32_t n_tiles = (N + BN - 1) / BN, m_tiles = (M + BM - 1) / BM;
@@ -334,7 +350,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const uint32_t t_begin = min(tiles, blockIdx.x * per), t_end = min(tiles, t_begin + per);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -342,6 +358,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], EPI_WARPS);
         }
+        mbar_init(a_full, 1);
+        mbar_init(a_empty, 1);
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -355,7 +373,31 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0) {
+    if (warp == 0 && RESA) {
+        if (lane == 0) {
+            // A once per row block (after the MMAs on the previous one are
+            // done), then the B tiles of each of the block's column tiles
+            uint32_t it = 0, loads = 0, cur_m = 0xFFFFFFFFu;
+            bool ok = true;
+            for (uint32_t t = t_begin; t < t_end && ok; ++t) {
+                const uint32_t mb = t / n_tiles, n0 = (t % n_tiles) * BN;
+                if (mb != cur_m) {
+                    if (loads > 0 && !(ok = mbar_wait_bounded(a_empty, (loads - 1) & 1, e.err))) break;
+                    mbar_arrive_expect_tx(a_full, nkb * TILE_A);
+                    for (uint32_t kb = 0; kb < nkb; ++kb)
+                        tma_load_2d(sA + kb * TILE_A, &tA, (int)(kb * BK), (int)(mb * BM), a_full);
+                    cur_m = mb;
+                    ++loads;
+                }
+                for (uint32_t kb = 0; kb < nkb; ++kb, ++it) {
+                    const uint32_t s = it % NST, ph = (it / NST) & 1;
+                    if (!(ok = mbar_wait_bounded(&empty[s], ph ^ 1, e.err))) break;
+                    mbar_arrive_expect_tx(&full[s], TILE_B);
+                    tma_load_2d(sB + s * TILE_B, &tB, (int)(kb * BK), (int)n0, &full[s]);
+                }
+            }
+        }
+    } else if (warp == 0) {
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
@@ -368,6 +410,38 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     tma_load_2d(sA + s * TILE_A, &tA, (int)(kb * BK), (int)m0, &full[s]);
                     tma_load_2d(sB + s * TILE_B, &tB, (int)(kb * BK), (int)n0, &full[s]);
                 }
+            }
+        }
+    } else if (warp == 1 && RESA) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            uint32_t it = 0, tc = 0, loads = 0, cur_m = 0xFFFFFFFFu;
+            bool ok = true;
+            for (uint32_t t = t_begin; t < t_end && ok; ++t, ++tc) {
+                const uint32_t mb = t / n_tiles;
+                if (mb != cur_m) {
+                    if (!(ok = mbar_wait_bounded(a_full, loads & 1, e.err))) break;
+                    cur_m = mb;
+                    ++loads;
+                }
+                const uint32_t buf = tc & 1, use = tc >> 1;
+                if (!(ok = mbar_wait_bounded(&acc_empty[buf], (use & 1) ^ 1, e.err))) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + buf * BN;
+                for (uint32_t kb = 0; kb < nkb; ++kb, ++it) {
+                    const uint32_t s = it % NST, ph = (it / NST) & 1;
+                    if (!(ok = mbar_wait_bounded(&full[s], ph, e.err))) break;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_addr(sA + kb * TILE_A), b0 = smem_addr(sB + s * TILE_B);
+#pragma unroll
+                    for (uint32_t k = 0; k < BK / 16; ++k)
+                        mma_bf16(acc, desc_sw128(a0 + k * 32), desc_sw128(b0 + k * 32), idesc, (kb | k) != 0);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&acc_full[buf]);
+                // the last tile of this row block: A may be replaced once
+                // these MMAs are done
+                if (t + 1 < t_end && (t + 1) / n_tiles != mb) mma_commit(a_empty);
             }
         }
     } else if (warp == 1) {
@@ -744,6 +818,12 @@ __global__ void select_rank_kernel(const float *__restrict__ v, uint32_t n, uint
     if (threadIdx.x == 0) *out = __uint_as_float((key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key);
 }
 
+bool env_flag(const char *name, bool dflt)
+{
+    const char *v = getenv(name);
+    return v ? atoi(v) != 0 : dflt;
+}
+
 uint64_t mix64(uint64_t x)
 {
     uint64_t z = x + 0x9E3779B97F4A7C15ull;
@@ -844,15 +924,25 @@ ann_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, uint32_t M, uint
     ann_status s = make_map(&ta, A, M, K);
     if (s == ANN_OK) s = make_map(&tb, B, N, K);
     if (s != ANN_OK) return s;
-    static bool attr = false;
-    if (!attr) {
+    // the fused top-P logits keep A resident when it fits (ANN_GEMM_RESIDENT_A=0 turns that off)
+    static const bool res_on = env_flag("ANN_GEMM_RESIDENT_A", true);
+    const bool resa = EPI == EPI_TOPP && K <= (uint32_t)RES_K && res_on;
+    static bool attr = false, attr_res = false;
+    if (resa && !attr_res) {
+        ANN_CUDA(cudaFuncSetAttribute(gemm_kernel<EPI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RES_SMEM));
+        attr_res = true;
+    }
+    if (!resa && !attr) {
         ANN_CUDA(cudaFuncSetAttribute(gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
         attr = true;
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    gemm_kernel<EPI><<<gemm_grid(M, N, (uint32_t)sms), GEMM_THREADS, GEMM_SMEM, st>>>(ta, tb, M, N, K, e);
+    if (resa)
+        gemm_kernel<EPI, true><<<gemm_grid(M, N, (uint32_t)sms), GEMM_THREADS, RES_SMEM, st>>>(ta, tb, M, N, K, e);
+    else
+        gemm_kernel<EPI><<<gemm_grid(M, N, (uint32_t)sms), GEMM_THREADS, GEMM_SMEM, st>>>(ta, tb, M, N, K, e);
     ANN_CUDA(cudaGetLastError());
     return ANN_OK;
 }

@@ -298,3 +298,24 @@ def test_checkpoint_resumes_training(tmp_path):
     g.close()
     h.close()
     k.close()
+
+
+@pytest.mark.parametrize("h2,out,n", [(512, 20_000, 1000), (200, 9_000, 777)])
+def test_fused_top_p_many_tiles_per_cta(h2, out, n):
+    """Shapes where each persistent CTA computes dozens of tiles across
+    several row blocks (the resident-A logits kernel reloads A at each row
+    block switch), K = 512 and a ragged K = 200, a ragged last row block: the
+    fused top-8 equals the top-8 of the logits the unfused kernel writes."""
+    m = make_model(64, 128, h2, out, seed=17)
+    X = np.random.default_rng(18).standard_normal((n, 64)).astype(np.float32)
+    g = gpu_mlp(m, 1024)
+    Xt = torch.from_numpy(X).cuda()
+    z = g.forward(Xt).cpu().numpy().astype(np.float64)
+    seeds, pmax = g.predict(Xt, P=8, tau=0.0)
+    torch.cuda.synchronize()
+    g.sync()
+    own = np.lexsort((np.broadcast_to(np.arange(out), z.shape), -z), axis=1)[:, :8]
+    assert np.array_equal(seeds.cpu().numpy().view(np.uint32), own)
+    e = np.exp(z - z.max(axis=1, keepdims=True))
+    np.testing.assert_allclose(pmax.cpu().numpy(), 1.0 / e.sum(axis=1), rtol=1e-4)
+    g.close()
