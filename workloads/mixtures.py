@@ -167,9 +167,9 @@ WORKLOADS = {
                     "partitioned", 100_000, 16, center_range=(0.0, 255.0), sigma=16.0,
                     integer_range=(0, 255),
                     search=dict(k=10, itopk=128, search_width=1, max_iters=160)),
-    4: WorkloadSpec(4, "learned-5M-256d-zipf", 5_000_000, 256, 5000, 10_000, 32, 64,
-                    "partitioned", 50_000, 16, sigma=8.0, zipf_s=1.1,
-                    search=dict(k=10, itopk=64, search_width=1, max_iters=160)),
+    4: WorkloadSpec(4, "learned-5M-256d-zipf", 5_000_000, 256, 5000, 10_000, 64, 128,
+                    "partitioned", 50_000, 16, sigma=8.0, zipf_s=1.1, spectrum_decay=0.5, part_size=5000,
+                    n_near=8, search=dict(k=10, itopk=64, search_width=1, max_iters=160)),
     5: WorkloadSpec(5, "serving-20M-96d", 20_000_000, 96, 20_000, 10_000, 32, 64,
                     "partitioned", 200_000, 16, center_range=(0.0, 10.0), sigma_range=(0.5, 4.0), normalize=True,
                     search=dict(k=10, itopk=64, search_width=1, max_iters=160)),
