@@ -244,6 +244,32 @@ ann_status ann_shards_get_links(const ann_shards *shards, uint32_t shard, uint32
 ann_status ann_shards_search(ann_shards *shards, const float *queries, uint32_t nq, const ann_search_params *params,
                              uint32_t n_forward, uint32_t *ids, float *dists, ann_query_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Graph construction (the paper takes the proximity graph as given, Section
+ * 2.1, and times its build beside the method's preprocessing, Section 5.7).
+ * ------------------------------------------------------------------------ */
+/* Exact kNN lists: ids (device, n x K) gets, for every node u of X (device,
+ * n x dim FP32 row-major), the K other nodes nearest to u by squared L2 in
+ * FP32 (one fused multiply-add per element, index order), ordered by
+ * (distance, id). Brute force: O(n^2 dim) work, for building graphs of up to
+ * a few million nodes. 2 <= n < 2^32 - 1, 1 <= K < n, K <= 2 ANN_MAX_DEGREE,
+ * and (96 rows x (dim + 1) + 32 K x 2) x 4 bytes of shared memory must fit a
+ * block (ANN_EINVAL otherwise). Asynchronous on `stream`. */
+ann_status ann_knn_exact(const float *X, uint64_t n, uint32_t dim, uint32_t K, uint32_t *ids, void *stream);
+/* Prune kNN lists (device, n x K; each row distinct ids, ANN_INVALID_ID
+ * allowed) to a fixed-degree graph (device, n x degree): edge u -> v at rank
+ * r is detoured via the node at rank a < r of u's list when v sits in that
+ * node's list at a rank c < r; u's list is ordered by (number of detours,
+ * rank) and its first degree / 2 entries are kept; every kept edge w -> v,
+ * at position p of w's kept part, offers w to v, and v takes its offers in
+ * (p, w) order, at most degree - degree / 2; v's row is its kept part, then
+ * those reverse edges, then the rest of its ordered list, with repeats and v
+ * itself dropped, cut to `degree` and padded with ANN_INVALID_ID. degree <=
+ * min(K, ANN_MAX_DEGREE), K <= 2 ANN_MAX_DEGREE. Allocates temporaries of
+ * about n (K + 4 degree) x 4 bytes; synchronous on `stream`. */
+ann_status ann_graph_prune(const uint32_t *knn, uint64_t n, uint32_t K, uint32_t degree, uint32_t *graph,
+                           void *stream);
+
 /* Ghost index of each node id (device ids, n) by binary search over the
  * ascending ghost ids, into out (device, n); ANN_INVALID_ID where an id is
  * not a ghost node. Turns ghost-staging results into training labels. */

@@ -31,7 +31,7 @@ STATUS = {0: "ANN_OK", 1: "ANN_EINVAL", 2: "ANN_ENOMEM", 3: "ANN_ECUDA", 4: "ANN
 EXPORTS = ("ann_default_params", "ann_index_create", "ann_index_load", "ann_index_free", "ann_index_info",
            "ann_index_export", "ann_search", "ann_search_host", "ann_search_host_noalloc", "ann_search_profile",
            "ann_sync", "ann_shards_create", "ann_shards_free", "ann_shards_link", "ann_shards_set_links",
-           "ann_shards_get_links", "ann_shards_search",
+           "ann_shards_get_links", "ann_shards_search", "ann_knn_exact", "ann_graph_prune",
            "ann_encode", "ann_dir_table", "ann_mlp_create", "ann_mlp_free", "ann_mlp_set_params", "ann_mlp_get",
            "ann_mlp_forward", "ann_mlp_train_step", "ann_mlp_train_epochs", "ann_mlp_predict", "ann_mlp_sync",
            "ann_mlp_save", "ann_mlp_load", "ann_mlp_set_input_norm", "ann_mlp_get_input_norm",
@@ -97,6 +97,8 @@ def lib() -> C.CDLL:
             L.ann_search_host_noalloc.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, vp, vp]
             L.ann_search_profile.argtypes = [vp, vp, u32, C.POINTER(SearchParams), vp, u32, vp, vp, vp, vp]
             L.ann_sync.argtypes = [vp, vp]
+            L.ann_knn_exact.argtypes = [vp, u64, u32, u32, vp, vp]
+            L.ann_graph_prune.argtypes = [vp, u64, u32, u32, vp, vp]
             L.ann_shards_create.argtypes = [vp, u32, vp, C.POINTER(vp)]
             L.ann_shards_free.argtypes = [vp]
             L.ann_shards_link.argtypes = [vp, C.POINTER(SearchParams), vp]
@@ -462,6 +464,27 @@ class Shards:
             self.close()
         except Exception:
             pass
+
+
+def knn_exact(x, K: int, stream=None):
+    """Exact kNN lists of the device rows x (n x dim FP32): int32-view CUDA
+    tensor n x K (ann_knn_exact)."""
+    import torch
+    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+    ids = torch.empty((x.shape[0], K), dtype=torch.int32, device=x.device)
+    _check(lib().ann_knn_exact(x.data_ptr(), x.shape[0], x.shape[1], K, ids.data_ptr(), _stream_ptr(stream)))
+    return ids
+
+
+def graph_prune(knn, degree: int, stream=None):
+    """The pruned graph of device kNN lists (int32-view n x K): CUDA tensor
+    n x degree (ann_graph_prune)."""
+    import torch
+    assert knn.is_cuda and knn.dtype == torch.int32 and knn.is_contiguous()
+    g = torch.empty((knn.shape[0], degree), dtype=torch.int32, device=knn.device)
+    _check(lib().ann_graph_prune(knn.data_ptr(), knn.shape[0], knn.shape[1], degree, g.data_ptr(),
+                                 _stream_ptr(stream)))
+    return g
 
 
 def stats_to_numpy(st) -> np.ndarray:
