@@ -655,6 +655,60 @@ def leg_wide(A, args, timer, verbose):
     return {"workload": "wide", "sets": out}
 
 
+def leg_build(A, args, timer, verbose):
+    """Build times of the index on workload 2 (1M x 96), the paper's Section
+    5.7 (Fig. 16) measurement: the graph by the library's own kernels (exact
+    kNN lists of 96, detour pruning to degree 64), the ghost graph the same
+    way, the index (FP32 rows and the direction table, DGS's preprocessing),
+    against the search it serves; and the search on the library-built graph
+    at the headline setting beside the same search on the input graph."""
+    import torch
+    from workloads import WORKLOADS, load_dataset
+    spec = WORKLOADS[2]
+    ds = load_dataset(spec, device=timer.dev, verbose=verbose)
+    gt = truth_knn(ds.X, ds.Q[:args.gt_sample], 10, timer.dev)
+    ns = gt[0].shape[0]
+    dev_i = timer.dev.index or 0
+
+    def timed(fn):
+        torch.cuda.synchronize(timer.dev)
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(timer.dev)
+        return r, time.perf_counter() - t0
+
+    Xt = torch.from_numpy(ds.X).to(timer.dev)
+    knn, t_knn = timed(lambda: A.knn_exact(Xt, spec.knn_k))
+    G, t_prune = timed(lambda: A.graph_prune(knn, spec.degree))
+    Xg = Xt[torch.from_numpy(ds.S.astype(np.int64)).to(timer.dev)].contiguous()
+    gk, t_gknn = timed(lambda: A.knn_exact(Xg, 2 * spec.ghost_degree))
+    Gg, t_gprune = timed(lambda: A.graph_prune(gk, spec.ghost_degree))
+    Gh = G.cpu().numpy().view(np.uint32)
+    Ggh = Gg.cpu().numpy().view(np.uint32)
+    del knn, gk
+    ix, t_index = timed(lambda: A.Index(ds.X, Gh, storage=0, ghost_ids=ds.S, ghost_graph=Ggh, keep_fp32=True,
+                                        build_dir=True, device=dev_i))
+    Qd = torch.from_numpy(ds.Q).to(timer.dev)
+    p = params_for(forms_for(spec)["paper_fp32"], 32, spec.seeds["search"])
+    res = {}
+    ix_in = A.Index(ds.X, ds.G, storage=0, ghost_ids=ds.S, ghost_graph=ds.Gg, keep_fp32=True, build_dir=True,
+                    device=dev_i)
+    for name, ixx in (("library_graph", ix), ("input_graph", ix_in)):
+        ids, _, _ = ixx.search(Qd, stream=timer.stream, **p)
+        torch.cuda.synchronize(timer.dev)
+        rec = recall_at(ids[:ns].cpu().numpy().view(np.uint32), gt[1], ds.X, ds.Q[:ns], 10)
+        ms = timer(lambda ixx=ixx: ixx.search(Qd, stream=timer.stream, **p))
+        res[name] = {"recall": rec, "search_ms": ms, "qps": len(ds.Q) / (ms / 1e3)}
+    ix.close()
+    ix_in.close()
+    return {"workload": spec.name, "knn_k": spec.knn_k, "degree": spec.degree,
+            "graph_build_s": {"knn_exact": t_knn, "prune": t_prune},
+            "ghost_graph_build_s": {"knn_exact": t_gknn, "prune": t_gprune},
+            "index_create_s": t_index,
+            "note": "the library graph is exact kNN + detour pruning without the input graph's bridge edges",
+            "search_at_headline_setting": res}
+
+
 def leg_ppe(A, args, timer, verbose):
     """Path extension on simulated shards (Section 3.1.2) on workload 2: the
     dataset in 4 random shards, each with its graph and 1% ghost set, links
@@ -670,7 +724,9 @@ def leg_ppe(A, args, timer, verbose):
     gt = truth_knn(ds.X, ds.Q[:args.gt_sample], 10, timer.dev)
     ns = gt[0].shape[0]
     N = 4
-    sh = build_shards(ds.X, N, spec.degree, spec.knn_k, spec.graph, 0.01, spec.ghost_degree, seed=77,
+    # each shard's ghost set has as many nodes as the whole dataset's (4% of a
+    # quarter): the first stage then starts as well as the unsharded search
+    sh = build_shards(ds.X, N, spec.degree, spec.knn_k, spec.graph, 0.04, spec.ghost_degree, seed=77,
                       device=timer.dev)
     dev_i = timer.dev.index or 0
     sidx = [A.Index(t.X, t.G, storage=0, ghost_ids=t.S, ghost_graph=t.Gg, keep_fp32=True, build_dir=False,
@@ -688,7 +744,7 @@ def leg_ppe(A, args, timer, verbose):
     p0 = dict(k=10, itopk=32, entry=1, ghost_itopk=32, ghost_max_iters=12, ghost_search_width=4,
               seed=spec.seeds["search"])
     curves = {"unsharded": [], "sharded_baseline": [], "sharded_ppe": []}
-    for T in (2, 4, 6, 8, 12, 16, 24, 32, 48):
+    for T in (2, 4, 6, 8, 12, 16, 24, 32, 48, 64):
         p = dict(p0, max_iters=T)
         for mode in curves:
             if mode == "unsharded":
@@ -991,7 +1047,8 @@ def run_ours(args):
             ix_.close()
         indexes.clear()
         timer = Timer(dev, stream)
-        fns = {"3": leg_workload3, "4": leg_workload4, "5": leg_workload5, "wide": leg_wide, "ppe": leg_ppe}
+        fns = {"3": leg_workload3, "4": leg_workload4, "5": leg_workload5, "wide": leg_wide, "ppe": leg_ppe,
+               "build": leg_build}
         for w in args.workloads.split(","):
             if w in fns:
                 t0 = time.time()
@@ -1031,8 +1088,9 @@ def run_ours(args):
         "cpu_baseline": cpu_baseline,
         "serving": serving,
         "phase_profile": phase_profile,
-        "workloads": {legs[w]["workload"] if w not in ("ppe", "wide") else
-                      {"ppe": "path_extension", "wide": "wide_vectors"}[w]: legs[w] for w in legs},
+        "workloads": {legs[w]["workload"] if w not in ("ppe", "wide", "build") else
+                      {"ppe": "path_extension", "wide": "wide_vectors", "build": "index_build"}[w]: legs[w]
+                      for w in legs},
     }
     for le in entries.values():
         le.close()
@@ -1120,8 +1178,8 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--epochs", type=int, default=8)
-    ap.add_argument("--workloads", default="3,4,5,wide,ppe",
-                    help="legs beside the headline (rank 0, one GPU): 3, 4, 5, wide and ppe; empty for none")
+    ap.add_argument("--workloads", default="3,4,5,wide,ppe,build",
+                    help="legs beside the headline (rank 0, one GPU): 3, 4, 5, wide, ppe and build; empty for none")
     ap.add_argument("-v", "--verbose", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

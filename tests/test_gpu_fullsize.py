@@ -82,22 +82,25 @@ def test_scale_1m_bench_configuration():
     ix.close()
 
 
-@pytest.mark.parametrize("storage,k,itopk", [(O.F16, 10, 128), (O.E4M3, 10, 128), (O.F16, 100, 256)])
-def test_precision_10m(storage, k, itopk):
+@pytest.mark.parametrize("storage,k,itopk,ghost", [(O.F16, 10, 64, (128, 4, 64)), (O.E4M3, 10, 64, (128, 4, 64)),
+                                                   (O.F16, 100, 128, (256, 4, 48))])
+def test_precision_10m(storage, k, itopk, ghost):
     """Workload 3 (10M x 128 integers, degree 32): FP16 and E4M3 storage with
-    FP32 rerank, k = 10 and k = 100. The bar here is parity; recall is only
-    bounded below: the 10,000 clusters sit at nearly equal distances from one
-    another (uniform centers in 128-d), which leaves the ghost graph little
-    to steer by, and recall at these settings measured 0.86-0.89."""
+    FP32 rerank, k = 10 and k = 100, at recall@10 >= 0.95. A query's answer
+    lies in its own cluster; what decides recall is whether the ghost stage
+    reaches that cluster among 10,000 near-equidistant ones (85% with a
+    64-entry one-parent ghost queue, 98-100% with 128-256 entries and 4
+    parents per ghost iteration, measured), hence the wide ghost stage."""
     import paper_2507_17094_gb300 as A
     from workloads import WORKLOADS, load_dataset
     ds = load_dataset(WORKLOADS[3], device="cuda")
     ix = A.Index(ds.X, ds.G, storage=storage, ghost_ids=ds.S, ghost_graph=ds.Gg)
-    p = dict(k=k, itopk=itopk, max_iters=2 * itopk + 32, entry=1, dgs_discard=0.5, ghost_max_iters=64,
-             rerank=1, seed=4003)
+    lg, wg, tg = ghost
+    p = dict(k=k, itopk=itopk, max_iters=itopk + 16, entry=1, dgs_discard=0.5, ghost_itopk=lg,
+             ghost_search_width=wg, ghost_max_iters=tg, rerank=1, seed=4003)
     g_ids, g_d, st = gpu_search(ix, ds.Q, **p)
     assert (st["status"] == 0).all()
-    rec = check_sample(ds, storage, g_ids, g_d, sample_rows(len(ds.Q), 150, 2), p, 0.8)
+    rec = check_sample(ds, storage, g_ids, g_d, sample_rows(len(ds.Q), 150, 2), p, 0.95)
     Qd = torch.from_numpy(ds.Q).cuda()
     rate = qps(lambda: ix.search(Qd, **p), len(ds.Q))
     print(f"workload 3 storage {storage} k {k} itopk {itopk}: recall {rec:.3f}, {rate / 1e6:.3f}M QPS, "
@@ -108,7 +111,10 @@ def test_precision_10m(storage, k, itopk):
 def test_learned_entry_5m():
     """Workload 4 (5M x 256, Zipf cluster sizes, ghost set 50,000): the MLP
     256->512->512->50,000 trained on 200,000 ghost-staging labels, against
-    plain ghost staging on 10,000 held-out queries (20% between clusters)."""
+    plain ghost staging on 10,000 held-out queries (20% between clusters),
+    at the same queue size. Measured at itopk 256 with the benchmark's ghost
+    stage: ghost staging 0.946, learned entry 0.96-0.97 with a fifth of the
+    ghost rows."""
     import paper_2507_17094_gb300 as A
     from paper_2507_17094_gb300.entry import LearnedEntry, ghost_labels
     from workloads import WORKLOADS, init_mlp_params, load_dataset, make_queries
@@ -118,13 +124,14 @@ def test_learned_entry_5m():
     Qtr = torch.from_numpy(make_queries(spec, nq=200_000, seed=spec.seeds["query"] + 100)).cuda()
     Qva = torch.from_numpy(make_queries(spec, nq=5_000, seed=spec.seeds["query"] + 200)).cuda()
     le = LearnedEntry(ix, init_mlp_params(spec.d, 512, 512, spec.ghost_n, spec.seeds["mlp"]), max_batch=10_000)
-    losses = le.fit(Qtr, ghost_labels(ix, Qtr, seed=1), epochs=8, seed=3)
-    tau, hit = le.calibrate(Qva, ghost_labels(ix, Qva, seed=1))
-    assert losses[-1] < 0.5 * losses[0] and hit > 0.3   # measured: loss 7.1 -> 1.5, label in top 8 for 45%
+    losses = le.fit(Qtr, ghost_labels(ix, Qtr, seed=spec.seeds["search"]), epochs=8, seed=spec.seeds["mlp"])
+    tau, hit = le.calibrate(Qva, ghost_labels(ix, Qva, seed=spec.seeds["search"]))
+    assert losses[-1] < 0.5 * losses[0] and hit > 0.5   # measured: loss 8.0 -> 0.79, label in top 8 for 54%
     Q = torch.from_numpy(ds.Q).cuda()
     seeds, _ = le.seeds(Q)
-    common = dict(k=10, itopk=64, max_iters=160, dgs_discard=0.5, rerank=1, seed=4004, ghost_max_iters=64)
-    idx = sample_rows(len(ds.Q), 200, 3)
+    common = dict(k=10, itopk=256, max_iters=272, dgs_discard=0.5, rerank=1, seed=4004, ghost_itopk=128,
+                  ghost_search_width=4, ghost_max_iters=48)
+    idx = sample_rows(len(ds.Q), 300, 3)
     gt, gd = O.knn_f64(ds.X, ds.Q[idx], 10)
     out = {}
     for name, extra in (("ghost", dict(entry=1)), ("learned", dict(entry=2, given=seeds, ghost_max_iters_given=4))):
@@ -143,7 +150,7 @@ def test_learned_entry_5m():
           f"{out['learned'][1]:.0f} {out['learned'][2] / 1e6:.3f}M QPS (predict included); tau {tau:.3g}, "
           f"val hit {hit:.3f}, fallback {float((seeds[:, 0] == -1).float().mean()):.3f}")
     assert out["learned"][1] < out["ghost"][1]
-    assert out["learned"][0] >= out["ghost"][0] - 0.02
+    assert out["learned"][0] >= 0.95 and out["learned"][0] >= out["ghost"][0] - 0.005
     le.close()
     ix.close()
 
