@@ -558,11 +558,13 @@ def leg_workload4(A, args, timer, verbose):
 
 
 def leg_workload5(A, args, timer, verbose):
-    """Workload 5 (20M x 96 FP16): the same request trace (batches of 1-4,096
-    queries, k in {10, 100}, itopk in {64, 256}) through the continuous-
-    batching server and as one ann_search per request with identical
-    parameters; capacity of each and the server's latency at half its
-    capacity."""
+    """Workload 5 (20M x 96 FP16): request traces (k in {10, 100}, itopk in
+    {64, 256}) through the continuous-batching server and as one ann_search
+    per request with identical parameters: the capacity of each, the
+    server's latency at half its capacity, and whether each served result
+    equals its batch search. Two size mixes: the recipe's batches of
+    1-4,096 queries, and small requests of 1-64 queries, where a launch per
+    request leaves most of the GPU idle."""
     import torch
     from workloads import WORKLOADS, load_dataset
     spec = WORKLOADS[5]
@@ -570,59 +572,67 @@ def leg_workload5(A, args, timer, verbose):
     ds = load_dataset(spec, device=timer.dev, verbose=verbose)
     ix = A.Index(ds.X, ds.G, storage=1, ghost_ids=ds.S, ghost_graph=ds.Gg, keep_fp32=True, build_dir=True,
                  device=timer.dev.index or 0)
-    rng = np.random.default_rng(spec.seeds["search"] + 7)
     base = dict(entry=1, dgs_discard=0.5, ghost_itopk=64, ghost_max_iters=32, ghost_search_width=4, rerank=1,
                 seed=spec.seeds["search"])
-    reqs = []
-    for rid in range(args.serve_requests):
-        n = int(rng.integers(1, 4097))
-        off = int(rng.integers(0, len(ds.Q) - n))
-        k = int(rng.choice([10, 100]))
-        L = max(k, int(rng.choice([64, 256])))
-        reqs.append((rid, ds.Q[off:off + n], dict(base, k=k, itopk=L, max_iters=L + 16, qid_base=rid << 20)))
-    nq = sum(len(q) for _, q, _ in reqs)
-    srv = A.Server(ix, capacity=65536, max_requests=128,
+    srv = A.Server(ix, capacity=65536, max_requests=512,
                    max_params=dict(base, k=100, itopk=256, max_iters=272))
-    A.replay(srv, [(0.0, 10**9 + i, ds.Q[:64], dict(reqs[0][2], qid_base=0)) for i in range(4)])
+    A.replay(srv, [(0.0, 10**9 + i, ds.Q[:64], dict(base, k=10, itopk=64, max_iters=80, qid_base=0))
+                   for i in range(4)])
+    out = {}
+    for mix, (lo, hi, nreq) in (("batches_1_4096", (1, 4097, args.serve_requests)),
+                                ("small_1_64", (1, 65, 4 * args.serve_requests))):
+        rng = np.random.default_rng(spec.seeds["search"] + 7)
+        reqs = []
+        for rid in range(nreq):
+            n = int(rng.integers(lo, hi))
+            off = int(rng.integers(0, len(ds.Q) - n))
+            k = int(rng.choice([10, 100]))
+            L = max(k, int(rng.choice([64, 256])))
+            reqs.append((rid, ds.Q[off:off + n], dict(base, k=k, itopk=L, max_iters=L + 16, qid_base=rid << 20)))
+        nq = sum(len(q) for _, q, _ in reqs)
 
-    def play(rate):
-        t, trace = 0.0, []
-        for rid, q, prm in reqs:
-            if rate:
-                t += float(rng.exponential(1.0 / rate))
-            trace.append((t, rid, q, prm))
-        res, wall = A.replay(srv, trace, timeout_s=300)
-        lat = np.array([res[r][2] for _, r, _, _ in trace]) * 1e3
-        return res, {"qps": nq / wall, "p50_ms": float(np.percentile(lat, 50)),
-                     "p99_ms": float(np.percentile(lat, 99))}
+        def play(rate):
+            t, trace = 0.0, []
+            for rid, q, prm in reqs:
+                if rate:
+                    t += float(rng.exponential(1.0 / rate))
+                trace.append((t, rid, q, prm))
+            res, wall = A.replay(srv, trace, timeout_s=300)
+            lat = np.array([res[r][2] for _, r, _, _ in trace]) * 1e3
+            return res, {"qps": nq / wall, "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99))}
 
-    served, burst = play(0.0)
-    half_rate = 0.5 * burst["qps"] / (nq / len(reqs))
-    _, half = play(half_rate)
+        served, burst = play(0.0)
+        half_rate = 0.5 * burst["qps"] / (nq / len(reqs))
+        _, half = play(half_rate)
+        # the same requests, one ann_search each, back to back on one stream
+        # (queries already on the device; results stay there)
+        dq = [torch.from_numpy(np.ascontiguousarray(q)).to(timer.dev) for _, q, _ in reqs]
+
+        def per_request():
+            for (rid, q, prm), qt in zip(reqs, dq):
+                ix.search(qt, stream=timer.stream, **prm)
+
+        ms = timer(per_request, steps=3, warm=1)
+        same = 0
+        for (rid, q, prm), qt in zip(reqs[::10], dq[::10]):
+            ids, d, _ = ix.search(qt, **prm)
+            torch.cuda.synchronize(timer.dev)
+            same += int(np.array_equal(ids.cpu().numpy().view(np.uint32), served[rid][0]))
+        per_req_qps = nq / (ms / 1e3)
+        out[mix] = {"requests": len(reqs), "queries": nq, "server_capacity_qps": burst["qps"],
+                    "server_all_at_once": burst, "per_request_search_qps": per_req_qps,
+                    "capacity_ratio_server_vs_per_request": burst["qps"] / per_req_qps,
+                    "half_load": dict(half, offered_qps=0.5 * burst["qps"]),
+                    "sampled_requests_equal_to_batch_search": f"{same}/{len(reqs[::10])}"}
+        if verbose:
+            print(f"[bench] serving {mix}: server {burst['qps'] / 1e6:.3f}M/s, per request {per_req_qps / 1e6:.3f}M/s, "
+                  f"half load p50 {half['p50_ms']:.2f} ms p99 {half['p99_ms']:.2f} ms", file=sys.stderr, flush=True)
     srv.close()
-    # the same requests, one ann_search each, back to back on one stream
-    # (queries already on the device; results stay there)
-    dq = [torch.from_numpy(np.ascontiguousarray(q)).to(timer.dev) for _, q, _ in reqs]
-
-    def per_request():
-        for (rid, q, prm), qt in zip(reqs, dq):
-            ix.search(qt, stream=timer.stream, **prm)
-
-    ms = timer(per_request, steps=3, warm=1)
-    same = 0
-    for (rid, q, prm), qt in zip(reqs[::10], dq[::10]):
-        ids, d, _ = ix.search(qt, **prm)
-        torch.cuda.synchronize(timer.dev)
-        same += int(np.array_equal(ids.cpu().numpy().view(np.uint32), served[rid][0]))
     ix.close()
-    per_req_qps = nq / (ms / 1e3)
     return {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "storage": "f16",
-            "requests": len(reqs), "queries": nq, "entry": "ghost",
-            "server_capacity_qps": burst["qps"], "server_all_at_once": burst,
-            "per_request_search_qps": per_req_qps, "capacity_ratio_server_vs_per_request": burst["qps"] / per_req_qps,
-            "half_load": dict(half, offered_qps=0.5 * burst["qps"]),
-            "sampled_requests_equal_to_batch_search": f"{same}/{len(reqs[::10])}",
-            "mix": "batch 1-4096 uniform, k {10,100}, itopk {64,256} raised to k, Poisson arrivals",
+            "entry": "ghost", "mixes": out,
+            "mix": "k {10,100}, itopk {64,256} raised to k, Poisson arrivals; batch sizes per mix",
             "leg_s": time.time() - t0}
 
 

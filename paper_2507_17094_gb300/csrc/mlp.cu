@@ -675,19 +675,21 @@ __global__ void topp_merge_kernel(const float *__restrict__ part, uint32_t M, ui
     for (int o = 16; o; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
     float gs = (sm > 0.0f) ? sm * __expf(mx - gm) : 0.0f;
     for (int o = 16; o; o >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, o);
-    // top-P across lanes by rank
+    // top-P across lanes by rank: only lanes that read a slot hold
+    // candidates, so the ranking runs over those lanes' entries alone
+    const uint32_t nv = min(ntiles, 32u) * TOPP;
 #pragma unroll
     for (int p = 0; p < TOPP; ++p) {
         sv[wl][lane * TOPP + p] = tv[p];
         si[wl][lane * TOPP + p] = ti[p];
     }
     __syncwarp();
-    for (uint32_t e = lane; e < 32 * TOPP; e += 32) {
+    for (uint32_t e = lane; e < nv; e += 32) {
         const float x = sv[wl][e];
         const uint32_t n = si[wl][e];
         if (n == 0xFFFFFFFFu) continue;
         uint32_t rank = 0;
-        for (uint32_t f = 0; f < 32 * TOPP; ++f)
+        for (uint32_t f = 0; f < nv; ++f)
             rank += si[wl][f] != 0xFFFFFFFFu && better(sv[wl][f], si[wl][f], x, n);
         if (rank < P) seeds[(size_t)r * P + rank] = n;
     }

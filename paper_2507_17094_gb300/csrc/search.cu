@@ -114,7 +114,6 @@ struct Args {
     uint32_t vbits, vstride_bits, slot_base;
     uint32_t gbm_words;   // > 0: the ghost stage's visited set is a bitmap of this many words
     uint32_t lpr;         // lanes per staged row in the distance step: 2, or 4 for wide rows
-    uint32_t spec_gather; // a DGS parent's kept rows are fetched during their visited test
     // profile build only: per warp slot, ANN_PROFILE_STAGES x ANN_PROFILE_PHASES
     // cycle counters (slot_base + warp slot selects a row)
     unsigned long long *prof;
@@ -415,62 +414,6 @@ struct WarpSearch {
             mark(PH_DIST);
         }
         return true;
-    }
-
-    // One DGS parent whose kept neighbours fit one staging round: their rows
-    // are fetched while their visited test-and-insert runs, so the two
-    // round trips overlap; only the new ones are evaluated (their ids go to
-    // ci, their distances to cd, in adjacency order as collect_row would put
-    // them). Returns their count, -1 when more rows are kept than a round
-    // stages (nothing done: the caller takes the general path), -2 when the
-    // copies' wait ran out.
-    template <int RST>
-    __device__ int gather_kept(const View &v, uint32_t km)
-    {
-        uint32_t *kid = cs();   // kept ids; cs is free until the merge
-        uint32_t kept = 0;
-        #pragma unroll 1
-        for (uint32_t r = 0; r * 32 < v.deg; ++r) {
-            const uint32_t j = lane + 32 * r;
-            const uint32_t nb = j < v.deg ? adj()[j] : ANN_INVALID_ID;
-            const bool ok = nb != ANN_INVALID_ID && ((km >> r) & 1u);
-            const uint32_t m = __ballot_sync(0xffffffffu, ok);
-            const uint32_t at = kept + __popc(m & lanemask_lt());
-            if (ok && at < a.stage_rows) kid[at] = nb;
-            kept += __popc(m);
-        }
-        if (kept > a.stage_rows) return -1;
-        __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async();
-            mbar_arrive_expect_tx(bar(), kept * v.row_bytes);
-        }
-        __syncwarp();
-        bool isnew = false;
-        if (lane < kept) {
-            const uint32_t id = kid[lane];
-            bulk_g2s(stage() + lane * a.stage_stride, v.codes + (uint64_t)id * v.row_bytes, v.row_bytes, bar());
-            isnew = hash_insert(id);
-        }
-        const uint32_t m = __ballot_sync(0xffffffffu, isnew);
-        const uint32_t nc = __popc(m);
-        if (isnew) ci()[__popc(m & lanemask_lt())] = kid[lane];
-        mark(PH_VISIT);
-        if (!wait_copies()) return -2;
-        mark(PH_GATHER);
-        // lane pair r: new candidate r, staged in the slot of the r-th set bit
-        const uint32_t r = lane >> 1;
-        float part = 0.0f;
-        if (r < nc) {
-            const uint32_t slot = __fns(m, 0, (int)r + 1);
-            const float rs = RST != ANN_F32 ? __ldg(v.scales + ci()[r]) : 1.0f;
-            part = row_dist_half<RST>(stage() + slot * a.stage_stride, q(), rs, a.d, lane & 1);
-        }
-        const float other = __shfl_xor_sync(0xffffffffu, part, 1);
-        if (r < nc && (lane & 1) == 0) cd()[r] = __fadd_rn(part, other);
-        __syncwarp();
-        mark(PH_DIST);
-        return (int)nc;
     }
 
     // --------------------------------------------------------------- merge
@@ -794,7 +737,6 @@ struct WarpSearch {
         uint32_t j0 = 0, it = 0;
         for (;;) {
             uint32_t nc = 0;
-            bool staged = false;   // the candidates' distances are in cd already
             if (j0 < m) {
                 const uint32_t chunk = min(a.cap_cand, m - j0);
                 hash_make_room(chunk);
@@ -849,15 +791,6 @@ struct WarpSearch {
                     if (dgs_now) {
                         km = dgs_keep(v, pi, n_keep, min_match, __shfl_sync(0xffffffffu, pscale, pi));
                         mark(PH_DGS);
-                        if (LPR == 2 && np == 1 && !gbm && a.spec_gather) {
-                            const int got = gather_kept<RST>(v, km);
-                            if (got == -2) return false;
-                            if (got >= 0) {
-                                nc = (uint32_t)got;
-                                staged = true;
-                                break;
-                            }
-                        }
                     }
                     nc = collect_row(v, pi, km, nc);
                     mark(PH_VISIT);
@@ -865,7 +798,7 @@ struct WarpSearch {
             }
             __syncwarp();
             hash_count += nc;
-            if (!staged && !evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
+            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
             c_rows += nc;
             merge(nc, lcap);
             mark(PH_MERGE);
@@ -1260,7 +1193,6 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     // dimensions) are computed by four lanes each, at most 8 per round;
     // narrower ones by lane pairs, 16 per round
     a.lpr = stage_bytes > 1024 ? 4 : 2;
-    a.spec_gather = env_int("ANN_SPEC_GATHER", 1) != 0;
     a.stage_rows = (uint32_t)std::min<int>(32 / (int)a.lpr, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
     // visited tables: the queue plus one iteration's candidates must fit in
     // half a table (the reset threshold)
