@@ -762,12 +762,23 @@ def leg_ppe(A, args, timer, verbose):
             else:
                 fwd = 1 if mode == "sharded_ppe" else 0
                 run = lambda p=p, fwd=fwd: ring.search(Qd, n_forward=fwd, stream=timer.stream, **p)   # noqa: E731
-            ids, _, _ = run()
+            if mode == "unsharded":
+                ids, _, st = full.search(Qd, stream=timer.stream, stats=True, **p)
+            else:
+                ids, _, st = ring.search(Qd, n_forward=1 if mode == "sharded_ppe" else 0, stats=True,
+                                         stream=timer.stream, **p)
             torch.cuda.synchronize(timer.dev)
+            stn = A.stats_to_numpy(st.reshape(-1, st.shape[-1]))
+            # iterations per query summed over its stages: base and ghost
+            it_q = (stn["iters"].astype(np.int64) + stn["ghost_iters"]).reshape(-1, nq).sum(axis=0)
             rec = recall_at(ids[:ns].cpu().numpy().view(np.uint32), gt[1], ds.X, ds.Q[:ns], 10)
             ms = timer(run)
-            curves[mode].append({"max_iters": T, "recall": rec, "qps": nq / (ms / 1e3)})
+            curves[mode].append({"max_iters": T, "recall": rec, "qps": nq / (ms / 1e3),
+                                 "iters_per_query": float(it_q.mean()),
+                                 "rows_per_query": float((stn["vec_rows"].astype(np.int64) + stn["ghost_vec_rows"])
+                                                         .reshape(-1, nq).sum(axis=0).mean())})
     reach = {m: next((c["max_iters"] for c in v if c["recall"] >= 0.90), None) for m, v in curves.items()}
+    reach_it = {m: next((c["iters_per_query"] for c in v if c["recall"] >= 0.90), None) for m, v in curves.items()}
     ring.close()
     for ix in sidx:
         ix.close()
@@ -776,7 +787,8 @@ def leg_ppe(A, args, timer, verbose):
         print(f"[bench] ppe: iterations to recall 0.90 {reach}", file=sys.stderr, flush=True)
     return {"workload": spec.name, "shards": N, "shard_n": [int(len(t.ids)) for t in sh], "forwarded": 1,
             "link_params": link_p, "link_build_s": link_s, "search": {k: v for k, v in p0.items() if k != "seed"},
-            "iters_to_recall_0.90": reach, "curves": curves, "leg_s": time.time() - t0}
+            "iters_to_recall_0.90": reach, "total_iters_per_query_at_recall_0.90": reach_it, "curves": curves,
+            "leg_s": time.time() - t0}
 
 
 # ------------------------------------------------------------------ our arm

@@ -15,9 +15,10 @@
 // one of several compute streams, so kernels of successive requests overlap
 // and every running kernel takes queries from the same FIFO: a request that
 // arrives while others are on the GPU is picked up as soon as a warp frees.
-// Each launch has capacity (blocks x warps x queries per warp) for at least
-// its own request, and a kernel only leaves early when the ring is empty, so
-// every published query is served.
+// Each launch has capacity (blocks x warps x queries per warp) for every
+// query in flight, its own request's included (so a burst of small requests
+// fills the GPU instead of one block per request), and a kernel only leaves
+// early when the ring is empty, so every published query is served.
 //
 // poll(): a request is done when its host-mapped flag is set (by the warp
 // that finished its last query, after a system-scope fence); its results are
@@ -277,7 +278,12 @@ ann_status ann_server_submit(ann_server *s, uint64_t req_id, const float *querie
             r.cap = s->cap;
             r.kmax = s->kmax;
             r.per_warp = s->per_warp;
-            st = serve_launch(s->plan, r, nq, c, si);
+            // sized for every query not yet known complete (this request and
+            // the ones before it), not just this request's: the kernel's
+            // warps pop any query from the ring, and warps that find it empty
+            // leave at once, so a burst of small requests still fills the GPU
+            const uint64_t pending = s->tail + nq - oldest;
+            st = serve_launch(s->plan, r, (uint32_t)std::min<uint64_t>(pending, s->cap), c, si);
         }
     }
     if (st == ANN_OK && e != cudaSuccess) st = cuda_fail(e, "ann_server_submit");
