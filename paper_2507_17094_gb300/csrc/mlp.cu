@@ -129,6 +129,41 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Cluster helpers (the multicast logits kernel runs in clusters of two CTAs).
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// A 2-D TMA load whose data, and the completion of its bytes, land at the
+// same shared-memory offsets in every CTA of `mask` within the cluster.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                               uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, "
+        "{%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar)), "h"(mask)
+        : "memory");
+}
+
+// tcgen05.commit arriving on the barrier at the same offset in every CTA of `mask`.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_addr(bar)),
+        "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -320,11 +355,16 @@ __device__ __forceinline__ void topp_flush(const EpiArgs &e, const TopP &tp, uin
     o[2 * TOPP + 1] = tp.sm;
 }
 
-template <int EPI, bool RESA = false>
+// MODE 0: the ring of (A, B) tiles; 1: resident A; 2: resident A, and the
+// CTAs run in clusters of two on the two row blocks of a pair, loading half
+// of each B tile each and multicasting it to both (B is read from L2 once
+// per pair instead of once per CTA).
+template <int EPI, int MODE = 0>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, uint32_t M,
                 uint32_t N, uint32_t K, EpiArgs e)
 {
+    constexpr bool RESA = MODE >= 1, MC = MODE == 2;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;
     uint8_t *smem = smem_raw + pad;
@@ -345,14 +385,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t nkb = (K + BK - 1) / BK;
     const uint32_t n_tiles = (N + BN - 1) / BN, m_tiles = (M + BM - 1) / BM;
-    const uint32_t tiles = n_tiles * m_tiles;
-    const uint32_t per = (tiles + gridDim.x - 1) / gridDim.x;
-    const uint32_t t_begin = min(tiles, blockIdx.x * per), t_end = min(tiles, t_begin + per);
+    // work units: tiles, or with clusters (row-block pair, column tile);
+    // unit t covers row block rb(t) = row unit (t / n_tiles), or with
+    // clusters row block 2 (t / n_tiles) + the CTA's rank in its pair
+    const uint32_t crank = MC ? cluster_rank() : 0u;
+    const uint32_t units = MC ? gridDim.x / 2 : gridDim.x, me = MC ? blockIdx.x / 2 : blockIdx.x;
+    const uint32_t tiles = n_tiles * (MC ? (m_tiles + 1) / 2 : m_tiles);
+    const uint32_t per = (tiles + units - 1) / units;
+    const uint32_t t_begin = min(tiles, me * per), t_end = min(tiles, t_begin + per);
+    auto rb_of_unit = [&](uint32_t u) { return MC ? 2 * u + crank : u; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], MC ? 2 : 1);   // with clusters, both CTAs' MMAs free a stage
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -362,6 +408,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         mbar_init(a_empty, 1);
         fence_mbar_init();
     }
+    // both CTAs' barriers exist before either multicasts into the other
+    if (MC) cluster_sync_all();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
                      "r"((uint32_t)(2 * BN))
@@ -377,23 +425,27 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (lane == 0) {
             // A once per row block (after the MMAs on the previous one are
             // done), then the B tiles of each of the block's column tiles
-            uint32_t it = 0, loads = 0, cur_m = 0xFFFFFFFFu;
+            uint32_t it = 0, loads = 0, cur_u = 0xFFFFFFFFu;
             bool ok = true;
             for (uint32_t t = t_begin; t < t_end && ok; ++t) {
-                const uint32_t mb = t / n_tiles, n0 = (t % n_tiles) * BN;
-                if (mb != cur_m) {
+                const uint32_t u = t / n_tiles, n0 = (t % n_tiles) * BN;
+                if (u != cur_u) {
                     if (loads > 0 && !(ok = mbar_wait_bounded(a_empty, (loads - 1) & 1, e.err))) break;
                     mbar_arrive_expect_tx(a_full, nkb * TILE_A);
                     for (uint32_t kb = 0; kb < nkb; ++kb)
-                        tma_load_2d(sA + kb * TILE_A, &tA, (int)(kb * BK), (int)(mb * BM), a_full);
-                    cur_m = mb;
+                        tma_load_2d(sA + kb * TILE_A, &tA, (int)(kb * BK), (int)(rb_of_unit(u) * BM), a_full);
+                    cur_u = u;
                     ++loads;
                 }
                 for (uint32_t kb = 0; kb < nkb; ++kb, ++it) {
                     const uint32_t s = it % NST, ph = (it / NST) & 1;
                     if (!(ok = mbar_wait_bounded(&empty[s], ph ^ 1, e.err))) break;
                     mbar_arrive_expect_tx(&full[s], TILE_B);
-                    tma_load_2d(sB + s * TILE_B, &tB, (int)(kb * BK), (int)n0, &full[s]);
+                    if (MC)   // this CTA's half of the B tile (64 rows), to both CTAs
+                        tma_load_2d_mc(sB + s * TILE_B + crank * (TILE_B / 2), &tB, (int)(kb * BK),
+                                       (int)(n0 + crank * (BN / 2)), &full[s], (uint16_t)3);
+                    else
+                        tma_load_2d(sB + s * TILE_B, &tB, (int)(kb * BK), (int)n0, &full[s]);
                 }
             }
         }
@@ -415,13 +467,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     } else if (warp == 1 && RESA) {
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16(BM, BN);
-            uint32_t it = 0, tc = 0, loads = 0, cur_m = 0xFFFFFFFFu;
+            uint32_t it = 0, tc = 0, loads = 0, cur_u = 0xFFFFFFFFu;
             bool ok = true;
             for (uint32_t t = t_begin; t < t_end && ok; ++t, ++tc) {
-                const uint32_t mb = t / n_tiles;
-                if (mb != cur_m) {
+                const uint32_t u = t / n_tiles;
+                if (u != cur_u) {
                     if (!(ok = mbar_wait_bounded(a_full, loads & 1, e.err))) break;
-                    cur_m = mb;
+                    cur_u = u;
                     ++loads;
                 }
                 const uint32_t buf = tc & 1, use = tc >> 1;
@@ -436,12 +488,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
                     for (uint32_t k = 0; k < BK / 16; ++k)
                         mma_bf16(acc, desc_sw128(a0 + k * 32), desc_sw128(b0 + k * 32), idesc, (kb | k) != 0);
-                    mma_commit(&empty[s]);
+                    if (MC) mma_commit_mc(&empty[s], (uint16_t)3);   // frees the stage in both CTAs
+                    else mma_commit(&empty[s]);
                 }
                 mma_commit(&acc_full[buf]);
                 // the last tile of this row block: A may be replaced once
                 // these MMAs are done
-                if (t + 1 < t_end && (t + 1) / n_tiles != mb) mma_commit(a_empty);
+                if (t + 1 < t_end && (t + 1) / n_tiles != u) mma_commit(a_empty);
             }
         }
     } else if (warp == 1) {
@@ -471,7 +524,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         // epilogue warps 2..9: warp w reads accumulator lanes 32 * (w % 4) ..
         // + 31 (its quarter) and columns 64 * h .. + 63 of each tile
         const uint32_t q = warp & 3, h = (warp - 2) >> 2;
-        uint32_t tc = 0, cur_m = 0xFFFFFFFFu;
+        uint32_t tc = 0, cur_u = 0xFFFFFFFFu;
         TopP tp;
         tp.reset();
         for (uint32_t t = t_begin; t < t_end; ++t, ++tc) {
@@ -479,16 +532,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[buf], use & 1, e.err));
             if (!ok) break;
             tc_fence_after();
-            const uint32_t mb = t / n_tiles, n0 = (t % n_tiles) * BN;
-            const uint32_t m = mb * BM + q * 32 + lane;
-            if (EPI == EPI_TOPP && mb != cur_m) {
+            const uint32_t u = t / n_tiles, n0 = (t % n_tiles) * BN;
+            const uint32_t m = rb_of_unit(u) * BM + q * 32 + lane;
+            if (EPI == EPI_TOPP && u != cur_u) {
                 // a new row block: the previous one's partial is complete
-                if (cur_m != 0xFFFFFFFFu) {
-                    const uint32_t pm = cur_m * BM + q * 32 + lane;
-                    if (pm < M) topp_flush(e, tp, pm, (blockIdx.x - (cur_m * n_tiles) / per) * 2 + h);
+                if (cur_u != 0xFFFFFFFFu) {
+                    const uint32_t pm = rb_of_unit(cur_u) * BM + q * 32 + lane;
+                    if (pm < M) topp_flush(e, tp, pm, (me - (cur_u * n_tiles) / per) * 2 + h);
                 }
                 tp.reset();
-                cur_m = mb;
+                cur_u = u;
             }
 #pragma unroll 1
             for (uint32_t c0 = h * (BN / 2); c0 < (h + 1) * (BN / 2); c0 += 32) {
@@ -501,13 +554,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
-        if (EPI == EPI_TOPP && cur_m != 0xFFFFFFFFu) {
-            const uint32_t pm = cur_m * BM + q * 32 + lane;
-            if (pm < M) topp_flush(e, tp, pm, (blockIdx.x - (cur_m * n_tiles) / per) * 2 + h);
+        if (EPI == EPI_TOPP && cur_u != 0xFFFFFFFFu) {
+            const uint32_t pm = rb_of_unit(cur_u) * BM + q * 32 + lane;
+            if (pm < M) topp_flush(e, tp, pm, (me - (cur_u * n_tiles) / per) * 2 + h);
         }
     }
     tc_fence_before();
     __syncthreads();
+    // no CTA leaves while its pair may still multicast into it or arrive on
+    // its barriers
+    if (MC) cluster_sync_all();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
                      : "memory");
@@ -875,14 +931,14 @@ ann_status get_encoder()
 }
 
 // Tensor map of a row-major BF16 matrix (rows x K, row stride K elements),
-// box BK x 128, 128-byte swizzle; out-of-range elements read as zero.
-ann_status make_map(CUtensorMap *map, const void *ptr, uint32_t rows, uint32_t K)
+// box BK x box_rows, 128-byte swizzle; out-of-range elements read as zero.
+ann_status make_map(CUtensorMap *map, const void *ptr, uint32_t rows, uint32_t K, uint32_t box_rows = 128)
 {
     ann_status s = get_encoder();
     if (s != ANN_OK) return s;
     const cuuint64_t dims[2] = {K, rows};
     const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    const cuuint32_t box[2] = {BK, 128};
+    const cuuint32_t box[2] = {BK, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -894,23 +950,76 @@ ann_status make_map(CUtensorMap *map, const void *ptr, uint32_t rows, uint32_t K
     return ANN_OK;
 }
 
-// One persistent CTA per SM (fewer if there are fewer tiles).
-uint32_t gemm_grid(uint32_t M, uint32_t N, uint32_t sms)
+// Which GEMM variant runs: the fused top-P logits with K <= RES_K keep A
+// resident (ANN_GEMM_RESIDENT_A=0 turns that off); ANN_GEMM_MULTICAST=1
+// runs them in clusters of two CTAs that share each B tile by multicast
+// (measured no faster: the L2 reads of B are not what bounds the kernel);
+// everything else streams both operands.
+int gemm_mode(int epi, uint32_t K)
 {
-    const uint32_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-    return std::max(1u, std::min(tiles, sms));
+    static const bool res_on = env_flag("ANN_GEMM_RESIDENT_A", true);
+    static const bool mc_on = env_flag("ANN_GEMM_MULTICAST", false);
+    if (epi != EPI_TOPP || K > (uint32_t)RES_K || !res_on) return 0;
+    return mc_on ? 2 : 1;
+}
+
+// Work units of a launch (tiles, or with clusters row-block pairs x column
+// tiles) and the persistent grid: one CTA per SM (pairs of CTAs with
+// clusters), fewer if there is less work.
+uint32_t gemm_units(uint32_t M, uint32_t N, int mode)
+{
+    const uint32_t n_tiles = (N + BN - 1) / BN, m_tiles = (M + BM - 1) / BM;
+    return n_tiles * (mode == 2 ? (m_tiles + 1) / 2 : m_tiles);
+}
+
+// Clusters of two that can be resident at once (SMs pair up within a GPC,
+// so this can be below half the SM count); queried once.
+uint32_t pair_slots(uint32_t sms);
+
+uint32_t gemm_grid(uint32_t M, uint32_t N, uint32_t sms, int mode = 0)
+{
+    const uint32_t units = gemm_units(M, N, mode);
+    return mode == 2 ? 2 * std::max(1u, std::min(units, pair_slots(sms))) : std::max(1u, std::min(units, sms));
 }
 
 // Top-P partial slots per row: two column halves times the largest number
-// of CTAs whose contiguous tile ranges meet one row block.
-uint32_t topp_slots(uint32_t M, uint32_t N, uint32_t sms)
+// of CTAs (pairs, with clusters) whose contiguous unit ranges meet one row
+// unit.
+uint32_t topp_slots(uint32_t M, uint32_t N, uint32_t sms, int mode)
 {
-    const uint32_t n_tiles = (N + BN - 1) / BN, m_tiles = (M + BM - 1) / BM;
-    const uint32_t tiles = n_tiles * m_tiles, per = (tiles + gemm_grid(M, N, sms) - 1) / gemm_grid(M, N, sms);
+    const uint32_t n_tiles = (N + BN - 1) / BN;
+    const uint32_t units = gemm_units(M, N, mode), row_units = units / n_tiles;
+    const uint32_t ctas = mode == 2 ? gemm_grid(M, N, sms, mode) / 2 : gemm_grid(M, N, sms, mode);
+    const uint32_t per = (units + ctas - 1) / ctas;
     uint32_t smax = 1;
-    for (uint32_t mb = 0; mb < m_tiles; ++mb)
-        smax = std::max(smax, ((mb + 1) * n_tiles - 1) / per - (mb * n_tiles) / per + 1);
+    for (uint32_t u = 0; u < row_units; ++u)
+        smax = std::max(smax, ((u + 1) * n_tiles - 1) / per - (u * n_tiles) / per + 1);
     return 2 * smax;
+}
+
+uint32_t pair_slots(uint32_t sms)
+{
+    static uint32_t cached = 0;
+    if (!cached) {
+        cudaFuncSetAttribute(gemm_kernel<EPI_TOPP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, RES_SMEM);
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(sms);
+        cfg.blockDim = dim3(GEMM_THREADS);
+        cfg.dynamicSmemBytes = RES_SMEM;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, gemm_kernel<EPI_TOPP, 2>, &cfg) != cudaSuccess || n <= 0)
+            n = (int)(sms / 2);
+        cudaGetLastError();
+        cached = (uint32_t)std::min<int>(n, (int)(sms / 2));
+    }
+    return cached;
 }
 
 template <int EPI>
@@ -922,29 +1031,44 @@ ann_status gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, uint32_t M, uint
         set_error("gemm: K = %u must be a multiple of 8", K);
         return ANN_EINVAL;
     }
+    const int mode = gemm_mode(EPI, K);
     CUtensorMap ta, tb;
     ann_status s = make_map(&ta, A, M, K);
-    if (s == ANN_OK) s = make_map(&tb, B, N, K);
+    if (s == ANN_OK) s = make_map(&tb, B, N, K, mode == 2 ? BN / 2 : 128);
     if (s != ANN_OK) return s;
-    // the fused top-P logits keep A resident when it fits (ANN_GEMM_RESIDENT_A=0 turns that off)
-    static const bool res_on = env_flag("ANN_GEMM_RESIDENT_A", true);
-    const bool resa = EPI == EPI_TOPP && K <= (uint32_t)RES_K && res_on;
-    static bool attr = false, attr_res = false;
-    if (resa && !attr_res) {
-        ANN_CUDA(cudaFuncSetAttribute(gemm_kernel<EPI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, RES_SMEM));
-        attr_res = true;
-    }
-    if (!resa && !attr) {
-        ANN_CUDA(cudaFuncSetAttribute(gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
-        attr = true;
+    static bool attr[3] = {false, false, false};
+    if (!attr[mode]) {
+        if (mode == 0)
+            ANN_CUDA(cudaFuncSetAttribute(gemm_kernel<EPI, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM));
+        else if (mode == 1)
+            ANN_CUDA(cudaFuncSetAttribute(gemm_kernel<EPI, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RES_SMEM));
+        else
+            ANN_CUDA(cudaFuncSetAttribute(gemm_kernel<EPI, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, RES_SMEM));
+        attr[mode] = true;
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (resa)
-        gemm_kernel<EPI, true><<<gemm_grid(M, N, (uint32_t)sms), GEMM_THREADS, RES_SMEM, st>>>(ta, tb, M, N, K, e);
-    else
-        gemm_kernel<EPI><<<gemm_grid(M, N, (uint32_t)sms), GEMM_THREADS, GEMM_SMEM, st>>>(ta, tb, M, N, K, e);
+    const uint32_t grid = gemm_grid(M, N, (uint32_t)sms, mode);
+    if (mode == 0) {
+        gemm_kernel<EPI, 0><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(ta, tb, M, N, K, e);
+    } else if (mode == 1) {
+        gemm_kernel<EPI, 1><<<grid, GEMM_THREADS, RES_SMEM, st>>>(ta, tb, M, N, K, e);
+    } else {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(GEMM_THREADS);
+        cfg.dynamicSmemBytes = RES_SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        ANN_CUDA(cudaLaunchKernelEx(&cfg, gemm_kernel<EPI, 2>, ta, tb, M, N, K, e));
+    }
     ANN_CUDA(cudaGetLastError());
     return ANN_OK;
 }
@@ -1378,7 +1502,7 @@ ann_status ann_mlp_predict(ann_mlp *m, const float *x, uint32_t n, uint32_t P, f
     ann_status s = ANN_OK;
     for (uint32_t r0 = 0; r0 < n && s == ANN_OK; r0 += m->maxb) {
         const uint32_t rows = std::min(m->maxb, n - r0);
-        const uint32_t ntiles = topp_slots(rows, m->out, (uint32_t)m->num_sms);
+        const uint32_t ntiles = topp_slots(rows, m->out, (uint32_t)m->num_sms, gemm_mode(EPI_TOPP, m->h2));
         const size_t need = (size_t)rows * ntiles * (2 * TOPP + 2) * 4;
         if (need > m->part_cap) {
             if (m->part) cudaFree(m->part);
