@@ -1184,6 +1184,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_predict_shapes(args):
+    """The learned entry's prediction alone (hidden layers, fused top-8
+    logits, merge) on 10,000 queries for workload 2's network (96 -> 512 ->
+    512 -> 10,000) and workload 4's (256 -> 512 -> 512 -> 50,000), random
+    initial weights, CUDA-event timed; one JSON line. Used to profile the
+    GEMM kernels (ncu on this command)."""
+    import torch
+    import paper_2507_17094_gb300 as A
+    from workloads import init_mlp_params
+    A.build()
+    out = {}
+    for d, n_out in ((96, 10_000), (256, 50_000)):
+        m = A.MLP(d, 512, 512, n_out, 16384)
+        m.set_params(*init_mlp_params(d, 512, 512, n_out, 1))
+        X = torch.randn(10_000, d, device="cuda", generator=torch.Generator("cuda").manual_seed(d))
+        for _ in range(args.warmup):
+            m.predict(X, P=8)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            m.predict(X, P=8)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        flop = 2.0 * 10_000 * (d * 512 + 512 * 512 + 512 * n_out)
+        out[f"{d}->512->512->{n_out}"] = {"ms": ms, "tflops": flop / ms / 1e9,
+                                          "frac_of_bf16_peak": flop / ms / 1e9 / measured_peaks()["bf16_tflops"]}
+        m.sync()
+        m.close()
+    print(json.dumps({"predict_shapes": out, "queries": 10_000, "steps": args.steps, "warmup": args.warmup}),
+          flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1202,11 +1236,15 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--workloads", default="3,4,5,wide,ppe,build",
                     help="legs beside the headline (rank 0, one GPU): 3, 4, 5, wide, ppe and build; empty for none")
+    ap.add_argument("--predict-shapes", action="store_true",
+                    help="time only the learned entry's prediction on two network shapes (GEMM profiling)")
     ap.add_argument("-v", "--verbose", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.predict_shapes:
+        run_predict_shapes(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
