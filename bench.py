@@ -333,8 +333,9 @@ def truth_knn(X: np.ndarray, Q: np.ndarray, k: int, dev, shortlist: int = 64):
     xn = (Xt * Xt).sum(1)
     ids = np.empty((len(Q), k), dtype=np.uint32)
     dists = np.empty((len(Q), k), dtype=np.float64)
-    for s0 in range(0, len(Q), 256):
-        q = torch.from_numpy(np.ascontiguousarray(Q[s0:s0 + 256])).to(dev, torch.float64)
+    step = int(max(16, min(256, 2_000_000_000 // max(1, Xt.shape[0]))))   # a chunk's FP64 matrix <= 16 GB
+    for s0 in range(0, len(Q), step):
+        q = torch.from_numpy(np.ascontiguousarray(Q[s0:s0 + step])).to(dev, torch.float64)
         d2 = xn[None, :] - 2.0 * (q @ Xt.T) + (q * q).sum(1)[:, None]
         cand = torch.topk(d2, min(shortlist, Xt.shape[0]), dim=1, largest=False).indices.cpu().numpy()
         for i in range(cand.shape[0]):
@@ -629,9 +630,25 @@ def leg_workload5(A, args, timer, verbose):
             print(f"[bench] serving {mix}: server {burst['qps'] / 1e6:.3f}M/s, per request {per_req_qps / 1e6:.3f}M/s, "
                   f"half load p50 {half['p50_ms']:.2f} ms p99 {half['p99_ms']:.2f} ms", file=sys.stderr, flush=True)
     srv.close()
+    # recall and the FP16 distance error against FP64 on a 1,000-query sample,
+    # at the mix's smaller setting (k 10, itopk 64), stored and reranked
+    ns = min(args.gt_sample, len(ds.Q))
+    gt = truth_knn(ds.X, ds.Q[:ns], 10, timer.dev)
+    qd = torch.from_numpy(np.ascontiguousarray(ds.Q[:ns])).to(timer.dev)
+    quality = {}
+    for tag, rr in (("stored", 0), ("reranked", 1)):
+        ids_e, d_e, _ = ix.search(qd, **dict(base, k=10, itopk=64, max_iters=80, rerank=rr))
+        torch.cuda.synchronize(timer.dev)
+        ie = ids_e.cpu().numpy().view(np.uint32)
+        de = d_e.cpu().numpy().astype(np.float64)
+        ok = ie != 0xFFFFFFFF
+        ex = pair_dist(ds.X, ds.Q[:ns], np.where(ok, ie, 0).astype(np.uint32))
+        rel = np.abs(de - ex)[ok] / np.maximum(ex[ok], 1e-30)
+        quality[tag] = {"recall_at_10": recall_at(ie, gt[1], ds.X, ds.Q[:ns], 10),
+                        "max_rel_distance_error": float(rel.max()), "mean_rel_distance_error": float(rel.mean())}
     ix.close()
     return {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "storage": "f16",
-            "entry": "ghost", "mixes": out,
+            "entry": "ghost", "mixes": out, "quality_k10_itopk64": quality,
             "mix": "k {10,100}, itopk {64,256} raised to k, Poisson arrivals; batch sizes per mix",
             "leg_s": time.time() - t0}
 
