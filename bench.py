@@ -407,13 +407,14 @@ class Timer:
         return statistics.median(a.elapsed_time(b) for a, b in ts)
 
 
-def sweep_forms(A, ds, spec, forms, timer, gt, verbose, tag, entries=None):
+def sweep_forms(A, ds, spec, forms, timer, gt, verbose, tag, entries=None, subsets=None):
     """Each form: storage, fixed params, an itopk sweep and k. The smallest
     itopk reaching recall@10 >= 0.95 on the ground-truth sample is the
     form's operating point (else the best recall seen); there the line gets
     QPS (all queries), the counted HBM bytes and their fraction, the mean
     rows and, for low-precision storage, the distance error against FP64
-    before and after the FP32 rerank."""
+    before and after the FP32 rerank. `subsets` (name -> boolean mask over
+    the ground-truth sample) adds each sweep row's recall on those queries."""
     import torch
     dev, stream = timer.dev, timer.stream
     Qd = torch.from_numpy(ds.Q).to(dev)
@@ -449,6 +450,8 @@ def sweep_forms(A, ds, spec, forms, timer, gt, verbose, tag, entries=None):
             a = ids[:ns].cpu().numpy().view(np.uint32)
             rec = recall_at(a, gt_d, ds.X, ds.Q[:ns], 10)
             row = {"itopk": L, "recall": rec}
+            for sname, m in (subsets or {}).items():
+                row.setdefault("recall_by_subset", {})[sname] = recall_at(a[m], gt_d[m], ds.X, ds.Q[:ns][m], 10)
             if f["k"] >= 100 and gt_ids.shape[1] >= 100:
                 row["recall_at_100"] = recall_at(a, gt_d, ds.X, ds.Q[:ns], 100)
             ms = timer(lambda: run(p))
@@ -529,8 +532,10 @@ def leg_workload3(A, args, timer, verbose):
 def leg_workload4(A, args, timer, verbose):
     """Workload 4 (5M x 256, Zipf cluster sizes, ghost set 50,000): plain
     ghost staging against the learned entry (MLP 256 -> 512 -> 512 ->
-    50,000 trained on the GPU), FP32 and FP16 / E4M3 with rerank."""
-    from workloads import WORKLOADS, load_dataset
+    50,000 trained on the GPU), FP32 and FP16 / E4M3 with rerank. Recall is
+    also split into the in-distribution queries and the 20% drawn between
+    clusters."""
+    from workloads import WORKLOADS, load_dataset, off_distribution_mask
     spec = WORKLOADS[4]
     t0 = time.time()
     ds = load_dataset(spec, off_fraction=0.2, device=timer.dev, verbose=verbose)
@@ -551,7 +556,9 @@ def leg_workload4(A, args, timer, verbose):
         "f16_learned": dict(storage=1, k=10, sweep=sw, params=dict(learned, rerank=1)),
         "e4m3_learned": dict(storage=2, k=10, sweep=sw, params=dict(learned, rerank=1)),
     }
-    res = sweep_forms(A, ds, spec, forms, timer, gt, verbose, "w4", entries)
+    off = off_distribution_mask(spec, 0.2)[:gt[0].shape[0]]
+    res = sweep_forms(A, ds, spec, forms, timer, gt, verbose, "w4", entries,
+                      subsets={"in_distribution": ~off, "off_distribution": off})
     le.close()
     return {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "nq": spec.nq,
             "off_distribution_fraction": 0.2, "gt_sample": int(gt[0].shape[0]), "learned_entry": info,

@@ -62,6 +62,11 @@ constexpr uint32_t kUnexpanded = 0, kPartial = 1, kExpanded = 2;
 constexpr uint64_t kGhostTag = 0x67686F7374ull;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kMaxDegWords = ANN_MAX_DEGREE / 32;
+// Resident 4-warp blocks per SM the register allocation is sized for.
+#ifndef ANN_SEARCH_BLOCKS_PER_SM
+#define ANN_SEARCH_BLOCKS_PER_SM 6
+#endif
+constexpr int kSearchBlocksPerSm = ANN_SEARCH_BLOCKS_PER_SM;
 
 // Entries that run the ghost stage first.
 __host__ __device__ __forceinline__ bool ghost_entry(uint32_t e)
@@ -931,7 +936,7 @@ struct WarpSearch {
 };
 
 template <int ST, bool PROF = false, int LPR = 2>
-__global__ void __launch_bounds__(128, 6) search_kernel(const Args a)
+__global__ void __launch_bounds__(128, kSearchBlocksPerSm) search_kernel(const Args a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -961,7 +966,7 @@ __global__ void __launch_bounds__(128, 6) search_kernel(const Args a)
 // warp that finishes a request's last query raises its completion flag in
 // host-mapped memory after a system-scope fence.
 template <int ST, int LPR = 2>
-__global__ void __launch_bounds__(128, 6) serve_kernel(const Args a, const ServeRing r)
+__global__ void __launch_bounds__(128, kSearchBlocksPerSm) serve_kernel(const Args a, const ServeRing r)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -34,3 +34,18 @@ def test_ghost_sample():
     s = ghost_sample(1000, 37, 5)
     assert len(set(s.tolist())) == 37 and np.all(np.diff(s.astype(np.int64)) > 0)
     assert np.array_equal(s, ghost_sample(1000, 37, 5))
+
+
+def test_off_distribution_queries_are_mixed_in():
+    """Workload 4's off-distribution queries sit at seeded random positions:
+    a prefix (a ground-truth sample) holds both kinds in proportion, and the
+    mask names exactly the queries far from every cluster center."""
+    from workloads import off_distribution_mask
+    s = WORKLOADS[4].scaled(5000, nq=2000, n_clusters=40)
+    q = make_queries(s, off_fraction=0.2)
+    m = off_distribution_mask(s, 0.2)
+    assert q.shape == (2000, 256) and m.sum() == 400
+    assert 0.1 < m[:500].mean() < 0.3
+    c = s.mixture().centers
+    d = ((q[:, None, :].astype(np.float64) - c[None]) ** 2).sum(-1).min(1)
+    assert d[m].min() > d[~m].max()

@@ -39,7 +39,7 @@ class Dataset:
 
 
 def _key(spec: WorkloadSpec, off_fraction: float) -> str:
-    blob = json.dumps({"spec": asdict(spec), "off": off_fraction, "v": 4}, sort_keys=True, default=str)
+    blob = json.dumps({"spec": asdict(spec), "off": off_fraction, "v": 5}, sort_keys=True, default=str)
     return f"{spec.name}-{hashlib.sha256(blob.encode()).hexdigest()[:16]}"
 
 

@@ -189,7 +189,9 @@ WORKLOADS = {
 def make_queries(spec: WorkloadSpec, nq: Optional[int] = None, seed: Optional[int] = None,
                  off_fraction: float = 0.0) -> np.ndarray:
     """Queries from the workload's mixture; a fraction may be drawn between
-    clusters (off-distribution)."""
+    clusters (off-distribution), placed at seeded random positions among the
+    others so that any prefix of the queries (a ground-truth sample) holds
+    both kinds in proportion."""
     nq = spec.nq if nq is None else nq
     seed = spec.seeds["query"] if seed is None else seed
     mix = spec.mixture()
@@ -197,7 +199,22 @@ def make_queries(spec: WorkloadSpec, nq: Optional[int] = None, seed: Optional[in
     q, _ = mix.sample(nq - n_off, seed)
     if n_off:
         q = np.concatenate([q, mix.sample_between(n_off, seed + 7)], axis=0)
+        q = q[np.random.Generator(np.random.PCG64(seed + 11)).permutation(nq)]
     return np.ascontiguousarray(q, dtype=np.float32)
+
+
+def off_distribution_mask(spec: WorkloadSpec, off_fraction: float, nq: Optional[int] = None,
+                          seed: Optional[int] = None) -> np.ndarray:
+    """Which of make_queries(spec, nq, seed, off_fraction)'s queries were drawn
+    between clusters (bool, nq)."""
+    nq = spec.nq if nq is None else nq
+    seed = spec.seeds["query"] if seed is None else seed
+    n_off = int(round(off_fraction * nq))
+    off = np.zeros(nq, dtype=bool)
+    if n_off:
+        off[nq - n_off:] = True
+        off = off[np.random.Generator(np.random.PCG64(seed + 11)).permutation(nq)]
+    return off
 
 
 def init_mlp_params(in_dim: int, hidden1: int, hidden2: int, out_dim: int, seed: int):
