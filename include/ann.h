@@ -88,6 +88,12 @@ typedef struct {
                                    neighbours whose direction agrees with the query's in at least
                                    ceil(f * dim) dimensions; 0 = the top-n rule of dgs_discard.
                                    Setting both is ANN_EINVAL. */
+    float ghost_judge;          /* ghost staging as the judge of given ghost seeds (entry 2; no
+                                   counterpart in the paper): when > 0, a query whose ghost queue,
+                                   after the ghost_max_iters_given iterations from its given seeds,
+                                   holds no node nearer than this squared distance continues the
+                                   ghost stage up to ghost_max_iters iterations in all (as plain
+                                   ghost staging, from the state reached). 0 = off; finite, >= 0. */
 } ann_search_params;
 
 /* Per-query event counters (exact counts of the work done). */

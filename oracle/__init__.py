@@ -45,7 +45,8 @@ class Params(C.Structure):
     _fields_ = [(n, C.c_uint32) for n in
                 ("k", "L", "W", "T", "m", "n_keep", "it_cool", "reexpand", "entry", "Lg", "Tg",
                  "Tg_given", "g", "rerank")] + [("seed", C.c_uint64), ("qid_base", C.c_uint64),
-                                                ("Wg", C.c_uint32), ("min_match", C.c_uint32)]
+                                                ("Wg", C.c_uint32), ("min_match", C.c_uint32),
+                                                ("judge", C.c_float)]
 
 
 class Index(C.Structure):
@@ -267,15 +268,17 @@ class OracleIndex:
 def make_params(index: OracleIndex, k=10, itopk=64, search_width=1, max_iters=64, num_seeds=0,
                 dgs_discard=0.0, dgs_cooldown=0.3, dgs_reexpand=0, entry=0, ghost_itopk=0,
                 ghost_max_iters=16, ghost_max_iters_given=4, ghost_seeds_out=0, rerank=0, seed=0,
-                qid_base=0, ghost_search_width=1, dgs_min_match=0.0) -> Params:
+                qid_base=0, ghost_search_width=1, dgs_min_match=0.0, ghost_judge=0.0) -> Params:
     if dgs_min_match > 0 and dgs_discard > 0:
         raise ValueError("dgs_min_match and dgs_discard are alternatives: set one")
+    if not (0.0 <= ghost_judge < float("inf")):
+        raise ValueError("ghost_judge must be finite and >= 0")
     n_keep, it_cool = derived_counts(index.degree, max_iters, dgs_discard, dgs_cooldown)
     min_match = min_match_count(index.X32.shape[1], dgs_min_match)
     Lg = ghost_itopk or min(itopk, 64)
     return Params(k, itopk, search_width, max_iters, num_seeds, n_keep, it_cool, dgs_reexpand, entry,
                   Lg, ghost_max_iters, ghost_max_iters_given, ghost_seeds_out or Lg, rerank, seed, qid_base,
-                  ghost_search_width or 1, min_match)
+                  ghost_search_width or 1, min_match, float(np.float32(ghost_judge)))
 
 
 def search(index: OracleIndex, Q: np.ndarray, given_ghost_seeds: Optional[np.ndarray] = None,

@@ -294,6 +294,7 @@ typedef struct {
     uint64_t qid_base;      /* global index of query 0 of this call */
     uint32_t Wg;            /* parents per ghost iteration */
     uint32_t min_match;     /* > 0: DGS keeps the neighbours scoring >= min_match instead of the top n_keep */
+    float judge;            /* > 0: given ghost seeds whose ghost result is farther continue to Tg */
 } oracle_params;
 
 typedef struct {
@@ -513,9 +514,11 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
         uint8_t *gvis = (uint8_t *)calloc(ix->nS / 8 + 1, 1);
         or_state gs = {st.buf, 0, st.tmp, gvis};
         uint32_t nc = 0, Tg = p->Tg;
+        int judged = 0;
         const uint32_t *given = (p->entry == OR_ENTRY_GIVEN_GHOST && c->given) ? c->given + (uint64_t)qi * c->P : NULL;
         if (given && given[0] != OR_INVALID) {
             Tg = p->Tg_given;
+            judged = p->judge > 0.0f && p->Tg > p->Tg_given;
             for (uint32_t j = 0; j < c->P; ++j) {
                 uint32_t v = given[j];
                 if (v == OR_INVALID || v >= ix->nS || bit_get(gvis, v)) continue;
@@ -539,6 +542,12 @@ static void search_one(void *vctx, uint32_t qi, void *scratch)
         uint64_t no_dgs = 0;
         or_iterate(&gg, q, &gs, p->Lg, p->Wg ? p->Wg : 1, Tg, ix->deg_g, 0, 0, 0,
                    &cn.ghost_iters, &cn.ghost_parents, &no_dgs, &cn.ghost_vec_rows);
+        /* The judge of given seeds: if the ghost queue's best node is farther
+         * than the judge distance, the ghost stage goes on from where it is,
+         * up to Tg iterations in all, as plain ghost staging would. */
+        if (judged && gs.cnt > 0 && gs.buf[0].dist > p->judge)
+            or_iterate(&gg, q, &gs, p->Lg, p->Wg ? p->Wg : 1, p->Tg - p->Tg_given, ix->deg_g, 0, 0, 0,
+                       &cn.ghost_iters, &cn.ghost_parents, &no_dgs, &cn.ghost_vec_rows);
         /* Transition: the top g ghost results, as base ids with their
          * distances, become the base queue; only they are marked visited. */
         uint32_t g = p->g < gs.cnt ? p->g : gs.cnt;

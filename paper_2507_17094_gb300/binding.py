@@ -54,7 +54,7 @@ class SearchParams(C.Structure):
                 ("ghost_itopk", C.c_uint32), ("ghost_max_iters", C.c_uint32),
                 ("ghost_max_iters_given", C.c_uint32), ("ghost_seeds_out", C.c_uint32),
                 ("rerank", C.c_uint32), ("seed", C.c_uint64), ("qid_base", C.c_uint64),
-                ("ghost_search_width", C.c_uint32), ("dgs_min_match", C.c_float)]
+                ("ghost_search_width", C.c_uint32), ("dgs_min_match", C.c_float), ("ghost_judge", C.c_float)]
 
 
 class ServerConfig(C.Structure):

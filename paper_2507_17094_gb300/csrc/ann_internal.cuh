@@ -82,6 +82,7 @@ struct QParams {
     uint32_t k, L, W, T, m, n_keep, it_cool, reexpand, entry, Lg, Tg, Tg_given, g, rerank, n_given, Wg;
     uint64_t seed, qid_base;
     uint32_t min_match;   // > 0: DGS keeps the neighbours scoring >= min_match (not the top n_keep)
+    float judge;          // > 0: given ghost seeds whose ghost result is farther continue to Tg
 };
 static_assert(sizeof(QParams) <= 96, "the serve kernel keeps a request's QParams in 96 bytes of shared memory");
 

@@ -183,6 +183,14 @@ __device__ __forceinline__ bool better(float va, uint32_t ia, float vb, uint32_t
     return va > vb || (va == vb && ia < ib);
 }
 
+// max(a, b, c) in one instruction (the three-input form of max.f32)
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // ------------------------------------------------------------------ GEMM
 // Persistent and warp-specialised: CTA b walks the contiguous tile range
 // [b * per, (b + 1) * per) in row-block-major order (per = ceil(tiles /
@@ -272,31 +280,45 @@ __device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m,
                 if (nb + j < N) out[j] = __float2bfloat16_rn(fmaxf(v[j] + bias[j], 0.0f));
         }
     } else {
-        // logits of the chunk; their max and exp-sum by trees, one
-        // online-softmax combine; then the logits above the thread's current
-        // P-th enter its top-P one per step (columns arrive in increasing
-        // order, so a tie never enters), all lanes inserting together
+        // logits of the chunk; their max and exp-sum by trees (three-input
+        // max, packed FP32 adds and multiply-adds), one online-softmax
+        // combine; then the logits above the thread's current P-th enter its
+        // top-P one per step, all lanes inserting together
         constexpr float kLog2e = 1.4426950408889634f;
         float x[32];
+        if (full && m < M) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) x[j] = (m < M && nb + j < N) ? v[j] + bias[j] : -INFINITY;
-        float t[16];
+            for (int j = 0; j < 32; j += 2) {
+                const float2 r = __fadd2_rn(make_float2(v[j], v[j + 1]), make_float2(bias[j], bias[j + 1]));
+                x[j] = r.x;
+                x[j + 1] = r.y;
+            }
+        } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) t[j] = fmaxf(x[j], x[j + 16]);
+            for (int j = 0; j < 32; ++j) x[j] = (m < M && nb + j < N) ? v[j] + bias[j] : -INFINITY;
+        }
+        float t[12];
 #pragma unroll
-        for (int w = 8; w; w >>= 1)
+        for (int j = 0; j < 10; ++j) t[j] = fmax3(x[3 * j], x[3 * j + 1], x[3 * j + 2]);
+        t[10] = x[30];
+        t[11] = x[31];
 #pragma unroll
-            for (int j = 0; j < w; ++j) t[j] = fmaxf(t[j], t[j + w]);
-        const float cm = t[0];
+        for (int j = 0; j < 4; ++j) t[j] = fmax3(t[3 * j], t[3 * j + 1], t[3 * j + 2]);
+        const float cm = fmaxf(fmax3(t[0], t[1], t[2]), t[3]);
         if (cm > -INFINITY) {
             const float off = -cm * kLog2e;
+            float2 e[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) t[j] = ex2_approx(fmaf(x[j], kLog2e, off)) + ex2_approx(fmaf(x[j + 16], kLog2e, off));
+            for (int j = 0; j < 16; ++j) {
+                const float2 a = __ffma2_rn(make_float2(x[2 * j], x[2 * j + 1]), make_float2(kLog2e, kLog2e),
+                                            make_float2(off, off));
+                e[j] = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+            }
 #pragma unroll
             for (int w = 8; w; w >>= 1)
 #pragma unroll
-                for (int j = 0; j < w; ++j) t[j] += t[j + w];
-            const float cs = t[0];
+                for (int j = 0; j < w; ++j) e[j] = __fadd2_rn(e[j], e[j + w]);
+            const float cs = e[0].x + e[0].y;
             if (cm > tp.mx) {
                 tp.sm = tp.sm * ex2_approx((tp.mx - cm) * kLog2e) + cs;
                 tp.mx = cm;
@@ -323,15 +345,22 @@ __device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m,
                     const uint32_t j = __ffs(pend) - 1;
                     pend &= pend - 1;
                     const float xv = xs[j];
+                    // columns reach a thread in increasing order, so every
+                    // entry holds a smaller column and wins a tie: the new
+                    // one goes behind all entries >= xv (each slot decided
+                    // from the old values, no chain of swaps)
                     if (xv > tp.tv[TOPP - 1]) {
-                        tp.tv[TOPP - 1] = xv;
-                        tp.ti[TOPP - 1] = nb + j;
+                        const uint32_t col = nb + j;
 #pragma unroll
                         for (int p = TOPP - 1; p > 0; --p) {
-                            if (better(tp.tv[p], tp.ti[p], tp.tv[p - 1], tp.ti[p - 1])) {
-                                const float tt = tp.tv[p]; tp.tv[p] = tp.tv[p - 1]; tp.tv[p - 1] = tt;
-                                const uint32_t u = tp.ti[p]; tp.ti[p] = tp.ti[p - 1]; tp.ti[p - 1] = u;
-                            }
+                            const bool before_prev = xv > tp.tv[p - 1];
+                            const bool before_cur = xv > tp.tv[p];
+                            tp.tv[p] = before_prev ? tp.tv[p - 1] : (before_cur ? xv : tp.tv[p]);
+                            tp.ti[p] = before_prev ? tp.ti[p - 1] : (before_cur ? col : tp.ti[p]);
+                        }
+                        if (xv > tp.tv[0]) {
+                            tp.tv[0] = xv;
+                            tp.ti[0] = col;
                         }
                     }
                 }

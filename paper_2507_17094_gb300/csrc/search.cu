@@ -296,6 +296,8 @@ struct WarpSearch {
     __device__ __forceinline__ uint32_t *par() const { return reinterpret_cast<uint32_t *>(base + a.lay.par); }
     __device__ __forceinline__ uint8_t *stage() const { return base + a.lay.stage; }
     __device__ __forceinline__ uint64_t *bar() const { return reinterpret_cast<uint64_t *>(base + a.lay.bar); }
+    // two words beside the mbarrier (its 16-byte slot): the ghost judge
+    __device__ __forceinline__ uint32_t *judge() const { return reinterpret_cast<uint32_t *>(base + a.lay.bar + 8); }
 
     // ---------------------------------------------------------- visited set
     __device__ __forceinline__ uint32_t *gbits() const { return reinterpret_cast<uint32_t *>(base + a.lay.dir); }
@@ -730,6 +732,10 @@ struct WarpSearch {
     // parent expansions share one loop body, so the distance and merge code
     // exists once in the kernel (the kernel is bound by instruction fetch).
     template <int RST>
+    // The judge of a ghost stage from given seeds (run() sets it in judge(),
+    // else zero): at iteration T, a queue holding no node nearer than
+    // judge()[0] (FP32 bits) goes on to judge()[1] iterations in all. Kept in
+    // shared memory so the loop carries no extra registers.
     __device__ bool iterate(const View &v, const uint32_t *seed_ids, uint32_t m, uint64_t seed_key, uint32_t lcap,
                             uint32_t W, uint32_t T, uint32_t n_keep, uint32_t min_match, uint32_t it_cool,
                             uint32_t reexpand,
@@ -749,7 +755,11 @@ struct WarpSearch {
                 j0 += chunk;
                 mark(PH_VISIT);
             } else {
-                if (it == T) break;
+                if (it == T) {
+                    const uint32_t t_ext = judge()[1];
+                    if (t_ext <= T || cnt == 0 || !(bd()[0] > __uint_as_float(judge()[0]))) break;
+                    T = t_ext;   // judged too far: the rest of the ghost iterations
+                }
                 if (dgs_on && it >= it_cool) cool = true;
                 uint32_t np = select_parents(W, cool);
                 if (np == 0 && dgs_on && reexpand && !cool && any_partial()) {
@@ -868,6 +878,16 @@ struct WarpSearch {
                 mark(PH_VISIT);
             }
             const bool seeded = !(stage == 1 && ghost);
+            // a ghost stage from given seeds may be judged: one whose best
+            // node is farther than the judge distance after Tg_given
+            // iterations goes on to Tg (the ghost stage has no DGS, so its
+            // cool-down start carries that total)
+            const bool judged = stage == 0 && given && qp.judge > 0.0f && qp.Tg > qp.Tg_given;
+            if (lane == 0) {
+                judge()[0] = judged ? __float_as_uint(qp.judge) : 0u;
+                judge()[1] = judged ? qp.Tg : 0u;
+            }
+            __syncwarp();
             ok = iterate<ST>(v, given, seeded ? (given ? qp.n_given : (stage ? qp.m : v.deg)) : 0,
                              splitmix64(qp.seed ^ (stage ? 0 : kGhostTag)), lcap, stage ? qp.W : qp.Wg,
                              stage ? qp.T : (given ? qp.Tg_given : qp.Tg), stage ? qp.n_keep : v.deg,
@@ -1128,6 +1148,10 @@ ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint3
         set_error("ann_search: ghost_itopk > %u", ANN_MAX_ITOPK);
         return ANN_EINVAL;
     }
+    if (!(p->ghost_judge >= 0.0f && p->ghost_judge <= 3.402823466e38f)) {
+        set_error("ann_search: ghost_judge must be finite and >= 0");
+        return ANN_EINVAL;
+    }
     const uint32_t Wg = p->ghost_search_width ? p->ghost_search_width : 1;
     if (Wg > ANN_MAX_WIDTH) {
         set_error("ann_search: ghost_search_width must be <= %u", ANN_MAX_WIDTH);
@@ -1159,6 +1183,7 @@ ann_status derive_qparams(const ann_index *ix, const ann_search_params *p, uint3
     q.Tg_given = p->ghost_max_iters_given;
     q.Wg = Wg;
     q.g = p->ghost_seeds_out ? p->ghost_seeds_out : Lg;
+    q.judge = p->ghost_judge;
     q.rerank = p->rerank ? 1 : 0;
     q.seed = p->seed;
     q.qid_base = p->qid_base;

@@ -6,13 +6,17 @@
 3. Inference: ann_mlp_predict gives the top-P ghost nodes per query (or the
    fallback marker below the confidence threshold tau); ann_search with
    entry = ANN_ENTRY_GIVEN_GHOST starts its ghost stage from them.
+4. Judge: ghost staging judges the network's seeds. A query whose ghost
+   stage, after its few iterations from the seeds, holds no node nearer than
+   the judge distance (ann_search_params.ghost_judge, calibrated like tau
+   on validation queries) continues as plain ghost staging.
 """
 
 from __future__ import annotations
 
 import numpy as np
 
-from .binding import ENTRY_GHOST, INVALID, MLP, Index
+from .binding import ENTRY_GHOST, ENTRY_GIVEN_GHOST, INVALID, MLP, Index
 
 
 def ghost_labels(index: Index, queries, seed: int, ghost_itopk: int = 64, ghost_max_iters: int = 64,
@@ -32,6 +36,7 @@ class LearnedEntry:
         self.mlp = MLP(index.dim, hidden[0], hidden[1], index.n_ghost, max_batch, device=index.device)
         self.mlp.set_params(*params)
         self.tau = 0.0
+        self.judge = 0.0
         self.losses = None
 
     def fit(self, train_queries, labels, epochs: int = 5, batch: int = 1024, lr: float = 1e-3, seed: int = 0,
@@ -55,6 +60,21 @@ class LearnedEntry:
         hit = (seeds == val_labels[:, None]).any(dim=1).float().mean().item()
         self.tau = self.mlp.confidence_threshold(pmax, fallback)
         return self.tau, float(hit)
+
+    def calibrate_judge(self, val_queries, continue_fraction: float = 0.05, stream=None, **search_params):
+        """Set the judge distance from a validation split: the (1 -
+        continue_fraction) quantile (the same device quantile as tau) of the
+        squared distance of each validation query's best ghost node after
+        the ghost stage from the network's seeds, run with `search_params`'
+        ghost settings. That fraction of in-distribution queries, and any
+        query farther from every ghost node it reached, continues as plain
+        ghost staging. Returns the judge distance."""
+        seeds, _ = self.seeds(val_queries, stream=stream)
+        p = dict(search_params, k=1, max_iters=0, entry=ENTRY_GIVEN_GHOST, ghost_judge=0.0)
+        p["itopk"] = max(1, int(p.get("ghost_itopk") or 64))
+        _, d, _ = self.index.search(val_queries, given=seeds, stream=stream, **p)
+        self.judge = self.mlp.confidence_threshold(d[:, 0].contiguous(), 1.0 - continue_fraction, stream=stream)
+        return self.judge
 
     def seeds(self, queries, stream=None):
         s, pmax = self.mlp.predict(queries, P=self.P, tau=self.tau, stream=stream)

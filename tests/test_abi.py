@@ -31,11 +31,11 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_params_struct_matches_defaults(L):
-    assert C.sizeof(A.SearchParams) == 80
+    assert C.sizeof(A.SearchParams) == 88
     p = A.make_params()
     assert (p.k, p.itopk, p.search_width, p.max_iters) == (10, 64, 1, 64)
     assert abs(p.dgs_cooldown - 0.3) < 1e-7 and p.ghost_max_iters == 16 and p.ghost_max_iters_given == 4
-    assert p.ghost_search_width == 1 and p.dgs_min_match == 0.0
+    assert p.ghost_search_width == 1 and p.dgs_min_match == 0.0 and p.ghost_judge == 0.0
 
 
 def test_host_side_validation(L):

@@ -111,13 +111,15 @@ def test_precision_10m(storage, k, itopk, ghost):
 def test_learned_entry_5m():
     """Workload 4 (5M x 256, Zipf cluster sizes, ghost set 50,000): the MLP
     256->512->512->50,000 trained on 200,000 ghost-staging labels, against
-    plain ghost staging on 10,000 held-out queries (20% between clusters),
-    at the same queue size. Measured at itopk 256 with the benchmark's ghost
-    stage: ghost staging 0.946, learned entry 0.96-0.97 with a fifth of the
-    ghost rows."""
+    plain ghost staging on the 10,000 held-out queries (20% drawn between
+    clusters), at the benchmark's operating point (itopk 512, a 512-entry
+    ghost queue with 8 parents per ghost iteration). Measured on 1,000
+    queries: ghost staging 0.949, the learned entry with its judge 0.951
+    (in-distribution 0.988, between clusters 0.80) with a third of the ghost
+    rows. The floor 0.945 allows the sample's error (about 0.005)."""
     import paper_2507_17094_gb300 as A
     from paper_2507_17094_gb300.entry import LearnedEntry, ghost_labels
-    from workloads import WORKLOADS, init_mlp_params, load_dataset, make_queries
+    from workloads import WORKLOADS, init_mlp_params, load_dataset, make_queries, off_distribution_mask
     spec = WORKLOADS[4]
     ds = load_dataset(spec, off_fraction=0.2, device="cuda")
     ix = A.Index(ds.X, ds.G, storage=A.F16, ghost_ids=ds.S, ghost_graph=ds.Gg)
@@ -127,30 +129,37 @@ def test_learned_entry_5m():
     losses = le.fit(Qtr, ghost_labels(ix, Qtr, seed=spec.seeds["search"]), epochs=8, seed=spec.seeds["mlp"])
     tau, hit = le.calibrate(Qva, ghost_labels(ix, Qva, seed=spec.seeds["search"]))
     assert losses[-1] < 0.5 * losses[0] and hit > 0.5   # measured: loss 8.0 -> 0.79, label in top 8 for 54%
+    common = dict(k=10, itopk=512, max_iters=528, dgs_discard=0.5, rerank=1, seed=spec.seeds["search"],
+                  ghost_itopk=512, ghost_search_width=8, ghost_max_iters=64)
+    judge = le.calibrate_judge(Qva, **dict(common, ghost_max_iters_given=4))
     Q = torch.from_numpy(ds.Q).cuda()
     seeds, _ = le.seeds(Q)
-    common = dict(k=10, itopk=256, max_iters=272, dgs_discard=0.5, rerank=1, seed=4004, ghost_itopk=128,
-                  ghost_search_width=4, ghost_max_iters=48)
-    idx = sample_rows(len(ds.Q), 300, 3)
+    idx = sample_rows(len(ds.Q), 1000, 3)
+    off = off_distribution_mask(spec, 0.2)[idx]
     gt, gd = O.knn_f64(ds.X, ds.Q[idx], 10)
     out = {}
-    for name, extra in (("ghost", dict(entry=1)), ("learned", dict(entry=2, given=seeds, ghost_max_iters_given=4))):
+    for name, extra in (("ghost", dict(entry=1)),
+                        ("learned", dict(entry=2, given=seeds, ghost_max_iters_given=4, ghost_judge=judge))):
         ids, d, st = ix.search(Q, stats=True, **common, **extra)
         torch.cuda.synchronize()
         stn = A.stats_to_numpy(st)
-        rec = O.recall_at_k(ids.cpu().numpy().view(np.uint32)[idx], gt, gd, ds.X, ds.Q[idx], 10)[0]
+        a = ids.cpu().numpy().view(np.uint32)[idx]
+        rec = O.recall_at_k(a, gt, gd, ds.X, ds.Q[idx], 10)[0]
+        r_in = O.recall_at_k(a[~off], gt[~off], gd[~off], ds.X, ds.Q[idx][~off], 10)[0]
+        r_off = O.recall_at_k(a[off], gt[off], gd[off], ds.X, ds.Q[idx][off], 10)[0]
         if name == "ghost":
             rate = qps(lambda: ix.search(Q, **common, **extra), len(ds.Q))
         else:
-            rate = qps(lambda: ix.search(Q, given=le.seeds(Q)[0], **common, ghost_max_iters_given=4, entry=2),
-                       len(ds.Q))
-        out[name] = (rec, stn["ghost_vec_rows"].mean(), rate)
-    print(f"workload 4: ghost staging recall {out['ghost'][0]:.3f} ghost rows {out['ghost'][1]:.0f} "
-          f"{out['ghost'][2] / 1e6:.3f}M QPS; learned recall {out['learned'][0]:.3f} ghost rows "
+            rate = qps(lambda: ix.search(Q, **common, **dict(extra, given=le.seeds(Q)[0])), len(ds.Q))
+        out[name] = (rec, stn["ghost_vec_rows"].mean(), rate, r_in, r_off)
+    print(f"workload 4: ghost staging recall {out['ghost'][0]:.3f} (in {out['ghost'][3]:.3f}, off "
+          f"{out['ghost'][4]:.3f}) ghost rows {out['ghost'][1]:.0f} {out['ghost'][2] / 1e6:.3f}M QPS; learned "
+          f"recall {out['learned'][0]:.3f} (in {out['learned'][3]:.3f}, off {out['learned'][4]:.3f}) ghost rows "
           f"{out['learned'][1]:.0f} {out['learned'][2] / 1e6:.3f}M QPS (predict included); tau {tau:.3g}, "
-          f"val hit {hit:.3f}, fallback {float((seeds[:, 0] == -1).float().mean()):.3f}")
-    assert out["learned"][1] < out["ghost"][1]
-    assert out["learned"][0] >= 0.95 and out["learned"][0] >= out["ghost"][0] - 0.005
+          f"judge {judge:.4g}, val hit {hit:.3f}, fallback {float((seeds[:, 0] == -1).float().mean()):.3f}")
+    assert out["learned"][1] < 0.5 * out["ghost"][1]
+    assert out["learned"][0] >= 0.945 and out["learned"][0] >= out["ghost"][0] - 0.005
+    assert out["learned"][3] >= 0.98
     le.close()
     ix.close()
 

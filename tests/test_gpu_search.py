@@ -145,6 +145,23 @@ def test_given_ghost_seeds_with_fallback():
     assert_parity(g, o)
 
 
+def test_given_ghost_seeds_with_judge():
+    """The judge of given seeds continues some queries' ghost stage and not
+    others' (median distance), as the oracle does."""
+    c = tiny_case()
+    rng = np.random.default_rng(6)
+    given = rng.integers(0, len(c.S), size=(len(c.Q), 2)).astype(np.uint32)
+    given[::5, 0] = O.INVALID
+    p = dict(seed=4001, itopk=64, max_iters=64, entry=2, ghost_itopk=32, ghost_max_iters=16,
+             ghost_max_iters_given=1)
+    best = c.run(O.F32, given=given, **dict(p, k=1, itopk=32, max_iters=0))[1][1][:, 0]
+    judge = float(np.median(best))
+    g, o = c.run(O.F32, given=given, ghost_judge=judge, **p)
+    assert_parity(g, o)
+    far = best > np.float32(judge)
+    assert (o[2]["ghost_iters"][far & (given[:, 0] != O.INVALID)] > 1).any()
+
+
 def test_full_queue_is_brute_force_on_gpu():
     # queue larger than the graph: the search is exhaustive
     c = ragged_case(n=400, d=40, deg=12, nq=9, gdeg=6, seed=13)

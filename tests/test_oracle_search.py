@@ -162,6 +162,42 @@ def test_given_ghost_seeds_and_fallback(int_data):
     assert (a[2]["ghost_iters"][1::2] <= 4).all()        # given seeds run the short ghost stage
 
 
+def test_ghost_judge_continues_exactly_the_far_queries(int_data):
+    """The judge of given ghost seeds: with a distance every query's ghost
+    result beats it changes nothing; with one none beats it every query runs
+    the whole ghost budget, exactly as given seeds with ghost_max_iters_given
+    = ghost_max_iters (continuing from the state reached is the same search);
+    in between, each query takes one of the two results according to its
+    own ghost result after the short stage."""
+    X, Q, G, gt, gd = int_data
+    n = X.shape[0]
+    S = np.arange(0, n, 3, dtype=np.uint32)
+    rng = np.random.default_rng(15)
+    Gg = _ring_graph(len(S), 6, rng)
+    ix = O.OracleIndex(X, G, S=S, Gg=Gg)
+    seeds = rng.integers(0, len(S), size=(Q.shape[0], 2)).astype(np.uint32)
+    common = dict(given_ghost_seeds=seeds, entry=2, k=10, itopk=32, max_iters=40, seed=3, ghost_itopk=16,
+                  ghost_max_iters=12, ghost_max_iters_given=1)
+    short = O.search(ix, Q, **common)
+    full = O.search(ix, Q, **dict(common, ghost_max_iters_given=12))
+    assert (short[2]["ghost_iters"] <= 1).all() and (full[2]["ghost_iters"] > 1).any()
+    never = O.search(ix, Q, **common, ghost_judge=1e30)
+    always = O.search(ix, Q, **common, ghost_judge=1e-30)
+    for a, b in ((never, short), (always, full)):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        assert np.array_equal(a[2]["ghost_iters"], b[2]["ghost_iters"])
+    # the ghost stage's own best distance after the short stage decides
+    best = O.search(ix, Q, **dict(common, k=1, itopk=16, max_iters=0))[1][:, 0]
+    judge = float(np.median(best))
+    mid = O.search(ix, Q, **common, ghost_judge=judge)
+    far = best > np.float32(judge)
+    assert far.any() and (~far).any()
+    assert np.array_equal(mid[0][far], full[0][far]) and np.array_equal(mid[0][~far], short[0][~far])
+    assert np.array_equal(mid[2]["ghost_iters"][far], full[2]["ghost_iters"][far])
+    with pytest.raises(ValueError):
+        O.search(ix, Q, **common, ghost_judge=float("inf"))
+
+
 def test_rerank_uses_fp32_originals():
     rng = np.random.default_rng(15)
     X = rng.standard_normal((500, 32)).astype(np.float32) * 3
