@@ -482,6 +482,12 @@ def sweep_forms(A, ds, spec, forms, timer, gt, verbose, tag, entries=None, subse
              "mean_iters": float(stn["iters"].mean()), "sweep": sweep}
         if "recall_at_100" in at:
             r["recall_at_100"] = at["recall_at_100"]
+        if p.get("entry") == 2:
+            # queries whose ghost stage ran past the seeds' short stage (fallback by tau, or the judge)
+            full = stn["ghost_iters"] > p.get("ghost_max_iters_given", 4)
+            r["full_ghost_stage_fraction"] = float(full.mean())
+            for sname, m in (subsets or {}).items():
+                r.setdefault("full_ghost_stage_by_subset", {})[sname] = float(full[:ns][m].mean())
         if f["storage"] != 0:
             errs = {}
             for tagr, rr in (("stored", 0), ("reranked", 1)):

@@ -113,9 +113,12 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// Two 32-column accumulator loads in flight together and one wait: the
+// second statement waits for both and names the first load's registers as
+// its operands, so no use of them can move above the wait.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr0, uint32_t taddr1, float (&v0)[32], float (&v1)[32])
 {
-    uint32_t r[32];
+    uint32_t r[32], s[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -123,10 +126,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr0));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]), "=r"(s[8]), "=r"(s[9]), "=r"(s[10]), "=r"(s[11]), "=r"(s[12]), "=r"(s[13]), "=r"(s[14]), "=r"(s[15]), "=r"(s[16]), "=r"(s[17]), "=r"(s[18]), "=r"(s[19]), "=r"(s[20]), "=r"(s[21]), "=r"(s[22]), "=r"(s[23]), "=r"(s[24]), "=r"(s[25]), "=r"(s[26]), "=r"(s[27]), "=r"(s[28]), "=r"(s[29]), "=r"(s[30]), "=r"(s[31]),
+          "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+        : "r"(taddr1)
+        : "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) {
+        v0[i] = __uint_as_float(r[i]);
+        v1[i] = __uint_as_float(s[i]);
+    }
 }
 
 // Cluster helpers (the multicast logits kernel runs in clusters of two CTAs).
@@ -218,26 +231,30 @@ struct TopP {
     }
 };
 
-// One 32-column chunk of a row (accumulator values v) for columns nb..nb+31.
-// Rows m >= M take part in the warp's collectives with no effect.
+// The bias of columns nb..nb+31 (0 past N; none for the plain FP32 store).
 template <int EPI>
-__device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m, uint32_t M, uint32_t nb, uint32_t N,
-                                               const EpiArgs &e, TopP &tp, float *xs)
+__device__ __forceinline__ void load_bias32(const EpiArgs &e, uint32_t nb, uint32_t N, float (&bias)[32])
+{
+    if (EPI == EPI_F32) return;
+    if (nb + 32 <= N) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+            const float4 b4 = __ldg(reinterpret_cast<const float4 *>(e.bias + nb + j));
+            bias[j] = b4.x; bias[j + 1] = b4.y; bias[j + 2] = b4.z; bias[j + 3] = b4.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) bias[j] = nb + j < N ? __ldg(e.bias + nb + j) : 0.0f;
+    }
+}
+
+// One 32-column chunk of a row (accumulator values v, the columns' bias) for
+// columns nb..nb+31, stored (the top-P epilogue is topp_pair).
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk(const float (&v)[32], const float (&bias)[32], uint32_t m, uint32_t M,
+                                               uint32_t nb, uint32_t N, const EpiArgs &e)
 {
     const bool full = nb + 32 <= N;
-    float bias[32];
-    if (EPI != EPI_F32) {
-        if (full) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-                const float4 b4 = __ldg(reinterpret_cast<const float4 *>(e.bias + nb + j));
-                bias[j] = b4.x; bias[j + 1] = b4.y; bias[j + 2] = b4.z; bias[j + 3] = b4.w;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) bias[j] = nb + j < N ? __ldg(e.bias + nb + j) : 0.0f;
-        }
-    }
     if (EPI == EPI_F32 || EPI == EPI_BIAS_F32) {
         if (m >= M) return;
         float *out = e.c + (size_t)m * e.ldc + nb;
@@ -279,94 +296,125 @@ __device__ __forceinline__ void epilogue_chunk(const float (&v)[32], uint32_t m,
             for (int j = 0; j < 32; ++j)
                 if (nb + j < N) out[j] = __float2bfloat16_rn(fmaxf(v[j] + bias[j], 0.0f));
         }
-    } else {
-        // logits of the chunk; their max and exp-sum by trees (three-input
-        // max, packed FP32 adds and multiply-adds), one online-softmax
-        // combine; then the logits above the thread's current P-th enter its
-        // top-P one per step, all lanes inserting together
-        constexpr float kLog2e = 1.4426950408889634f;
-        float x[32];
-        if (full && m < M) {
+    }
+}
+
+// The logits of a 32-column chunk above the thread's current P-th best
+// (bits of pend; their values parked in xs) enter its top-P one per step,
+// all lanes inserting together. Columns reach a thread in increasing order,
+// so every entry holds a smaller column and wins a tie: a new logit goes
+// behind all entries >= it, each slot decided from the old values (no chain
+// of swaps).
+__device__ __forceinline__ void topp_insert(TopP &tp, const float *xs, uint32_t pend, uint32_t nb)
+{
+    while (__any_sync(0xffffffffu, pend != 0)) {
+        if (pend) {
+            const uint32_t j = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const float xv = xs[j];
+            if (xv > tp.tv[TOPP - 1]) {
+                const uint32_t col = nb + j;
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-                const float2 r = __fadd2_rn(make_float2(v[j], v[j + 1]), make_float2(bias[j], bias[j + 1]));
-                x[j] = r.x;
-                x[j + 1] = r.y;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) x[j] = (m < M && nb + j < N) ? v[j] + bias[j] : -INFINITY;
-        }
-        float t[12];
-#pragma unroll
-        for (int j = 0; j < 10; ++j) t[j] = fmax3(x[3 * j], x[3 * j + 1], x[3 * j + 2]);
-        t[10] = x[30];
-        t[11] = x[31];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) t[j] = fmax3(t[3 * j], t[3 * j + 1], t[3 * j + 2]);
-        const float cm = fmaxf(fmax3(t[0], t[1], t[2]), t[3]);
-        if (cm > -INFINITY) {
-            const float off = -cm * kLog2e;
-            float2 e[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float2 a = __ffma2_rn(make_float2(x[2 * j], x[2 * j + 1]), make_float2(kLog2e, kLog2e),
-                                            make_float2(off, off));
-                e[j] = make_float2(ex2_approx(a.x), ex2_approx(a.y));
-            }
-#pragma unroll
-            for (int w = 8; w; w >>= 1)
-#pragma unroll
-                for (int j = 0; j < w; ++j) e[j] = __fadd2_rn(e[j], e[j + w]);
-            const float cs = e[0].x + e[0].y;
-            if (cm > tp.mx) {
-                tp.sm = tp.sm * ex2_approx((tp.mx - cm) * kLog2e) + cs;
-                tp.mx = cm;
-            } else {
-                tp.sm += cs * ex2_approx((cm - tp.mx) * kLog2e);
-            }
-        }
-        // most chunks hold nothing above the thread's P-th best: their max
-        // (cm) says so without a per-column test
-        uint32_t pend = 0;
-        const float th = tp.tv[TOPP - 1];
-        if (cm > th) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) pend |= (x[j] > th ? 1u : 0u) << j;
-        }
-        if (__any_sync(0xffffffffu, pend != 0)) {
-            if (pend) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) xs[j] = x[j];
-            }
-            __syncwarp();
-            while (__any_sync(0xffffffffu, pend != 0)) {
-                if (pend) {
-                    const uint32_t j = __ffs(pend) - 1;
-                    pend &= pend - 1;
-                    const float xv = xs[j];
-                    // columns reach a thread in increasing order, so every
-                    // entry holds a smaller column and wins a tie: the new
-                    // one goes behind all entries >= xv (each slot decided
-                    // from the old values, no chain of swaps)
-                    if (xv > tp.tv[TOPP - 1]) {
-                        const uint32_t col = nb + j;
-#pragma unroll
-                        for (int p = TOPP - 1; p > 0; --p) {
-                            const bool before_prev = xv > tp.tv[p - 1];
-                            const bool before_cur = xv > tp.tv[p];
-                            tp.tv[p] = before_prev ? tp.tv[p - 1] : (before_cur ? xv : tp.tv[p]);
-                            tp.ti[p] = before_prev ? tp.ti[p - 1] : (before_cur ? col : tp.ti[p]);
-                        }
-                        if (xv > tp.tv[0]) {
-                            tp.tv[0] = xv;
-                            tp.ti[0] = col;
-                        }
-                    }
+                for (int p = TOPP - 1; p > 0; --p) {
+                    const bool before_prev = xv > tp.tv[p - 1];
+                    const bool before_cur = xv > tp.tv[p];
+                    tp.tv[p] = before_prev ? tp.tv[p - 1] : (before_cur ? xv : tp.tv[p]);
+                    tp.ti[p] = before_prev ? tp.ti[p - 1] : (before_cur ? col : tp.ti[p]);
+                }
+                if (xv > tp.tv[0]) {
+                    tp.tv[0] = xv;
+                    tp.ti[0] = col;
                 }
             }
-            __syncwarp();
         }
+    }
+}
+
+// The fused top-P epilogue on a thread's 64 columns of a tile (accumulator
+// chunks v0, v1; columns nb..nb+63; rows m >= M take part in the warp's
+// collectives with no effect): the logits' max and exp-sum by trees over
+// all 64 (three-input max, packed FP32 adds and multiply-adds) and one
+// online-softmax combine; then each chunk's logits above the thread's P-th
+// best enter its top-P. Most chunks hold none: the 64 columns' max says so
+// without a per-column test.
+__device__ __forceinline__ void topp_pair(const float (&v0)[32], const float (&v1)[32], const float (&b0)[32],
+                                          const float (&b1)[32], uint32_t m, uint32_t M, uint32_t nb, uint32_t N,
+                                          TopP &tp, float *xs)
+{
+    constexpr float kLog2e = 1.4426950408889634f;
+    float x[64];
+    if (nb + 64 <= N && m < M) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+            const float2 r0 = __fadd2_rn(make_float2(v0[j], v0[j + 1]), make_float2(b0[j], b0[j + 1]));
+            const float2 r1 = __fadd2_rn(make_float2(v1[j], v1[j + 1]), make_float2(b1[j], b1[j + 1]));
+            x[j] = r0.x;
+            x[j + 1] = r0.y;
+            x[32 + j] = r1.x;
+            x[32 + j + 1] = r1.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            x[j] = (m < M && nb + j < N) ? v0[j] + b0[j] : -INFINITY;
+            x[32 + j] = (m < M && nb + 32 + j < N) ? v1[j] + b1[j] : -INFINITY;
+        }
+    }
+    float t[22];
+#pragma unroll
+    for (int j = 0; j < 21; ++j) t[j] = fmax3(x[3 * j], x[3 * j + 1], x[3 * j + 2]);
+    t[21] = x[63];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) t[j] = fmax3(t[3 * j], t[3 * j + 1], t[3 * j + 2]);
+    t[7] = t[21];
+    const float cm = fmax3(fmax3(t[0], t[1], t[2]), fmax3(t[3], t[4], t[5]), fmaxf(t[6], t[7]));
+    if (cm > -INFINITY) {
+        const float off = -cm * kLog2e;
+        float2 e[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const float2 a = __ffma2_rn(make_float2(x[2 * j], x[2 * j + 1]), make_float2(kLog2e, kLog2e),
+                                        make_float2(off, off));
+            e[j] = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+        }
+#pragma unroll
+        for (int w = 16; w; w >>= 1)
+#pragma unroll
+            for (int j = 0; j < w; ++j) e[j] = __fadd2_rn(e[j], e[j + w]);
+        const float cs = e[0].x + e[0].y;
+        if (cm > tp.mx) {
+            tp.sm = tp.sm * ex2_approx((tp.mx - cm) * kLog2e) + cs;
+            tp.mx = cm;
+        } else {
+            tp.sm += cs * ex2_approx((cm - tp.mx) * kLog2e);
+        }
+    }
+    uint32_t pend0 = 0, pend1 = 0;
+    const float th = tp.tv[TOPP - 1];
+    if (cm > th) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            pend0 |= (x[j] > th ? 1u : 0u) << j;
+            pend1 |= (x[32 + j] > th ? 1u : 0u) << j;
+        }
+    }
+    if (__any_sync(0xffffffffu, pend0 != 0)) {
+        if (pend0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) xs[j] = x[j];
+        }
+        __syncwarp();
+        topp_insert(tp, xs, pend0, nb);
+        __syncwarp();
+    }
+    if (__any_sync(0xffffffffu, pend1 != 0)) {
+        if (pend1) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) xs[j] = x[32 + j];
+        }
+        __syncwarp();
+        topp_insert(tp, xs, pend1, nb + 32);
+        __syncwarp();
     }
 }
 
@@ -572,16 +620,27 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 tp.reset();
                 cur_u = u;
             }
-#pragma unroll 1
-            for (uint32_t c0 = h * (BN / 2); c0 < (h + 1) * (BN / 2); c0 += 32) {
-                float v[32];
-                __syncwarp();
-                tmem_ld32(tmem + buf * BN + ((q * 32u) << 16) + c0, v);
-                epilogue_chunk<EPI>(v, m, M, n0 + c0, N, e, tp, xs_all + (threadIdx.x - 64) * XS_STRIDE);
-            }
+            // the warp's two 32-column chunks of the tile in one round of
+            // accumulator loads; the accumulator is released to the MMA
+            // warp before the epilogue arithmetic
+            // (the chunks' bias loads are in flight meanwhile)
+            static_assert(BN / 2 == 64, "two 32-column chunks per epilogue warp and tile");
+            const uint32_t nb = n0 + h * (BN / 2);
+            float v0[32], v1[32], bias0[32], bias1[32];
+            load_bias32<EPI>(e, nb, N, bias0);
+            load_bias32<EPI>(e, nb + 32, N, bias1);
+            __syncwarp();
+            const uint32_t ta = tmem + buf * BN + ((q * 32u) << 16) + h * (BN / 2);
+            tmem_ld32x2(ta, ta + 32, v0, v1);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            if (EPI == EPI_TOPP) {
+                topp_pair(v0, v1, bias0, bias1, m, M, nb, N, tp, xs_all + (threadIdx.x - 64) * XS_STRIDE);
+            } else {
+                epilogue_chunk<EPI>(v0, bias0, m, M, nb, N, e);
+                epilogue_chunk<EPI>(v1, bias1, m, M, nb + 32, N, e);
+            }
         }
         if (EPI == EPI_TOPP && cur_u != 0xFFFFFFFFu) {
             const uint32_t pm = rb_of_unit(cur_u) * BM + q * 32 + lane;

@@ -138,9 +138,13 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
+// (da, ia) < (db, ib) in (distance, id) order. Distances are squared L2,
+// never negative nor NaN, and non-negative floats order as their bit
+// patterns do, so the key compares as one 64-bit integer (bits, id): two
+// integer compares instead of three float and integer ones.
 __device__ __forceinline__ bool key_less(float da, uint32_t ia, float db, uint32_t ib)
 {
-    return da < db || (da == db && ia < ib);
+    return (((uint64_t)__float_as_uint(da) << 32) | ia) < (((uint64_t)__float_as_uint(db) << 32) | ib);
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt()
@@ -775,7 +779,6 @@ struct WarpSearch {
                 const uint32_t adj_bytes = v.deg_pad * 4;
                 const uint32_t dir_bytes = v.deg_pad * w * 4;
                 uint32_t pid = 0;
-                float pscale = 1.0f;
                 if (lane < np) {
                     const uint32_t b = par()[lane];
                     pid = bi()[b];
@@ -793,7 +796,9 @@ struct WarpSearch {
                                  bar());
                         bulk_g2s(prow() + lane * a.prow_bytes, v.codes + (uint64_t)pid * v.row_bytes, v.row_bytes,
                                  bar());
-                        if (RST != ANN_F32) pscale = __ldg(v.scales + pid);
+                        // the parent's scale replaces its queue slot in
+                        // par() (read by DGS after the wait)
+                        if (RST != ANN_F32) par()[lane] = __float_as_uint(__ldg(v.scales + pid));
                     }
                 }
                 if (!wait_copies()) return false;
@@ -804,7 +809,8 @@ struct WarpSearch {
                 for (uint32_t pi = 0; pi < np; ++pi) {
                     uint32_t km = 0xffffffffu;
                     if (dgs_now) {
-                        km = dgs_keep(v, pi, n_keep, min_match, __shfl_sync(0xffffffffu, pscale, pi));
+                        km = dgs_keep(v, pi, n_keep, min_match,
+                                      RST != ANN_F32 ? __uint_as_float(par()[pi]) : 1.0f);
                         mark(PH_DGS);
                     }
                     nc = collect_row(v, pi, km, nc);
@@ -1035,9 +1041,9 @@ __global__ void __launch_bounds__(128, kSearchBlocksPerSm) serve_kernel(const Ar
 
 uint32_t align16(uint32_t x) { return (x + 15) & ~15u; }
 
-Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, uint32_t W, uint32_t adj_words,
-                   uint32_t dir_words, uint32_t prow_bytes, uint32_t stage_rows, uint32_t stage_stride,
-                   uint32_t gbm_words, bool serve)
+Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, uint32_t W, uint32_t W_max,
+                   uint32_t adj_words, uint32_t dir_words, uint32_t prow_bytes, uint32_t stage_rows,
+                   uint32_t stage_stride, uint32_t gbm_words, bool serve)
 {
     Layout L{};
     uint32_t o = 0;
@@ -1059,7 +1065,7 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
     const uint32_t dir_part = align16(dir_words * 4) + align16(dir_words ? W * prow_bytes : 0);
     L.dir = take(std::max(dir_part, gbm_words * 4));
     L.prow = L.dir + align16(dir_words * 4);
-    L.par = take(W * 4);
+    L.par = take(W_max * 4);   // parents of an iteration of either stage
     L.stage = take(stage_rows * stage_stride);
     L.bar = take(16);
     L.qp = take(serve ? 96 : 0);
@@ -1238,7 +1244,8 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     warps = 4;
     Layout lay{};
     for (;;) {
-        lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W, adj_words, dir_words, a.prow_bytes,
+        lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W,
+                          std::max(q.W, ghost_entry(q.entry) ? q.Wg : 1u), adj_words, dir_words, a.prow_bytes,
                           a.stage_rows, a.stage_stride, a.gbm_words, serve);
         if ((size_t)lay.total * warps <= ix->smem_optin) break;
         // wide rows: fewer staged rows per round before fewer warps per block

@@ -94,6 +94,7 @@ TINY_PARAMS = [
     dict(itopk=64, max_iters=0, entry=1),                                     # ghost stage only
     dict(itopk=32, max_iters=48, entry=1, dgs_discard=0.7, ghost_search_width=2, ghost_max_iters=24),
     dict(itopk=64, max_iters=64, entry=1, ghost_search_width=4, ghost_itopk=48),
+    dict(itopk=64, max_iters=64, entry=1, dgs_discard=0.5, ghost_search_width=8, ghost_itopk=64),  # Wg > W
     dict(itopk=64, max_iters=64, dgs_min_match=0.55),                       # DGS by similarity
     dict(itopk=64, max_iters=64, entry=1, dgs_min_match=0.6, dgs_reexpand=1),
     dict(itopk=32, max_iters=96, search_width=2, entry=1, dgs_min_match=0.5, dgs_cooldown=0.5),
@@ -108,8 +109,10 @@ def test_tiny_f32(params):
 
 @pytest.mark.parametrize("storage", [O.F16, O.E4M3])
 @pytest.mark.parametrize("rerank", [0, 1])
-def test_tiny_low_precision(storage, rerank):
-    g, o = tiny_case().run(storage, seed=4001, itopk=64, max_iters=64, entry=1, dgs_discard=0.5, rerank=rerank)
+@pytest.mark.parametrize("width", [1, 3])
+def test_tiny_low_precision(storage, rerank, width):
+    g, o = tiny_case().run(storage, seed=4001, itopk=64, max_iters=64, entry=1, dgs_discard=0.5, rerank=rerank,
+                           search_width=width)
     assert_parity(g, o)
 
 
