@@ -779,10 +779,14 @@ __global__ void adamw_kernel(float *__restrict__ w, const float *__restrict__ g,
 // Merge the per-tile top-P partials of each row; seeds = ghost ids of the
 // top P (ties: smaller id), pmax = the largest softmax probability; a row
 // with pmax < tau gets ANN_INVALID_ID as its first seed (fall back to
-// random ghost seeds). One warp per row.
+// random ghost seeds). One warp per row: each lane merges its slots (each
+// read in one round of 8-byte loads) into a sorted top-P list, then P
+// rounds of a warp-wide maximum over the lists' heads take the row's top P
+// in order (the slots cover disjoint columns, so ids are distinct).
 __global__ void topp_merge_kernel(const float *__restrict__ part, uint32_t M, uint32_t ntiles, uint32_t P,
                                   float tau, uint32_t *__restrict__ seeds, float *__restrict__ pmax)
 {
+    constexpr int SLOT = 2 * TOPP + 2;
     __shared__ float sv[4][32 * TOPP];
     __shared__ uint32_t si[4][32 * TOPP];
     const uint32_t lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -794,12 +798,20 @@ __global__ void topp_merge_kernel(const float *__restrict__ part, uint32_t M, ui
     for (int p = 0; p < TOPP; ++p) { tv[p] = -INFINITY; ti[p] = 0xFFFFFFFFu; }
     float mx = -INFINITY, sm = 0.0f;
     for (uint32_t t = lane; t < ntiles; t += 32) {
-        const float *o = part + ((size_t)r * ntiles + t) * (2 * TOPP + 2);
+        const float2 *o2 = reinterpret_cast<const float2 *>(part + ((size_t)r * ntiles + t) * SLOT);
+        float o[SLOT];
+#pragma unroll
+        for (int k = 0; k < SLOT / 2; ++k) {
+            const float2 a = __ldg(o2 + k);
+            o[2 * k] = a.x;
+            o[2 * k + 1] = a.y;
+        }
         const float tm = o[2 * TOPP], ts = o[2 * TOPP + 1];
         if (ts > 0.0f) {
             if (tm > mx) { sm = sm * __expf(mx - tm) + ts; mx = tm; }
             else sm += ts * __expf(tm - mx);
         }
+#pragma unroll
         for (int p = 0; p < TOPP; ++p) {
             const float x = o[p];
             const uint32_t n = __float_as_uint(o[TOPP + p]);
@@ -819,23 +831,31 @@ __global__ void topp_merge_kernel(const float *__restrict__ part, uint32_t M, ui
     for (int o = 16; o; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
     float gs = (sm > 0.0f) ? sm * __expf(mx - gm) : 0.0f;
     for (int o = 16; o; o >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, o);
-    // top-P across lanes by rank: only lanes that read a slot hold
-    // candidates, so the ranking runs over those lanes' entries alone
-    const uint32_t nv = min(ntiles, 32u) * TOPP;
+    // top-P across lanes: P rounds of the best head (every lane ends each
+    // butterfly with the same winner; the lane holding it advances)
 #pragma unroll
     for (int p = 0; p < TOPP; ++p) {
         sv[wl][lane * TOPP + p] = tv[p];
         si[wl][lane * TOPP + p] = ti[p];
     }
     __syncwarp();
-    for (uint32_t e = lane; e < nv; e += 32) {
-        const float x = sv[wl][e];
-        const uint32_t n = si[wl][e];
-        if (n == 0xFFFFFFFFu) continue;
-        uint32_t rank = 0;
-        for (uint32_t f = 0; f < nv; ++f)
-            rank += si[wl][f] != 0xFFFFFFFFu && better(sv[wl][f], si[wl][f], x, n);
-        if (rank < P) seeds[(size_t)r * P + rank] = n;
+    uint32_t hp = 0;
+    for (uint32_t k = 0; k < P; ++k) {
+        const uint32_t id = hp < TOPP ? si[wl][lane * TOPP + hp] : 0xFFFFFFFFu;
+        const float v = hp < TOPP ? sv[wl][lane * TOPP + hp] : -INFINITY;
+        float bv = v;
+        uint32_t bid = id;
+        for (int o = 16; o; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const uint32_t oid = __shfl_xor_sync(0xffffffffu, bid, o);
+            if (oid != 0xFFFFFFFFu && (bid == 0xFFFFFFFFu || better(ov, oid, bv, bid))) {
+                bv = ov;
+                bid = oid;
+            }
+        }
+        if (bid == 0xFFFFFFFFu) break;   // no entries left (the same in every lane)
+        if (id == bid) ++hp;
+        if (lane == 0) seeds[(size_t)r * P + k] = bid;
     }
     __syncwarp();
     const float pm = gs > 0.0f ? 1.0f / gs : 0.0f;
