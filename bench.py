@@ -579,14 +579,47 @@ def leg_workload4(A, args, timer, verbose):
             "forms": res, "leg_s": time.time() - t0}
 
 
+def serve_trace(A, srv, reqs, rng, timer, per_request, batch_search):
+    """One request trace through a server: capacity with every request at
+    once, latency at half that rate (Poisson arrivals), the same requests as
+    one call each (per_request), and the share of sampled served results
+    equal to their batch search (batch_search(q, prm) -> ids)."""
+    nq = sum(len(q) for _, q, _ in reqs)
+
+    def play(rate):
+        t, trace = 0.0, []
+        for rid, q, prm in reqs:
+            if rate:
+                t += float(rng.exponential(1.0 / rate))
+            trace.append((t, rid, q, prm))
+        res, wall = A.replay(srv, trace, timeout_s=300)
+        lat = np.array([res[r][2] for _, r, _, _ in trace]) * 1e3
+        return res, {"qps": nq / wall, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99))}
+
+    served, burst = play(0.0)
+    _, half = play(0.5 * burst["qps"] / (nq / len(reqs)))
+    ms = timer(per_request, steps=3, warm=1)
+    same = sum(int(np.array_equal(batch_search(q, prm), served[rid][0])) for rid, q, prm in reqs[::10])
+    per_req_qps = nq / (ms / 1e3)
+    return {"requests": len(reqs), "queries": nq, "server_capacity_qps": burst["qps"],
+            "server_all_at_once": burst, "per_request_search_qps": per_req_qps,
+            "capacity_ratio_server_vs_per_request": burst["qps"] / per_req_qps,
+            "half_load": dict(half, offered_qps=0.5 * burst["qps"]),
+            "sampled_requests_equal_to_batch_search": f"{same}/{len(reqs[::10])}"}
+
+
 def leg_workload5(A, args, timer, verbose):
     """Workload 5 (20M x 96 FP16): request traces (k in {10, 100}, itopk in
     {64, 256}) through the continuous-batching server and as one ann_search
     per request with identical parameters: the capacity of each, the
     server's latency at half its capacity, and whether each served result
-    equals its batch search. Two size mixes: the recipe's batches of
-    1-4,096 queries, and small requests of 1-64 queries, where a launch per
-    request leaves most of the GPU idle."""
+    equals its batch search. Two size mixes with ghost staging: the
+    recipe's batches of 1-4,096 queries, and small requests of 1-64 queries,
+    where a launch per request leaves most of the GPU idle. Then the
+    recipe's batches with the learned entry (MLP 96 -> 512 -> 512 ->
+    200,000 trained on the GPU; the server predicts each request's ghost
+    seeds as it arrives, and ghost staging judges them)."""
     import torch
     from workloads import WORKLOADS, load_dataset
     spec = WORKLOADS[5]
@@ -596,13 +629,8 @@ def leg_workload5(A, args, timer, verbose):
                  device=timer.dev.index or 0)
     base = dict(entry=1, dgs_discard=0.5, ghost_itopk=64, ghost_max_iters=32, ghost_search_width=4, rerank=1,
                 seed=spec.seeds["search"])
-    srv = A.Server(ix, capacity=65536, max_requests=512,
-                   max_params=dict(base, k=100, itopk=256, max_iters=272))
-    A.replay(srv, [(0.0, 10**9 + i, ds.Q[:64], dict(base, k=10, itopk=64, max_iters=80, qid_base=0))
-                   for i in range(4)])
-    out = {}
-    for mix, (lo, hi, nreq) in (("batches_1_4096", (1, 4097, args.serve_requests)),
-                                ("small_1_64", (1, 65, 4 * args.serve_requests))):
+
+    def make_reqs(lo, hi, nreq, prm_base):
         rng = np.random.default_rng(spec.seeds["search"] + 7)
         reqs = []
         for rid in range(nreq):
@@ -610,46 +638,73 @@ def leg_workload5(A, args, timer, verbose):
             off = int(rng.integers(0, len(ds.Q) - n))
             k = int(rng.choice([10, 100]))
             L = max(k, int(rng.choice([64, 256])))
-            reqs.append((rid, ds.Q[off:off + n], dict(base, k=k, itopk=L, max_iters=L + 16, qid_base=rid << 20)))
-        nq = sum(len(q) for _, q, _ in reqs)
+            reqs.append((rid, ds.Q[off:off + n], dict(prm_base, k=k, itopk=L, max_iters=L + 16,
+                                                        qid_base=rid << 20)))
+        return reqs, rng
 
-        def play(rate):
-            t, trace = 0.0, []
-            for rid, q, prm in reqs:
-                if rate:
-                    t += float(rng.exponential(1.0 / rate))
-                trace.append((t, rid, q, prm))
-            res, wall = A.replay(srv, trace, timeout_s=300)
-            lat = np.array([res[r][2] for _, r, _, _ in trace]) * 1e3
-            return res, {"qps": nq / wall, "p50_ms": float(np.percentile(lat, 50)),
-                         "p99_ms": float(np.percentile(lat, 99))}
+    def dev_queries(reqs):
+        return [torch.from_numpy(np.ascontiguousarray(q)).to(timer.dev) for _, q, _ in reqs]
 
-        served, burst = play(0.0)
-        half_rate = 0.5 * burst["qps"] / (nq / len(reqs))
-        _, half = play(half_rate)
-        # the same requests, one ann_search each, back to back on one stream
-        # (queries already on the device; results stay there)
-        dq = [torch.from_numpy(np.ascontiguousarray(q)).to(timer.dev) for _, q, _ in reqs]
+    def ids_of(t):
+        torch.cuda.synchronize(timer.dev)
+        return t.cpu().numpy().view(np.uint32)
 
-        def per_request():
+    srv = A.Server(ix, capacity=65536, max_requests=512,
+                   max_params=dict(base, k=100, itopk=256, max_iters=272))
+    A.replay(srv, [(0.0, 10**9 + i, ds.Q[:64], dict(base, k=10, itopk=64, max_iters=80, qid_base=0))
+                   for i in range(4)])
+    out = {}
+    for mix, (lo, hi, nreq) in (("batches_1_4096", (1, 4097, args.serve_requests)),
+                                ("small_1_64", (1, 65, 4 * args.serve_requests))):
+        reqs, rng = make_reqs(lo, hi, nreq, base)
+        dq = dev_queries(reqs)
+
+        def per_request(reqs=reqs, dq=dq):
+            # one ann_search per request, back to back on one stream (queries
+            # already on the device; results stay there)
             for (rid, q, prm), qt in zip(reqs, dq):
                 ix.search(qt, stream=timer.stream, **prm)
 
-        ms = timer(per_request, steps=3, warm=1)
-        same = 0
-        for (rid, q, prm), qt in zip(reqs[::10], dq[::10]):
-            ids, d, _ = ix.search(qt, **prm)
-            torch.cuda.synchronize(timer.dev)
-            same += int(np.array_equal(ids.cpu().numpy().view(np.uint32), served[rid][0]))
-        per_req_qps = nq / (ms / 1e3)
-        out[mix] = {"requests": len(reqs), "queries": nq, "server_capacity_qps": burst["qps"],
-                    "server_all_at_once": burst, "per_request_search_qps": per_req_qps,
-                    "capacity_ratio_server_vs_per_request": burst["qps"] / per_req_qps,
-                    "half_load": dict(half, offered_qps=0.5 * burst["qps"]),
-                    "sampled_requests_equal_to_batch_search": f"{same}/{len(reqs[::10])}"}
+        def batch_search(q, prm):
+            return ids_of(ix.search(torch.from_numpy(np.ascontiguousarray(q)).to(timer.dev), **prm)[0])
+
+        out[mix] = serve_trace(A, srv, reqs, rng, timer, per_request, batch_search)
         if verbose:
-            print(f"[bench] serving {mix}: server {burst['qps'] / 1e6:.3f}M/s, per request {per_req_qps / 1e6:.3f}M/s, "
-                  f"half load p50 {half['p50_ms']:.2f} ms p99 {half['p99_ms']:.2f} ms", file=sys.stderr, flush=True)
+            r = out[mix]
+            print(f"[bench] serving {mix}: server {r['server_capacity_qps'] / 1e6:.3f}M/s, per request "
+                  f"{r['per_request_search_qps'] / 1e6:.3f}M/s, half load p50 {r['half_load']['p50_ms']:.2f} ms "
+                  f"p99 {r['half_load']['p99_ms']:.2f} ms", file=sys.stderr, flush=True)
+    srv.close()
+    # the learned entry: a second server that predicts each request's seeds
+    le, info = train_entry(ds, spec, ix, timer.dev, verbose, args.train_queries, args.epochs,
+                           judge_params=dict(ghost_itopk=64, ghost_max_iters=32, ghost_search_width=4,
+                                             ghost_max_iters_given=4))
+    lbase = dict(base, entry=2, ghost_max_iters_given=4, ghost_judge=le.judge)
+    le.seeds(torch.from_numpy(np.ascontiguousarray(ds.Q[:4096])).to(timer.dev))   # size the scratch once
+    srv = A.Server(ix, capacity=65536, max_requests=512, max_params=dict(lbase, k=100, itopk=256, max_iters=272),
+                   mlp=le.mlp, seeds_per_query=le.P, tau=le.tau)
+    A.replay(srv, [(0.0, 10**9 + i, ds.Q[:64], dict(lbase, k=10, itopk=64, max_iters=80, qid_base=0))
+                   for i in range(4)])
+    reqs, rng = make_reqs(1, 4097, args.serve_requests, lbase)
+    dq = dev_queries(reqs)
+
+    def per_request_learned():
+        # prediction + ann_search per request, back to back on one stream
+        for (rid, q, prm), qt in zip(reqs, dq):
+            seeds, _ = le.seeds(qt, stream=timer.stream)
+            ix.search(qt, given=seeds, stream=timer.stream, **prm)
+
+    def batch_search_learned(q, prm):
+        qt = torch.from_numpy(np.ascontiguousarray(q)).to(timer.dev)
+        return ids_of(ix.search(qt, given=le.seeds(qt)[0], **prm)[0])
+
+    out["learned_batches_1_4096"] = serve_trace(A, srv, reqs, rng, timer, per_request_learned, batch_search_learned)
+    out["learned_batches_1_4096"]["learned_entry"] = info
+    if verbose:
+        r = out["learned_batches_1_4096"]
+        print(f"[bench] serving learned: server {r['server_capacity_qps'] / 1e6:.3f}M/s, per request "
+              f"{r['per_request_search_qps'] / 1e6:.3f}M/s, half load p50 {r['half_load']['p50_ms']:.2f} ms "
+              f"p99 {r['half_load']['p99_ms']:.2f} ms", file=sys.stderr, flush=True)
     srv.close()
     # recall and the FP16 distance error against FP64 on a 1,000-query sample,
     # at the mix's smaller setting (k 10, itopk 64), stored and reranked
@@ -667,9 +722,17 @@ def leg_workload5(A, args, timer, verbose):
         rel = np.abs(de - ex)[ok] / np.maximum(ex[ok], 1e-30)
         quality[tag] = {"recall_at_10": recall_at(ie, gt[1], ds.X, ds.Q[:ns], 10),
                         "max_rel_distance_error": float(rel.max()), "mean_rel_distance_error": float(rel.mean())}
+    ids_l, _, st_l = ix.search(qd, given=le.seeds(qd)[0], stats=True, **dict(lbase, k=10, itopk=64, max_iters=80))
+    stn_l = A.stats_to_numpy(st_l)
+    _, _, st_g = ix.search(qd, stats=True, **dict(base, k=10, itopk=64, max_iters=80))
+    quality["learned_reranked"] = {"recall_at_10": recall_at(ids_of(ids_l), gt[1], ds.X, ds.Q[:ns], 10),
+                                   "ghost_rows": float(stn_l["ghost_vec_rows"].mean()),
+                                   "ghost_rows_ghost_staging": float(A.stats_to_numpy(st_g)["ghost_vec_rows"].mean())}
+    le.close()
     ix.close()
     return {"workload": spec.name, "n": spec.n, "dim": spec.d, "degree": spec.degree, "storage": "f16",
-            "entry": "ghost", "mixes": out, "quality_k10_itopk64": quality,
+            "entry": "ghost staging; learned entry (learned_batches_1_4096)", "mixes": out,
+            "quality_k10_itopk64": quality,
             "mix": "k {10,100}, itopk {64,256} raised to k, Poisson arrivals; batch sizes per mix",
             "leg_s": time.time() - t0}
 

@@ -70,7 +70,8 @@ class LearnedEntry:
         query farther from every ghost node it reached, continues as plain
         ghost staging. Returns the judge distance."""
         seeds, _ = self.seeds(val_queries, stream=stream)
-        p = dict(search_params, k=1, max_iters=0, entry=ENTRY_GIVEN_GHOST, ghost_judge=0.0)
+        # the ghost stage's own (stored-precision) distance, as the kernel's judge sees it
+        p = dict(search_params, k=1, max_iters=0, entry=ENTRY_GIVEN_GHOST, ghost_judge=0.0, rerank=0)
         p["itopk"] = max(1, int(p.get("ghost_itopk") or 64))
         _, d, _ = self.index.search(val_queries, given=seeds, stream=stream, **p)
         self.judge = self.mlp.confidence_threshold(d[:, 0].contiguous(), 1.0 - continue_fraction, stream=stream)
