@@ -20,10 +20,11 @@ from .binding import ENTRY_GHOST, ENTRY_GIVEN_GHOST, INVALID, MLP, Index
 
 
 def ghost_labels(index: Index, queries, seed: int, ghost_itopk: int = 64, ghost_max_iters: int = 64,
-                 stream=None):
+                 ghost_search_width: int = 1, stream=None):
     """Best ghost node of each query by ghost staging (CUDA int32 tensor)."""
     ids, _, _ = index.search(queries, k=1, itopk=ghost_itopk, max_iters=0, entry=ENTRY_GHOST,
-                             ghost_itopk=ghost_itopk, ghost_max_iters=ghost_max_iters, seed=seed, stream=stream)
+                             ghost_itopk=ghost_itopk, ghost_max_iters=ghost_max_iters,
+                             ghost_search_width=ghost_search_width, seed=seed, stream=stream)
     return index.ghost_index_of(ids[:, 0].contiguous(), stream=stream)
 
 

@@ -126,11 +126,11 @@ def test_learned_entry_5m():
     Qtr = torch.from_numpy(make_queries(spec, nq=200_000, seed=spec.seeds["query"] + 100)).cuda()
     Qva = torch.from_numpy(make_queries(spec, nq=5_000, seed=spec.seeds["query"] + 200)).cuda()
     le = LearnedEntry(ix, init_mlp_params(spec.d, 512, 512, spec.ghost_n, spec.seeds["mlp"]), max_batch=10_000)
-    losses = le.fit(Qtr, ghost_labels(ix, Qtr, seed=spec.seeds["search"]), epochs=8, seed=spec.seeds["mlp"])
-    tau, hit = le.calibrate(Qva, ghost_labels(ix, Qva, seed=spec.seeds["search"]))
-    assert losses[-1] < 0.5 * losses[0] and hit > 0.5   # measured: loss 8.0 -> 0.79, label in top 8 for 54%
-    common = dict(k=10, itopk=512, max_iters=528, dgs_discard=0.5, rerank=1, seed=spec.seeds["search"],
-                  ghost_itopk=512, ghost_search_width=8, ghost_max_iters=64)
+    gs = dict(ghost_itopk=512, ghost_search_width=8, ghost_max_iters=64)   # the search's ghost stage
+    losses = le.fit(Qtr, ghost_labels(ix, Qtr, seed=spec.seeds["search"], **gs), epochs=8, seed=spec.seeds["mlp"])
+    tau, hit = le.calibrate(Qva, ghost_labels(ix, Qva, seed=spec.seeds["search"], **gs))
+    assert losses[-1] < 0.5 * losses[0] and hit > 0.5
+    common = dict(k=10, itopk=512, max_iters=528, dgs_discard=0.5, rerank=1, seed=spec.seeds["search"], **gs)
     judge = le.calibrate_judge(Qva, **dict(common, ghost_max_iters_given=4))
     Q = torch.from_numpy(ds.Q).cuda()
     seeds, _ = le.seeds(Q)
