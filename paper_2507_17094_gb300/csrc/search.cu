@@ -171,6 +171,23 @@ __device__ __forceinline__ float stored_elem(const uint8_t *row, uint32_t i, flo
     return __fmul_rn(scale, __half2float(__half(h)));
 }
 
+// One element of the distance: acc += (q - stored)^2, the difference
+// rounded once. An FP16 row's scale is a power of two, so its stored value
+// s * h is exact in FP32 (for every row whose largest |x| is at least 2^-88,
+// where s * h stays a normal number) and q - s * h is one fused multiply-add,
+// equal to the rounded difference of q and the stored value; E4M3 scales are
+// not powers of two, so that stored value is rounded first.
+template <int ST>
+__device__ __forceinline__ void elem_step(float qv, const uint8_t *row, uint32_t i, float scale, float &acc)
+{
+    if (ST == ANN_F16) {
+        const float df = __fmaf_rn(-scale, __half2float(reinterpret_cast<const __half *>(row)[i]), qv);
+        acc = __fmaf_rn(df, df, acc);
+    } else {
+        step(qv, stored_elem<ST>(row, i, scale), acc);
+    }
+}
+
 // rn(y - x) and rn(acc + df * df) for two elements at once with the packed
 // FP32 pipe: fma(x, -1, y) rounds y - x once, so both results equal the
 // scalar __fsub_rn / __fmaf_rn of each component.
@@ -194,7 +211,7 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
                                                uint32_t h)
 {
     float2 s = make_float2(0.0f, 0.0f);  // s_{2h}, s_{2h+1}
-    const float2 sc = make_float2(scale, scale);
+    const float2 sc = make_float2(scale, scale), nsc = make_float2(-scale, -scale);
     uint32_t i = 0;
     if (ST == ANN_F32) {
 #pragma unroll 2
@@ -211,7 +228,9 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
                 const uint32_t e = i + 4 * g + 2 * h;
                 const __half2 hv = *reinterpret_cast<const __half2 *>(row + (size_t)e * 2);
                 const float2 y = *reinterpret_cast<const float2 *>(q + e);
-                step2(y, __fmul2_rn(sc, __half22float2(hv)), s);
+                // y - s h in one rounding (s h is exact: s is a power of two)
+                const float2 df = __ffma2_rn(nsc, __half22float2(hv), y);
+                s = __ffma2_rn(df, df, s);
             }
         }
     } else {
@@ -231,8 +250,8 @@ __device__ __forceinline__ float row_dist_half(const uint8_t *row, const float *
     // tail (d not a multiple of the vector width); i is a multiple of 4 here
     #pragma unroll 1
     for (; i < d; i += 4) {
-        if (i + 2 * h < d) step(q[i + 2 * h], stored_elem<ST>(row, i + 2 * h, scale), s.x);
-        if (i + 2 * h + 1 < d) step(q[i + 2 * h + 1], stored_elem<ST>(row, i + 2 * h + 1, scale), s.y);
+        if (i + 2 * h < d) elem_step<ST>(q[i + 2 * h], row, i + 2 * h, scale, s.x);
+        if (i + 2 * h + 1 < d) elem_step<ST>(q[i + 2 * h + 1], row, i + 2 * h + 1, scale, s.y);
     }
     return __fadd_rn(s.x, s.y);
 }
@@ -248,7 +267,7 @@ __device__ __forceinline__ float row_dist_quarter(const uint8_t *row, const floa
 {
     float s = 0.0f;
 #pragma unroll 4
-    for (uint32_t i = j; i < d; i += 4) step(q[i], stored_elem<ST>(row, i, scale), s);
+    for (uint32_t i = j; i < d; i += 4) elem_step<ST>(q[i], row, i, scale, s);
     return s;
 }
 

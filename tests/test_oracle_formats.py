@@ -90,6 +90,26 @@ def test_encode_f16_integer_data_is_exact():
     assert np.array_equal(O.decode(codes, scales, O.F16), X)
 
 
+def test_f16_stored_value_is_an_exact_product():
+    """An FP16 row's stored value s * h (s a power of two) is exact in FP32
+    for rows whose largest |x| is at least 2^-88, across magnitudes: so
+    q - s * h rounded once (one fused multiply-add, as the kernel forms it)
+    equals q minus the rounded stored value, as the oracle forms it."""
+    rng = np.random.default_rng(8)
+    mags = 2.0 ** rng.uniform(-88, 100, size=(400, 1))
+    X = (rng.standard_normal((400, 64)) * mags).astype(np.float32)
+    X[:5, 10:] = 0.0
+    codes, scales = O.encode(X, O.F16)
+    h = O.decode(codes, np.ones_like(scales), O.F16).astype(np.float64)
+    exact = scales[:, None].astype(np.float64) * h
+    stored = O.decode(codes, scales, O.F16)
+    assert np.array_equal(stored.astype(np.float64), exact)
+    Q = (rng.standard_normal((400, 64)) * mags).astype(np.float32)
+    two_step = (Q - stored).astype(np.float32)                      # rn(q - rn(s h))
+    fused = (Q.astype(np.float64) - exact).astype(np.float32)       # rn(q - s h): q - s h is exact in FP64 here
+    assert np.array_equal(two_step, fused)
+
+
 def test_encode_e4m3_error_bound():
     rng = np.random.default_rng(4)
     X = (rng.standard_normal((200, 96)) * rng.uniform(0.1, 50, (200, 1))).astype(np.float32)
