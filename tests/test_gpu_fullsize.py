@@ -115,9 +115,8 @@ def test_learned_entry_5m():
     clusters), at the benchmark's operating point (itopk 512, a 512-entry
     ghost queue with 8 parents per ghost iteration; the network's labels
     from that ghost stage). Measured on 1,000 queries: ghost staging
-    0.948-0.958, the learned entry with its judge 0.951-0.963 (in-distribution
-    0.988, between clusters 0.80-0.86) with a third of the ghost rows. The
-    floor 0.945 allows the sample's error (about 0.005)."""
+    0.949-0.959, the learned entry with its judge 0.961-0.970 (in-distribution
+    0.988-0.991, between clusters 0.85-0.89) with a third of the ghost rows."""
     import paper_2507_17094_gb300 as A
     from paper_2507_17094_gb300.entry import LearnedEntry, ghost_labels
     from workloads import WORKLOADS, init_mlp_params, load_dataset, make_queries, off_distribution_mask
@@ -159,7 +158,7 @@ def test_learned_entry_5m():
           f"{out['learned'][1]:.0f} {out['learned'][2] / 1e6:.3f}M QPS (predict included); tau {tau:.3g}, "
           f"judge {judge:.4g}, val hit {hit:.3f}, fallback {float((seeds[:, 0] == -1).float().mean()):.3f}")
     assert out["learned"][1] < 0.5 * out["ghost"][1]
-    assert out["learned"][0] >= 0.945 and out["learned"][0] >= out["ghost"][0] - 0.005
+    assert out["learned"][0] >= 0.95 and out["learned"][0] >= out["ghost"][0] - 0.005
     assert out["learned"][3] >= 0.98
     le.close()
     ix.close()
