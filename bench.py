@@ -34,6 +34,7 @@ import time
 
 import numpy as np
 
+T_START = time.time()
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -898,6 +899,62 @@ def leg_ppe(A, args, timer, verbose):
 
 
 # ------------------------------------------------------------------ our arm
+LEG_FNS = {"3": leg_workload3, "4": leg_workload4, "5": leg_workload5, "wide": leg_wide, "ppe": leg_ppe,
+           "build": leg_build}
+LEG_KEYS = {"3": "precision-10M-128d-int", "4": "learned-5M-256d-zipf", "5": "serving-20M-96d",
+            "wide": "wide_vectors", "ppe": "path_extension", "build": "index_build"}
+FINAL_RESERVE_S = 30.0   # kept back for the JSON line after the last leg
+MIN_LEG_S = 60.0         # a leg is not started with less than this left
+
+
+def run_leg_child(w: str, args, device: int, verbose: bool) -> dict:
+    """Run one side leg as `bench.py --leg w` in a child process (its own
+    CUDA context, its own process group) with a deadline of what is left of
+    --budget-s. A leg that would start too late is skipped, one that runs
+    past the deadline is ended; either is recorded in its place."""
+    left = args.budget_s - (time.time() - T_START) - FINAL_RESERVE_S
+    if left < MIN_LEG_S:
+        return {"skipped": f"wall budget: {max(left, 0.0):.0f} s left of --budget-s {args.budget_s:.0f}"}
+    cmd = [sys.executable, os.path.abspath(__file__), "--leg", w, "--leg-device", str(device),
+           "--steps", str(args.steps), "--warmup", str(args.warmup), "--gt-sample", str(args.gt_sample),
+           "--train-queries", str(args.train_queries), "--epochs", str(args.epochs),
+           "--serve-requests", str(args.serve_requests)] + (["-v"] if verbose else [])
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "LOCAL_WORLD_SIZE", "GROUP_RANK", "ROLE_RANK",
+                        "TORCHELASTIC_RUN_ID")}
+    t0 = time.time()
+    proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=None, text=True, env=env, cwd=ROOT,
+                            start_new_session=True)
+    try:
+        out, _ = proc.communicate(timeout=left)
+    except subprocess.TimeoutExpired:
+        os.killpg(proc.pid, 9)
+        proc.communicate()
+        return {"skipped": f"ended at the wall budget after {time.time() - t0:.0f} s "
+                           f"(--budget-s {args.budget_s:.0f})"}
+    if verbose:
+        print(f"[bench] leg {w} done in {time.time() - t0:.0f}s (rc {proc.returncode})", file=sys.stderr,
+              flush=True)
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    if proc.returncode != 0 or not lines:
+        return {"failed": f"child exited {proc.returncode}", "stdout_tail": out[-500:]}
+    return json.loads(lines[-1])
+
+
+def run_leg(args):
+    """Child side of run_leg_child: one leg on one GPU, its result as one
+    JSON line on stdout."""
+    import torch
+    import paper_2507_17094_gb300 as A
+    torch.cuda.set_device(args.leg_device)
+    dev = torch.device("cuda", args.leg_device)
+    A.build()
+    timer = Timer(dev, torch.cuda.current_stream(dev))
+    res = LEG_FNS[args.leg](A, args, timer, args.verbose)
+    torch.cuda.synchronize(dev)
+    print(json.dumps(res), flush=True)
+
+
 def run_ours(args):
     import torch
     import paper_2507_17094_gb300 as A
@@ -1166,6 +1223,8 @@ def run_ours(args):
                         "ids_match_gpu": match}
 
     # ------------------------------------------------------------ workloads 3-5 and path extension
+    # each leg runs in a child process with what is left of the wall budget,
+    # so the line below is printed in bounded time whatever the legs cost
     legs = {}
     if rank == 0 and world == 1 and args.workloads:
         for le_ in entries.values():
@@ -1174,16 +1233,11 @@ def run_ours(args):
         for ix_ in indexes.values():
             ix_.close()
         indexes.clear()
-        timer = Timer(dev, stream)
-        fns = {"3": leg_workload3, "4": leg_workload4, "5": leg_workload5, "wide": leg_wide, "ppe": leg_ppe,
-               "build": leg_build}
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
         for w in args.workloads.split(","):
-            if w in fns:
-                t0 = time.time()
-                legs[w] = fns[w](A, args, timer, verbose)
-                torch.cuda.empty_cache()
-                if verbose:
-                    print(f"[bench] leg {w} done in {time.time() - t0:.0f}s", file=sys.stderr, flush=True)
+            if w in LEG_FNS:
+                legs[w] = run_leg_child(w, args, local, verbose)
 
     peaks = measured_peaks()
     achieved = bytes_per_launch / mean_launch_s / 1e9
@@ -1216,9 +1270,8 @@ def run_ours(args):
         "cpu_baseline": cpu_baseline,
         "serving": serving,
         "phase_profile": phase_profile,
-        "workloads": {legs[w]["workload"] if w not in ("ppe", "wide", "build") else
-                      {"ppe": "path_extension", "wide": "wide_vectors", "build": "index_build"}[w]: legs[w]
-                      for w in legs},
+        "workloads": {LEG_KEYS[w]: legs[w] for w in legs},
+        "wall_s": time.time() - T_START, "budget_s": args.budget_s,
     }
     for le in entries.values():
         le.close()
@@ -1342,13 +1395,19 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--workloads", default="3,4,5,wide,ppe,build",
                     help="legs beside the headline (rank 0, one GPU): 3, 4, 5, wide, ppe and build; empty for none")
+    ap.add_argument("--budget-s", type=float, default=1020.0,
+                    help="wall-clock budget of the whole run; the side legs get what the headline leaves")
+    ap.add_argument("--leg", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--leg-device", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--predict-shapes", action="store_true",
                     help="time only the learned entry's prediction on two network shapes (GEMM profiling)")
     ap.add_argument("-v", "--verbose", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.predict_shapes:
+    if args.leg:
+        run_leg(args)
+    elif args.predict_shapes:
         run_predict_shapes(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -39,3 +39,26 @@ def test_form_selection_and_operating_points():
     assert sim["dgs_discard"] == 0.0 and 0.0 < sim["dgs_min_match"] <= 1.0   # the two rules are alternatives
     p = bench.params_for(forms["paper_fp32"], 32, 7)
     assert p["itopk"] == 32 and p["max_iters"] == 32 + 16 and "storage" not in p
+
+
+def test_side_legs_keep_to_the_wall_budget(monkeypatch):
+    """A side leg that would start with too little budget left is skipped; one
+    that runs past its deadline is ended (its whole process group) and
+    recorded, so the benchmark's line is still printed."""
+    import argparse
+    import subprocess
+    import time
+    import bench
+    args = argparse.Namespace(budget_s=0.0, steps=3, warmup=3, gt_sample=10, train_queries=10, epochs=1,
+                              serve_requests=1)
+    assert "skipped" in bench.run_leg_child("3", args, 0, False)
+
+    real_popen = subprocess.Popen
+    monkeypatch.setattr(bench, "MIN_LEG_S", 1.0)
+    monkeypatch.setattr(bench.subprocess, "Popen",
+                        lambda cmd, **kw: real_popen(["sleep", "30"], **kw))
+    args.budget_s = (time.time() - bench.T_START) + bench.FINAL_RESERVE_S + 2.0
+    t0 = time.time()
+    res = bench.run_leg_child("3", args, 0, False)
+    assert "ended at the wall budget" in res["skipped"]
+    assert time.time() - t0 < 10.0
