@@ -487,8 +487,12 @@ struct WarpSearch {
         }
         if (nc == 0) return;
         // 2. insertion point in the queue and rank among the candidates (the
-        //    counting loops here and in step 3 unroll by two only, to keep the
-        //    kernel's code small: it is bound by instruction fetch)
+        //    counting loop unrolls by two only, to keep the kernel's code
+        //    small: it is bound by instruction fetch). lr[rank] = insertion
+        //    point, in the staging area (free between gathers): candidate
+        //    keys are distinct, so ranks are a permutation, and a larger key
+        //    never has a smaller insertion point, so lr is non-decreasing.
+        uint32_t *lr = reinterpret_cast<uint32_t *>(stage());
         uint32_t min_lb = 0xffffffffu;
         #pragma unroll 1
         for (uint32_t c = lane; c < nc; c += 32) {
@@ -504,12 +508,14 @@ struct WarpSearch {
                 else hi = mid;
             }
             ks[c] = lo | (r << 16);
+            lr[r] = lo;
             min_lb = min(min_lb, lo);
         }
         for (int o = 16; o; o >>= 1) min_lb = min(min_lb, __shfl_xor_sync(0xffffffffu, min_lb, o));
         __syncwarp();
         // 3. shift queue entries [min_lb, cnt) by the number of candidates
-        //    inserted before them, last chunk first (in place)
+        //    inserted before them (those whose insertion point is <= the
+        //    entry's slot: a binary search of lr), last chunk first (in place)
         if (cnt > min_lb) {
             #pragma unroll 1
             for (int32_t top = (int32_t)cnt - 1; top >= (int32_t)min_lb; top -= 32) {
@@ -521,8 +527,12 @@ struct WarpSearch {
                     dd = qd[b];
                     id = qi[b];
                     s = qs[b];
-#pragma unroll 2
-                    for (uint32_t c = 0; c < nc; ++c) shift += (ks[c] & 0xffffu) <= (uint32_t)b;
+                    uint32_t hi = nc;
+                    while (shift < hi) {
+                        const uint32_t mid = (shift + hi) >> 1;
+                        if (lr[mid] <= (uint32_t)b) shift = mid + 1;
+                        else hi = mid;
+                    }
                 }
                 __syncwarp();
                 if (mine && (uint32_t)b + shift < lcap) {
@@ -1085,7 +1095,8 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
     L.dir = take(std::max(dir_part, gbm_words * 4));
     L.prow = L.dir + align16(dir_words * 4);
     L.par = take(W_max * 4);   // parents of an iteration of either stage
-    L.stage = take(stage_rows * stage_stride);
+    // the staged rows; the merge keeps its candidates' insertion points here
+    L.stage = take(std::max(stage_rows * stage_stride, cap_cand * 4));
     L.bar = take(16);
     L.qp = take(serve ? 96 : 0);
     L.total = align16(o);
