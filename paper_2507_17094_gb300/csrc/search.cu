@@ -1259,7 +1259,6 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     // dimensions) are computed by four lanes each, at most 8 per round;
     // narrower ones by lane pairs, 16 per round
     a.lpr = stage_bytes > 1024 ? 4 : 2;
-    a.stage_rows = (uint32_t)std::min<int>(32 / (int)a.lpr, std::max(1, env_int("ANN_STAGE_ROWS", 16)));
     // visited tables: the queue plus one iteration's candidates must fit in
     // half a table (the reset threshold)
     if (cap_buf + cap_cand > (1u << (kVisitedBits - 1))) {
@@ -1271,30 +1270,61 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     a.vbits = ix->visited.bits;   // 4,096 entries: measured faster than 2,048 or 1,024 (L2-resident either way)
     a.slot_base = 0;
     a.gbm_words = (ghost_entry(q.entry) && ix->n_ghost <= kGhostBitmapMax) ? (ix->n_ghost + 31) / 32 : 0;
-    warps = 4;
-    Layout lay{};
-    for (;;) {
-        lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W,
-                          std::max(q.W, ghost_entry(q.entry) ? q.Wg : 1u), adj_words, dir_words, a.prow_bytes,
-                          a.stage_rows, a.stage_stride, a.gbm_words, serve);
-        if ((size_t)lay.total * warps <= ix->smem_optin) break;
-        // wide rows: fewer staged rows per round before fewer warps per block
-        if (a.stage_rows > 4) { a.stage_rows /= 2; continue; }
-        if (warps > 1) { warps /= 2; continue; }
-        set_error("ann_search: per-query state (%u bytes) exceeds shared memory", lay.total);
-        return ANN_EINVAL;
+    // Shape for `rows` staged rows per gather round: the per-warp layout,
+    // warps per block (wide rows: fewer staged rows before fewer warps) and
+    // resident blocks per SM. False if no shape fits.
+    struct Shape {
+        Layout lay;
+        uint32_t rows;
+        int warps, nb;
+        size_t smem;
+    };
+    auto fit = [&](uint32_t rows, Shape &sh) -> bool {
+        sh.rows = rows;
+        sh.warps = 4;
+        for (;;) {
+            sh.lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W,
+                                 std::max(q.W, ghost_entry(q.entry) ? q.Wg : 1u), adj_words, dir_words,
+                                 a.prow_bytes, sh.rows, a.stage_stride, a.gbm_words, serve);
+            if ((size_t)sh.lay.total * sh.warps <= ix->smem_optin) break;
+            if (sh.rows > 4) { sh.rows /= 2; continue; }
+            if (sh.warps > 1) { sh.warps /= 2; continue; }
+            set_error("ann_search: per-query state (%u bytes) exceeds shared memory", sh.lay.total);
+            return false;
+        }
+        sh.smem = (size_t)sh.lay.total * sh.warps;
+        switch (ix->storage) {
+        case ANN_F32: sh.nb = blocks_per_sm<ANN_F32>(sh.warps, sh.smem, a.lpr); break;
+        case ANN_F16: sh.nb = blocks_per_sm<ANN_F16>(sh.warps, sh.smem, a.lpr); break;
+        default: sh.nb = blocks_per_sm<ANN_E4M3>(sh.warps, sh.smem, a.lpr); break;
+        }
+        if (sh.nb <= 0) {
+            set_error("ann_search: kernel does not fit on an SM (%zu bytes shared)", sh.smem);
+            return false;
+        }
+        return true;
+    };
+    // The staged rows take most of a warp's shared memory. With the full
+    // round (16 rows, 8 wide ones) shared memory can hold fewer warps than
+    // the registers allow (large queues, 1 KB rows); half a round then
+    // doubles the gather rounds but admits more resident warps, and the
+    // latency those warps hide is worth more (measured: +19% to +43% where
+    // the warps per SM rose, -18% where they did not). So half a round is
+    // taken only when it admits more warps per SM. ANN_STAGE_ROWS fixes the
+    // count instead (experiments).
+    const int env_rows = env_int("ANN_STAGE_ROWS", 0);
+    const uint32_t full = 32 / a.lpr;
+    Shape best;
+    if (!fit(env_rows > 0 ? (uint32_t)std::min<int>((int)full, env_rows) : full, best)) return ANN_EINVAL;
+    if (env_rows <= 0 && best.rows == full) {
+        Shape half;
+        if (fit(full / 2, half) && half.nb * half.warps > best.nb * best.warps) best = half;
     }
-    a.lay = lay;
-    smem = (size_t)lay.total * warps;
-    switch (ix->storage) {
-    case ANN_F32: nb = blocks_per_sm<ANN_F32>(warps, smem, a.lpr); break;
-    case ANN_F16: nb = blocks_per_sm<ANN_F16>(warps, smem, a.lpr); break;
-    default: nb = blocks_per_sm<ANN_E4M3>(warps, smem, a.lpr); break;
-    }
-    if (nb <= 0) {
-        set_error("ann_search: kernel does not fit on an SM (%zu bytes shared)", smem);
-        return ANN_EINVAL;
-    }
+    a.stage_rows = best.rows;
+    a.lay = best.lay;
+    warps = best.warps;
+    smem = best.smem;
+    nb = best.nb;
     return ANN_OK;
 }
 
