@@ -113,6 +113,8 @@ struct Args {
     int *err;
     Layout lay;
     uint32_t cap_cand, stage_rows, stage_stride, prow_bytes;
+    // the rerank's FP32 rows in the same staging area: rows per round, stride
+    uint32_t rr_rows, rr_stride;
     // visited tables: slot_base + warp slot selects one table of 2^vbits
     // entries (tables 2^vstride_bits entries apart)
     uint32_t *vtab;
@@ -404,14 +406,13 @@ struct WarpSearch {
     }
 
     // ----------------------------------------------------- evaluate rows
-    // Distances of rows ids[0, n) of `codes` into out[0, n), stage_rows
-    // (<= 32 / LPR) rows per bulk-copy round; lanes LPR r .. LPR r + LPR - 1
-    // compute row r (a lane pair, or four lanes for wide rows).
+    // Distances of rows ids[0, n) of `codes` into out[0, n), R (<= 32 / LPR)
+    // rows of `stride` bytes per bulk-copy round; lanes LPR r .. LPR r + LPR
+    // - 1 compute row r (a lane pair, or four lanes for wide rows).
     template <int RST>
     __device__ bool evaluate(const uint8_t *codes, const float *scales, uint32_t row_bytes, const uint32_t *ids,
-                             uint32_t n, float *out)
+                             uint32_t n, float *out, uint32_t R, uint32_t stride)
     {
-        const uint32_t R = a.stage_rows;
         #pragma unroll 1
         for (uint32_t b0 = 0; b0 < n; b0 += R) {
             const uint32_t rows = min(R, n - b0);
@@ -423,7 +424,7 @@ struct WarpSearch {
             __syncwarp();
             if (lane < rows) {
                 const uint32_t v = ids[b0 + lane];
-                bulk_g2s(stage() + lane * a.stage_stride, codes + (uint64_t)v * row_bytes, row_bytes, bar());
+                bulk_g2s(stage() + lane * stride, codes + (uint64_t)v * row_bytes, row_bytes, bar());
                 if (RST != ANN_F32) scale = __ldg(scales + v);
             }
             if (!wait_copies()) return false;
@@ -432,10 +433,10 @@ struct WarpSearch {
             const float rs = __shfl_sync(0xffffffffu, scale, r);
             float part = 0.0f;
             if (LPR == 2) {
-                if (r < rows) part = row_dist_half<RST>(stage() + r * a.stage_stride, q(), rs, a.d, lane & 1);
+                if (r < rows) part = row_dist_half<RST>(stage() + r * stride, q(), rs, a.d, lane & 1);
             } else {
                 // sum j of the row, then (s0 + s1) and (s2 + s3) on lane pairs
-                if (r < rows) part = row_dist_quarter<RST>(stage() + r * a.stage_stride, q(), rs, a.d, lane & 3);
+                if (r < rows) part = row_dist_quarter<RST>(stage() + r * stride, q(), rs, a.d, lane & 3);
                 part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, 1));
             }
             const float other = __shfl_xor_sync(0xffffffffu, part, LPR / 2);
@@ -848,7 +849,8 @@ struct WarpSearch {
             }
             __syncwarp();
             hash_count += nc;
-            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd())) return false;
+            if (!evaluate<RST>(v.codes, v.scales, v.row_bytes, ci(), nc, cd(), a.stage_rows, a.stage_stride))
+                return false;
             c_rows += nc;
             merge(nc, lcap);
             mark(PH_MERGE);
@@ -948,7 +950,10 @@ struct WarpSearch {
         }
         if (ok && qp.rerank) {
             // FP32 distances of the whole queue on the originals, then the top k
-            ok = evaluate<ANN_F32>(a.x32, nullptr, a.row32_bytes, bi(), cnt, bd());
+            // (a launch planned without rerank has no rerank rounds: such a
+            // query fails instead of looping)
+            ok = a.rr_rows > 0 && evaluate<ANN_F32>(a.x32, nullptr, a.row32_bytes, bi(), cnt, bd(), a.rr_rows,
+                                                    a.rr_stride);
             st.rerank_rows += cnt;
             if (ok) {
                 #pragma unroll 1
@@ -1072,7 +1077,7 @@ uint32_t align16(uint32_t x) { return (x + 15) & ~15u; }
 
 Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, uint32_t W, uint32_t W_max,
                    uint32_t adj_words, uint32_t dir_words, uint32_t prow_bytes, uint32_t stage_rows,
-                   uint32_t stage_stride, uint32_t gbm_words, bool serve)
+                   uint32_t stage_stride, uint32_t rr_stride, uint32_t gbm_words, bool serve)
 {
     Layout L{};
     uint32_t o = 0;
@@ -1095,8 +1100,9 @@ Layout make_layout(uint32_t d, uint32_t w, uint32_t cap_buf, uint32_t cap_cand, 
     L.dir = take(std::max(dir_part, gbm_words * 4));
     L.prow = L.dir + align16(dir_words * 4);
     L.par = take(W_max * 4);   // parents of an iteration of either stage
-    // the staged rows; the merge keeps its candidates' insertion points here
-    L.stage = take(std::max(stage_rows * stage_stride, cap_cand * 4));
+    // the staged rows (at least one of the rerank's FP32 rows); the merge
+    // keeps its candidates' insertion points here
+    L.stage = take(std::max(std::max(stage_rows * stage_stride, rr_stride), cap_cand * 4));
     L.bar = take(16);
     L.qp = take(serve ? 96 : 0);
     L.total = align16(o);
@@ -1253,8 +1259,12 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
     const bool dgs = q.n_keep < deg || q.min_match > 0;
     const uint32_t dir_words = dgs ? q.W * ix->deg_pad * ix->words : 0;
     a.prow_bytes = ix->row_bytes;
+    // the search stages stored rows; the rerank stages FP32 rows in the same
+    // area, fewer per round (it reads itopk rows per query, the search
+    // thousands), so the area is sized by the stored rows
     const uint32_t stage_bytes = std::max(ix->row_bytes, q.rerank ? a.row32_bytes : 0u);
-    a.stage_stride = smem_row_stride(stage_bytes);
+    a.stage_stride = smem_row_stride(ix->row_bytes);
+    a.rr_stride = q.rerank ? smem_row_stride(a.row32_bytes) : 0u;
     // rows of more than 1 KB (wide FP32 vectors, 512 and up to ANN_MAX_DIM
     // dimensions) are computed by four lanes each, at most 8 per round;
     // narrower ones by lane pairs, 16 per round
@@ -1285,7 +1295,7 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
         for (;;) {
             sh.lay = make_layout(ix->dim, ix->words, cap_buf, cap_cand, q.W,
                                  std::max(q.W, ghost_entry(q.entry) ? q.Wg : 1u), adj_words, dir_words,
-                                 a.prow_bytes, sh.rows, a.stage_stride, a.gbm_words, serve);
+                                 a.prow_bytes, sh.rows, a.stage_stride, a.rr_stride, a.gbm_words, serve);
             if ((size_t)sh.lay.total * sh.warps <= ix->smem_optin) break;
             if (sh.rows > 4) { sh.rows /= 2; continue; }
             if (sh.warps > 1) { sh.warps /= 2; continue; }
@@ -1321,6 +1331,7 @@ ann_status plan_args(ann_index *ix, const QParams &q, Args &a, int &warps, size_
         if (fit(full / 2, half) && half.nb * half.warps > best.nb * best.warps) best = half;
     }
     a.stage_rows = best.rows;
+    a.rr_rows = a.rr_stride ? std::min(full, std::max(1u, best.rows * a.stage_stride / a.rr_stride)) : 0u;
     a.lay = best.lay;
     warps = best.warps;
     smem = best.smem;
