@@ -903,6 +903,7 @@ LEG_FNS = {"3": leg_workload3, "4": leg_workload4, "5": leg_workload5, "wide": l
            "build": leg_build}
 LEG_KEYS = {"3": "precision-10M-128d-int", "4": "learned-5M-256d-zipf", "5": "serving-20M-96d",
             "wide": "wide_vectors", "ppe": "path_extension", "build": "index_build"}
+DEFAULT_LEGS = "3,4,5,wide,ppe,build"
 FINAL_RESERVE_S = 30.0   # kept back for the JSON line after the last leg
 MIN_LEG_S = 60.0         # a leg is not started with less than this left
 
@@ -1393,7 +1394,7 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--epochs", type=int, default=8)
-    ap.add_argument("--workloads", default="3,4,5,wide,ppe,build",
+    ap.add_argument("--workloads", default=DEFAULT_LEGS,
                     help="legs beside the headline (rank 0, one GPU): 3, 4, 5, wide, ppe and build; empty for none")
     ap.add_argument("--budget-s", type=float, default=1020.0,
                     help="wall-clock budget of the whole run; the side legs get what the headline leaves")

@@ -62,3 +62,21 @@ def test_side_legs_keep_to_the_wall_budget(monkeypatch):
     res = bench.run_leg_child("3", args, 0, False)
     assert "ended at the wall budget" in res["skipped"]
     assert time.time() - t0 < 10.0
+
+
+def test_side_leg_registry_and_failed_child(monkeypatch):
+    """Every default side leg has a runner and a result key; a child that
+    exits with an error is recorded as failed, not parsed."""
+    import argparse
+    import subprocess
+    import time
+    import bench
+    for w in bench.DEFAULT_LEGS.split(","):
+        assert w in bench.LEG_FNS and w in bench.LEG_KEYS
+    real_popen = subprocess.Popen
+    monkeypatch.setattr(bench.subprocess, "Popen",
+                        lambda cmd, **kw: real_popen(["sh", "-c", "echo '{\"partial\": 1}'; exit 3"], **kw))
+    args = argparse.Namespace(budget_s=(time.time() - bench.T_START) + bench.FINAL_RESERVE_S + bench.MIN_LEG_S + 60,
+                              steps=3, warmup=3, gt_sample=10, train_queries=10, epochs=1, serve_requests=1)
+    res = bench.run_leg_child("4", args, 0, False)
+    assert res["failed"] == "child exited 3"
