@@ -157,7 +157,11 @@ ann_status ann_index_export(const ann_index *index, int which, void *host_dst, u
  *   ids, dists   device, nq x k (caller-owned)
  *   stats        device, nq ann_query_stats, or NULL
  *   stream       cudaStream_t (NULL = legacy default stream)
- * Asynchronous on `stream`; returns after the launch. */
+ * Asynchronous on `stream`; returns after the launch. The launch shape is
+ * chosen per call from the parameters (rows gathered per round: 16, or 8 of
+ * rows over 1 KB, halved when that admits more resident warps per SM); the
+ * environment variable ANN_STAGE_ROWS fixes the rows per round instead (for
+ * experiments). Results do not depend on the shape. */
 ann_status ann_search(ann_index *index, const float *queries, uint32_t nq, const ann_search_params *params,
                       const uint32_t *given_seeds, uint32_t n_given, uint32_t *ids, float *dists,
                       ann_query_stats *stats, void *stream);
